@@ -1,0 +1,215 @@
+"""Do the oracle's pins catch plausible mistakes?
+
+Each case plants one slip in a private copy of the oracle's C source (a
+dropped term, a wrong sign, a swapped index or operand), builds it into a
+temporary library on the CPU and runs a fast battery of the pins used in
+test_oracle_*.py against it.  At least one pin must fail for every slip;
+the unmodified source must pass them all.
+"""
+import math
+import os
+import subprocess
+
+import mpmath
+import numpy as np
+import pytest
+
+import oracle
+import swof_inputs as si
+from mp_scheme import MPScheme
+from swe_closed_forms import dam_break_profile
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "swof_oracle.c")
+
+MUTATIONS = {
+    "drop_S_L": ("*f2l = F[1] + 0.5 * g * (hpa * hpa - hL * hL);", "*f2l = F[1];"),
+    "drop_S_R": ("*f2r = F[1] + 0.5 * g * (hmb * hmb - hR * hR);", "*f2r = F[1];"),
+    "Fc_sign": ("double fcx = hg *", "double fcx = -hg *"),
+    "Fc_dropped_y": ("- dtdy * ((o->fy2l[c] - o->fy2r[s]) + fcy);", "- dtdy * (o->fy2l[c] - o->fy2r[s]);"),
+    "modvel_swap": ("*unm = un[c] - (hpv * rh) * (0.5 * dun);", "*unm = un[c] - (hmv * rh) * (0.5 * dun);"),
+    "modvel_sign": ("*unp = un[c] + (hmv * rh) * (0.5 * dun);", "*unp = un[c] - (hmv * rh) * (0.5 * dun);"),
+    "hll_c1c2_swapped": ("F[k] = (c2 * FL[k] - c1 * FR[k]) * r", "F[k] = (c1 * FL[k] - c2 * FR[k]) * r"),
+    "hll_diffusion_sign": ("+ w * (UR[k] - UL[k]);", "+ w * (UL[k] - UR[k]);"),
+    "hll_c2_uses_minus": ("double c2 = fmax(unL + cL, unR + cR);", "double c2 = fmax(unL + cL, unR - cR);"),
+    "minmod_max": ("if (a >= 0.0 && b >= 0.0) return fmin(a, b);", "if (a >= 0.0 && b >= 0.0) return fmax(a, b);"),
+    "hydrostatic_min": ("double zmax = fmax(zpa, zmb);", "double zmax = fmin(zpa, zmb);"),
+    "eta_not_h": ("double de = oracle_minmod(ec - em, ep - ec);", "double de = oracle_minmod(h[c] - h[cm], h[cp] - h[c]);"),
+    "wall_no_negate": ("fill_ghost_x(o, qx, -1.0);", "fill_ghost_x(o, qx, 1.0);"),
+    "west_index": ("double hs = h[c] - dtdx * (o->fx1[c] - o->fx1[w])", "double hs = h[c] - dtdx * (o->fx1[c] - o->fx1[s])"),
+    "transverse_flux_axis": ("- dtdy * (o->fy3[c] - o->fy3[s]);", "- dtdy * (o->fx3[c] - o->fx3[s]);"),
+    "friction_h_power": ("double hinv43 = (y * y) * (y * y);", "double hinv43 = (y * y) * y;"),
+    "friction_old_speed_dropped": ("double den = 1.0 + (dt * g * n2) * speed * hinv43;", "double den = 1.0 + (dt * g * n2) * hinv43;"),
+    "heun_no_average": ("double h = 0.5 * (o->h[c] + o->h2[c]);", "double h = o->h2[c];"),
+    "ga_psi_sign": ("(1.0 + ((o->p.psi + h) * o->p.dtheta) / vi)", "(1.0 + ((o->p.psi - h) * o->p.dtheta) / vi)"),
+    "ga_suction_dropped": ("(1.0 + ((o->p.psi + h) * o->p.dtheta) / vi)", "(1.0 + (h * o->p.dtheta) / vi)"),
+    "cfl_dy_as_dx": ("double den = lx / o->dx + ly / o->dy;", "double den = lx / o->dx + ly / o->dx;"),
+    "cfl_uses_cell_not_face": ("fabs(o->xup[c]) + sqrt(g * o->xhp[c]));", "fabs(o->xum[c]) + sqrt(g * o->xhm[c]));"),
+    "rain_before_dt_scale": ("double rdt = dt * o->p.rain_rate;", "double rdt = o->p.rain_rate;"),
+    "icbrt_one_newton_step": ("for (int it = 0; it < 4; ++it) {", "for (int it = 0; it < 1; ++it) {"),
+}
+
+
+def _build_variant(tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"{name}: pattern must occur exactly once"
+    path = tmp_path / f"{name}.c"
+    path.write_text(src.replace(old, new))
+    so = tmp_path / f"lib{name}.so"
+    subprocess.run(["gcc", "-O1", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+                    str(path), "-o", str(so), "-lm"], check=True)
+    return oracle.load_library(str(so))
+
+
+# ---- the battery: each returns True when the pin holds -------------------
+
+def pin_mp_second_implementation(L):
+    rng = np.random.default_rng(3)
+    nx, ny = 5, 4
+    z = 0.2 * rng.standard_normal((ny, nx))
+    h = 0.5 + rng.random((ny, nx))
+    h[rng.random((ny, nx)) < 0.2] = 0.0
+    qx = h * 0.4 * rng.standard_normal((ny, nx))
+    qy = h * 0.4 * rng.standard_normal((ny, nx))
+    kw = dict(bc=(0, 1, 1, 0), manning_n=0.04, rain_rate=1e-3, ks=1e-4, psi=0.1, dtheta=0.3)
+    o = oracle.Oracle(nx, ny, 0.3, 0.25, z, friction=1, rain_t_off=1e9, infiltration=1,
+                      library=L, **kw)
+    o.set_state(h, qx, qy)
+    o.set_vinf(np.full((ny, nx), 0.01))
+    m = MPScheme(nx, ny, 0.3, 0.25, z, h, qx, qy, infiltration=True, **kw)
+    m.vinf = [[mpmath.mpf(0.01) for _ in range(nx)] for _ in range(ny)]
+    for _ in range(3):
+        m.step(o.step(1)[0])
+    ok = True
+    for a, b in zip(o.state(), m.state()):
+        ok &= bool(np.max(np.abs(a - b)) <= 1e-13 * max(np.max(np.abs(b)), 1e-300))
+    return ok
+
+
+def pin_lake_at_rest(L):
+    w = si.lake_at_rest(n=24, level=1.0)
+    o = oracle.Oracle(w.nx, w.ny, w.dx, w.dy, w.z, library=L)
+    o.set_state(w.h, w.qx, w.qy)
+    o.step(100)
+    h, qx, qy = o.state()
+    wet = w.h > 0
+    return bool(np.max(np.abs((h + w.z)[wet] - 1.0)) <= 1e-12
+                and np.max(np.abs(qx)) <= 1e-12 and np.max(np.abs(qy)) <= 1e-12)
+
+
+def pin_mass_and_positivity(L):
+    w = si.random_state(24, 20, seed=11, dry_frac=0.3, vel=1.2)
+    o = oracle.Oracle(w.nx, w.ny, w.dx, w.dy, w.z, library=L, friction=1, manning_n=0.03)
+    o.set_state(w.h, w.qx, w.qy)
+    m0 = o.diag()["volume"]
+    o.step(60)
+    d = o.diag()
+    return bool(abs(d["volume"] - m0) / m0 <= 1e-12 and d["min_h"] >= 0.0)
+
+
+def pin_stoker(L):
+    n, ny = 200, 4
+    dx = 10.0 / n
+    x = (np.arange(n) + 0.5) * dx
+    H = np.tile(np.where(x < 5.0, 1.0, 0.5), (ny, 1))
+    o = oracle.Oracle(n, ny, dx, dx, np.zeros_like(H), t_end=1.0, library=L)
+    o.set_state(H, 0 * H, 0 * H)
+    o.run_to(1.0)
+    h = o.state()[0][0]
+    he, _ = dam_break_profile(x, 1.0, 5.0, 1.0, 0.5)
+    return bool(np.sum(np.abs(h - he)) / np.sum(he) < 5e-3)
+
+
+def pin_symmetry(L):
+    wx = si.dam_break(n=32, dx=0.3, axis="x")
+    wy = si.dam_break(n=32, dx=0.3, axis="y")
+    res = []
+    for w in (wx, wy):
+        o = oracle.Oracle(w.nx, w.ny, w.dx, w.dy, w.z, library=L)
+        o.set_state(w.h, w.qx, w.qy)
+        o.step(20)
+        res.append(o.state())
+    return bool(np.array_equal(res[0][0], res[1][0].T) and np.array_equal(res[0][1], res[1][2].T))
+
+
+def pin_cfl_uniform(L):
+    h, u, v, dx, dy, n = 0.7, -0.9, 0.35, 0.4, 0.25, 6
+    o = oracle.Oracle(n, n, dx, dy, np.zeros((n, n)), bc=(1, 1, 1, 1), dt_max=10.0, library=L)
+    o.set_state(np.full((n, n), h), np.full((n, n), h * u), np.full((n, n), h * v))
+    c = math.sqrt(9.81 * h)
+    return math.isclose(o.step(1)[0], 0.5 / ((abs(u) + c) / dx + (abs(v) + c) / dy), rel_tol=1e-14)
+
+
+def pin_cfl_muscl_faces(L):
+    """On a smooth, non-uniform flow the CFL speed uses the MUSCL face values:
+    compare with the 50-digit second implementation's lambda."""
+    rng = np.random.default_rng(5)
+    nx, ny = 6, 5
+    h = 1.0 + 0.3 * rng.random((ny, nx))
+    qx = h * rng.standard_normal((ny, nx))
+    qy = h * rng.standard_normal((ny, nx))
+    z = 0.1 * rng.standard_normal((ny, nx))
+    o = oracle.Oracle(nx, ny, 0.5, 0.5, z, library=L)
+    o.set_state(h, qx, qy)
+    m = MPScheme(nx, ny, 0.5, 0.5, z, h, qx, qy)
+    lx, ly = o.lam()
+    mlx, mly = m.lam()
+    return math.isclose(lx, float(mlx), rel_tol=1e-14) and math.isclose(ly, float(mly), rel_tol=1e-14)
+
+
+def pin_friction_uniform(L):
+    n, h0, q0, nm = 8, 0.8, 0.6, 0.12
+    o = oracle.Oracle(n, n, 1.0, 1.0, np.zeros((n, n)), bc=(1, 1, 1, 1), friction=1,
+                      manning_n=nm, dt_max=0.05, library=L)
+    o.set_state(np.full((n, n), h0), np.full((n, n), q0), np.zeros((n, n)))
+    dts = o.step(30)
+    q = q0
+    for dt in dts:
+        k = dt * 9.81 * nm * nm / h0 ** (7.0 / 3.0)
+        q1 = q / (1.0 + k * abs(q))
+        q = 0.5 * (q + q1 / (1.0 + k * abs(q1)))
+    return bool(np.allclose(o.state()[1], q, rtol=1e-14, atol=0))
+
+
+def pin_ponding_time(L):
+    n = 4
+    R, ks, psi, dth = 50.0 * si.RAIN_MM_PER_H, 1e-6, 0.1, 0.3
+    o = oracle.Oracle(n, n, 1.0, 1.0, np.zeros((n, n)), bc=(1, 1, 1, 1), dt_max=1.0,
+                      rain_rate=R, rain_t_off=600.0, infiltration=1, ks=ks, psi=psi,
+                      dtheta=dth, library=L)
+    o.set_state(np.zeros((n, n)), np.zeros((n, n)), np.zeros((n, n)))
+    t = 0.0
+    for _ in range(300):
+        t += o.step(1)[0]
+        if o.state()[0][0, 0] > 0:
+            break
+    tp = ks * psi * dth / (R * (R - ks))
+    return abs(t - tp) <= 2.0 and math.isclose(o.diag()["rain_in"], R * n * n * t, rel_tol=1e-12)
+
+
+BATTERY = [pin_mp_second_implementation, pin_lake_at_rest, pin_mass_and_positivity,
+           pin_stoker, pin_symmetry, pin_cfl_uniform, pin_cfl_muscl_faces,
+           pin_friction_uniform, pin_ponding_time]
+
+
+def _run_battery(L):
+    out = {}
+    for pin in BATTERY:
+        try:
+            out[pin.__name__] = bool(pin(L))
+        except Exception:   # a crash or a raised error counts as a failed pin
+            out[pin.__name__] = False
+    return out
+
+
+def test_unmodified_oracle_passes_battery(tmp_path):
+    L = _build_variant(tmp_path, "unmodified", "double oracle_minmod", "double oracle_minmod")
+    res = _run_battery(L)
+    assert all(res.values()), res
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(tmp_path, name):
+    old, new = MUTATIONS[name]
+    L = _build_variant(tmp_path, name, old, new)
+    res = _run_battery(L)
+    assert not all(res.values()), f"no pin caught mutation {name}: {res}"
