@@ -1,0 +1,364 @@
+#!/usr/bin/env python3
+"""Throughput of the FullSWOF_2D time step on the 4096 x 4096 valley flood.
+
+One "step" is one full Heun time step (Algorithm 1: wave-speed/dt kernel,
+stage 1, stage 2 with the Heun average and sources) over every interior cell
+of the grid, dry cells included; the metric is cell-updates per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Our arm times the CUDA path (libswof through its C ABI) with CUDA events on
+the stream the kernels run on; the state of the valley flood evolves over
+the warm-up and timed steps.  The headline is the FP32 bulk path; the FP64
+path (bit-identical to the oracle) is timed on the same workload and
+reported under "variants".  --impl reference times the CPU oracle (the
+plain FP64 C implementation, all host cores) on the same workload.
+With N > 1 (torchrun) every rank runs its own replica of the grid: the path
+is one grid per GPU, so N GPUs process N grids ("replicas only").
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import signal
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gcell-updates/s at 4096^2, % HBM roofline; FP32/batch/surrogate vs FP64 plain"
+UNIT = "Gcell-updates/s"
+FALLBACK_HBM_GBS = 6800.0
+
+# Algorithmic bytes per cell and launch (minimum DRAM traffic of each kernel:
+# every input read once, every output written once).
+BYTES = {
+    "fp32": {"lambda": 12, "stage1": 12 + 8 + 12, "stage2": 12 + 8 + 12 + 12},
+    "fp64": {"lambda": 24, "stage1": 24 + 8 + 24, "stage2": 24 + 8 + 24 + 24},
+}
+# Algorithmic bytes of a whole step with the wave speeds fused away: U^n and
+# z read and U* written in stage 1, U*, z, U^n read and U^{n+1} written in
+# stage 2 (17 words per cell).
+STEP_BYTES = {"fp32": 68, "fp64": 136}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def recorded_traffic(kernel: str, precision: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    src = os.path.join(ROOT, "paper_1307_4839_gb300", "csrc", "swof_kernels.cuh")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    f = os.path.join(ROOT, "profiles", f"{kernel}_{precision}_valley4096.txt")
+    if not os.path.exists(f):
+        return None
+    vals = {}
+    for line in open(f):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha256_16") != sha:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.send_signal(signal.SIGTERM)
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for k, name in enumerate(names):
+                    if f[5 + k].lower().startswith("active"):
+                        reasons.add(name)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload(n: int):
+    import swof_inputs as si
+    return si.valley(n)
+
+
+def workload_name(w) -> str:
+    return (f"valley flood {w.nx}x{w.ny}, dx=dy={w.dx} m, V-valley (side slope 0.15, long. slope 0.003) "
+            f"+ fractal noise (1.5 m, H=0.8, seed 1), {w.extra['reservoir']} m level pool behind row "
+            f"{w.extra['dam_row']}, Manning n={w.manning_n}, outflow N edge, walls elsewhere")
+
+
+def time_oracle(w, steps_cap: int, budget_s: float):
+    """Oracle on the full grid: steps until the time budget is used."""
+    import oracle
+    o = oracle.Oracle.from_workload(w)
+    t0 = time.perf_counter()
+    n = 0
+    while n < steps_cap:
+        o.step(1)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return n, dt, oracle.threads()
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    w = workload(args.n)
+    cells = w.nx * w.ny
+    import oracle as orc
+    o = orc.Oracle.from_workload(w)
+    for _ in range(args.warmup):
+        o.step(1)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    el = time.perf_counter() - t0
+    value = cells * args.steps / el * 1e-9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload_name(w), "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": orc.threads(), "kind": "oracle",
+                             "sample": f"{args.steps} full-grid steps after {args.warmup} warm-up steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def measure(sw, torch, w, precision: str, steps: int, warmup: int, ws: int, clocks: Clocks | None):
+    prec = sw.FP32 if precision == "fp32" else sw.FP64
+    # a dedicated (non-null) stream: the kernels and the timing events share it
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    s = sw.Solver.from_workload(w, prec, stream=stream.cuda_stream)
+    s.step(warmup)
+    torch.cuda.synchronize()
+    barrier(ws)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if clocks:
+        clocks.start()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s.step(steps, sync=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    barrier(ws)
+    ms = e0.elapsed_time(e1)
+    info = s.step(0)
+    assert info.status == 0, f"device status {info.status}"
+    # per-kernel device time, CUDA events around each launch on the same stream
+    s.enable_timing(True)
+    s.step(steps, sync=False)
+    t = s.timing()
+    s.enable_timing(False)
+    d = s.diagnostics()
+    return ms, t, clk, d, s
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    import torch
+
+    import paper_1307_4839_gb300 as sw
+    sw.build()
+    sw.load()
+    torch.cuda.set_device(local)
+    w = workload(args.n)
+    cells = w.nx * w.ny
+    hbm, peak_kind = peaks()
+
+    clocks = Clocks(local)
+    ms, t, clk, diag, solver = measure(sw, torch, w, "fp32", args.steps, args.warmup, ws, clocks)
+    ms_max = max_over_ranks(ms, ws)
+    ms_step = ms_max / args.steps
+    value = ws * cells / (ms_step * 1e-3) * 1e-9
+
+    k = args.steps
+    avg = {"lambda": t["lambda_ms"] / k, "stage1": t["stage1_ms"] / k, "stage2": t["stage2_ms"] / k}
+    dom = max(avg, key=avg.get)
+    achieved = BYTES["fp32"][dom] * cells / (avg[dom] * 1e-3) * 1e-9
+    roofline = {"bound": "hbm", "kernel": f"k_stage<float,{dom[-1]}>" if dom != "lambda" else "k_lambda<float>",
+                "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "peak_kind": f"{peak_kind} copy bandwidth (burst)",
+                "traffic": recorded_traffic(dom, "fp32"),
+                "algorithmic_bytes_per_cell": BYTES["fp32"][dom],
+                "kernel_ms": {kk: round(v, 5) for kk, v in avg.items()},
+                "step_frac_of_hbm": STEP_BYTES["fp32"] * cells / (ms_step * 1e-3) * 1e-9 / hbm}
+
+    variants = {}
+    if not args.no_fp64:
+        k64 = max(5, args.steps // 4)
+        ms64, t64, _, _, s64 = measure(sw, torch, w, "fp64", k64, args.warmup, ws, None)
+        ms64 = max_over_ranks(ms64, ws)
+        v64 = ws * cells / (ms64 / k64 * 1e-3) * 1e-9
+        avg64 = {"lambda": t64["lambda_ms"] / k64, "stage1": t64["stage1_ms"] / k64,
+                 "stage2": t64["stage2_ms"] / k64}
+        variants["fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": ms64 / k64, "steps": k64,
+                            "fp32_over_fp64": value / v64,
+                            "kernel_ms": {kk: round(v, 4) for kk, v in avg64.items()},
+                            "hbm_frac_algorithmic": STEP_BYTES["fp64"] * cells / (ms64 / k64 * 1e-3) * 1e-9 / hbm,
+                            "bound": "alu (FP64 pipe)"}
+        del s64
+
+    e2e = None
+    if not args.no_e2e:
+        S = args.e2e_steps
+        s = sw.Solver.from_workload(w, sw.FP32)
+        h, qx, qy = w.h, w.qx, w.qy
+        s.set_state(h, qx, qy)
+        s.step(2)
+        s.state()
+        barrier(ws)
+        t0 = time.perf_counter()
+        s.set_state(h, qx, qy)
+        s.step(S, sync=False)
+        out = s.state()
+        el = time.perf_counter() - t0
+        el = max_over_ranks(el, ws)
+        nbytes = 3 * cells * 4
+        e2e = {"value": ws * cells * S / el * 1e-9, "unit": UNIT,
+               "h2d_bytes_per_step": nbytes / S, "d2h_bytes_per_step": nbytes / S,
+               "steps_per_call": S,
+               "what": "swof_set_state(host float64) + swof_step(S) + swof_get_state(host float64)"}
+        del s, out
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        n, el, cores = time_oracle(w, 8, 12.0)
+        cpu = {"value": cells * n / el * 1e-9, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{n} full-grid FP64 steps of the same valley from its initial state"}
+
+    launches = 3 * args.steps
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_name(w), "grid": [w.nx, w.ny], "precision": "fp32 bulk, fp64 dt/time/budgets",
+                   "l2": f"inputs larger than L2 (working set {(9 * (w.ny + 4) * (w.nx + 8) * 4) / 1e6:.0f} MB)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "counted": "all interior cells, dry cells included"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "variants": variants,
+        "final_state": {"t": diag["t"], "volume": diag["volume"], "min_h": diag["min_h"]},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

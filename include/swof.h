@@ -1,0 +1,189 @@
+/*
+ * swof.h -- C ABI of libswof, a GB300 (sm_103a) implementation of the time
+ * step of FullSWOF_2D's well-balanced finite-volume shallow-water solver
+ * (arXiv 1307.4839, "FullSWOF_Paral", Sec. 2-3 and Algorithm 1).
+ *
+ * The problem (Sec. 2.1, Eq. (SW2D)): unknowns h [m], qx = hu, qy = hv
+ * [m^2/s] on an nx x ny Cartesian grid of cells dx x dy, fixed topography z,
+ * rain R(t), Green-Ampt infiltration I (Sec. 3.5), Manning friction
+ * (Sec. 2.1), ghost-cell boundary conditions (Sec. 2.2).  One step
+ * (Algorithm 1) is two Heun stages (Sec. 3.2), each: boundary conditions ->
+ * MUSCL-minmod reconstruction (Sec. 3.4) -> hydrostatic reconstruction ->
+ * HLL flux (Sec. 3.3) -> scheme Eq. (SW1Dscheme) in x and y -> semi-implicit
+ * friction (Sec. 3.2); then the Heun average, rain and infiltration, with dt
+ * from the CFL condition Eq. (cfl) on the MUSCL face values.
+ *
+ * Conventions (all entry points):
+ *   - Return SWOF_OK (0) or a negative SWOF_E* code; nothing throws or exits.
+ *   - Host arrays are row-major [ny][nx] float64, x fastest; they are copied,
+ *     the caller keeps ownership.  Output arrays are caller-allocated.
+ *   - A context owns all of its device memory; it is bound to the CUDA
+ *     device current at swof_create and to one stream (params.stream, or an
+ *     internal stream when NULL).  A context is not thread-safe.
+ *   - Work is enqueued asynchronously; swof_get_* synchronise the stream.
+ *   - Errors raised on the device (non-finite state, exhausted dt
+ *     sequence, CFL violation in fixed-dt mode) are latched in the context:
+ *     later steps become no-ops and the code is returned by the next call
+ *     that synchronises (swof_step with info != NULL, swof_get_*).
+ */
+#ifndef SWOF_H
+#define SWOF_H
+
+#if defined(__GNUC__)
+#define SWOF_API __attribute__((visibility("default")))
+#else
+#define SWOF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define SWOF_OK            0
+#define SWOF_EINVAL       -1   /* bad argument (NULL, size, enum, layout) */
+#define SWOF_ENOMEM       -2   /* device allocation failed */
+#define SWOF_ECUDA        -3   /* a CUDA runtime call failed */
+#define SWOF_ENONFINITE   -4   /* NaN/Inf in the state or in the wave speeds */
+#define SWOF_ENEGATIVE    -5   /* negative water depth in a state passed in */
+#define SWOF_ECFL         -6   /* fixed dt larger than the CFL bound Eq. (cfl) */
+#define SWOF_EDTSEQ       -7   /* replayed dt sequence exhausted */
+#define SWOF_ETIMEOUT     -8   /* a bounded device wait ran out */
+#define SWOF_EDTUNDERFLOW -9   /* CFL dt below params.dt_min */
+#define SWOF_ESTATE      -10   /* call not valid in the context's state */
+
+/* ---- enums ---- */
+#define SWOF_FP64 0            /* all arithmetic in FP64 (parity path) */
+#define SWOF_FP32 1            /* bulk FP32 stencil; FP64 dt, time, budgets */
+#define SWOF_CFL_SUM 0         /* dt = n_CFL / (lx/dx + ly/dy) */
+#define SWOF_CFL_MIN 1         /* dt = n_CFL * min(dx/lx, dy/ly) */
+#define SWOF_BC_WALL 0         /* mirror ghosts, normal discharge negated */
+#define SWOF_BC_OUTFLOW 1      /* free outflow: edge cell extended */
+#define SWOF_FRIC_NONE 0
+#define SWOF_FRIC_MANNING 1    /* S_f = n^2 |u| u / h^{4/3}, Sec. 2.1 */
+
+typedef struct swof_ctx swof_ctx;
+
+typedef struct swof_params {
+    double g;              /* gravity, 9.81 (Sec. 2.1) */
+    double cfl;            /* n_CFL, 0.5 at second order (Sec. 3.3) */
+    double h_dry;          /* dry threshold [m]: u = v = 0 and q := 0 below */
+    double dt_max;         /* dt cap; dt when every wave speed is zero */
+    double dt_min;         /* CFL dt below this -> SWOF_EDTUNDERFLOW (0: off) */
+    double t_end;          /* the last step is clamped to end here */
+    int precision;         /* SWOF_FP64 | SWOF_FP32 */
+    int cfl_mode;          /* SWOF_CFL_SUM | SWOF_CFL_MIN */
+    int bc[4];             /* W, E, S, N edges: SWOF_BC_WALL | SWOF_BC_OUTFLOW */
+    int friction;          /* SWOF_FRIC_NONE | SWOF_FRIC_MANNING */
+    double manning_n;      /* Manning n [s m^-1/3] when friction_map is NULL */
+    const double *friction_map;  /* per-cell n [ny][nx], host, copied; nullable */
+    double rain_rate;      /* uniform rain R [m/s] (Eq. (SW2D)) */
+    double rain_t_on, rain_t_off;  /* rain falls for t in [on, off) */
+    int infiltration;      /* 1: Green-Ampt (Sec. 3.5) */
+    double ks;             /* K_s [m/s] when ks_map is NULL */
+    const double *ks_map;  /* per-cell K_s [ny][nx], host, copied; nullable */
+    double psi;            /* wetting-front suction head h_f [m], > 0 */
+    double dtheta;         /* theta_s - theta_i */
+    int check_cfl;         /* 1: count steps whose dt breaks Eq. (cfl) at U* */
+    double dt_fixed;       /* > 0: fixed dt (Eq. (cfl) violation -> SWOF_ECFL) */
+    void *stream;          /* cudaStream_t to enqueue on; NULL: an internal
+                              non-blocking stream (the legacy default stream
+                              is handle 0, so it cannot be selected here) */
+} swof_params;
+
+typedef struct swof_step_info {
+    double t;              /* simulated time after the call */
+    double dt;             /* last dt */
+    long long steps;       /* steps taken since creation */
+    int status;            /* latched device status (SWOF_OK or SWOF_E*) */
+} swof_step_info;
+
+typedef struct swof_diag {
+    double t, last_dt;
+    long long steps;
+    double volume;         /* sum h dx dy, deterministic fixed-order tree */
+    double rain_in;        /* rain volume added [m^3] */
+    double infiltrated;    /* volume infiltrated [m^3] */
+    double outflow;        /* net volume out through the edges [m^3] */
+    double min_h;          /* smallest interior depth */
+    long long cfl_viol;    /* steps with dt above the CFL bound at U* */
+} swof_diag;
+
+/* Fill *p with the defaults: g 9.81, cfl 0.5, h_dry 1e-6, dt_max 0.1,
+ * dt_min 0, t_end 1e30, FP64, CFL_SUM, walls, no friction/rain/infiltration. */
+SWOF_API void swof_default_params(swof_params *p);
+
+/* Create a solver for an nx x ny grid (nx, ny >= 2) of cells dx x dy with
+ * topography z [ny][nx] (host, copied; ghost z by the boundary rule).
+ * Allocates every device buffer (padded SoA, 2 ghost layers); the state
+ * starts dry (h = q = 0) at t = 0.  Sec. 2.1 / Sec. 6.1 (2 ghost layers at
+ * second order).  Errors: SWOF_EINVAL, SWOF_ENOMEM, SWOF_ECUDA. */
+SWOF_API int swof_create(int nx, int ny, double dx, double dy, const double *z,
+                const swof_params *p, swof_ctx **out);
+
+/* Destroy a context and free its device memory; NULL-safe.  Synchronises. */
+SWOF_API void swof_destroy(swof_ctx *ctx);
+
+/* Set the conservative state (h, hu, hv), host [ny][nx] float64, copied and
+ * converted to the context precision; ghosts are refilled.  Rejects NaN/Inf
+ * (SWOF_ENONFINITE) and h < 0 (SWOF_ENEGATIVE) before touching the state. */
+SWOF_API int swof_set_state(swof_ctx *ctx, const double *h, const double *hu, const double *hv);
+
+/* Copy the state to host arrays [ny][nx] float64 (FP32 values widened).
+ * Synchronises; returns a latched device status if one is set. */
+SWOF_API int swof_get_state(swof_ctx *ctx, double *h, double *hu, double *hv);
+
+/* Same with device pointers of dense [ny][nx] arrays of the given dtype
+ * (SWOF_FP64: double, SWOF_FP32: float), e.g. torch tensors' data_ptr();
+ * enqueued on the context stream.  Values are converted when the dtype
+ * differs from the context precision.  No validation of the values. */
+SWOF_API int swof_set_state_device(swof_ctx *ctx, const void *h, const void *hu, const void *hv, int dtype);
+SWOF_API int swof_get_state_device(swof_ctx *ctx, void *h, void *hu, void *hv, int dtype);
+
+/* Infiltrated depth V_inf (Sec. 3.5), host [ny][nx] float64. */
+SWOF_API int swof_get_infiltrated(swof_ctx *ctx, double *vinf);
+SWOF_API int swof_set_infiltrated(swof_ctx *ctx, const double *vinf);
+
+/* Simulated time (FP64); resets nothing else. */
+SWOF_API int swof_set_time(swof_ctx *ctx, double t);
+
+/* Advance n full Heun steps (Algorithm 1), each with one dt from Eq. (cfl)
+ * (or the replayed sequence, or dt_fixed).  Asynchronous when info is NULL;
+ * with info non-NULL the call synchronises and reports t, dt, steps and the
+ * latched status (also the return value). n = 0 is allowed. */
+SWOF_API int swof_step(swof_ctx *ctx, int n, swof_step_info *info);
+
+/* Replay the given dt values (host, copied) for the next n steps instead of
+ * Eq. (cfl), e.g. the oracle's sequence for parity.  n = 0 switches replay
+ * off.  Running past the end latches SWOF_EDTSEQ. */
+SWOF_API int swof_set_dt_sequence(swof_ctx *ctx, const double *dts, int n);
+
+/* dt of each step taken so far (up to max values, oldest first) into host
+ * out; *count gets how many were written.  Synchronises. */
+SWOF_API int swof_get_dt_history(swof_ctx *ctx, double *out, int max, int *count);
+
+/* Diagnostics (volume by a deterministic reduction, budgets, min h).
+ * Synchronises. */
+SWOF_API int swof_get_diagnostics(swof_ctx *ctx, swof_diag *d);
+
+/* Device time of the last swof_step call's kernels, split per kernel
+ * family (wave-speed/dt, stage 1, stage 2) in milliseconds, when timing was
+ * switched on with swof_enable_timing(ctx, 1).  Synchronises. */
+SWOF_API int swof_enable_timing(swof_ctx *ctx, int on);
+SWOF_API int swof_get_timing(swof_ctx *ctx, double *ms_lambda, double *ms_stage1, double *ms_stage2, int *launches);
+
+/* Capture the next n-step sequence into a CUDA graph and replay it on later
+ * swof_step calls with the same n (0 switches graphs off). Launch-bound
+ * small grids gain the most. */
+SWOF_API int swof_use_graph(swof_ctx *ctx, int on);
+
+/* Human-readable text for a status code (static storage). */
+SWOF_API const char *swof_strerror(int code);
+
+/* Library build information (static storage). */
+SWOF_API const char *swof_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SWOF_H */

@@ -1,0 +1,280 @@
+"""Python binding of libswof (include/swof.h): argument marshalling only.
+
+Every step of the shallow-water time step runs in the CUDA kernels of
+libswof.so; this module loads that library through ctypes, mirrors its
+structs, exposes the C entry points under the same names, and wraps them in
+a small `Solver` class.  There is no CPU fallback: if the library is not
+built (see `build()`), or no CUDA device is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from .build import LIB as _LIB_PATH
+from .build import build
+
+__all__ = ["build", "load", "Solver", "SwofError", "SwofParams", "SwofDiag", "SwofStepInfo",
+           "FP64", "FP32", "BC_WALL", "BC_OUTFLOW", "FRIC_NONE", "FRIC_MANNING"]
+
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ENEGATIVE, ECFL, EDTSEQ, ETIMEOUT, EDTUNDERFLOW, ESTATE = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8, -9, -10)
+FP64, FP32 = 0, 1
+CFL_SUM, CFL_MIN = 0, 1
+BC_WALL, BC_OUTFLOW = 0, 1
+FRIC_NONE, FRIC_MANNING = 0, 1
+
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+class SwofParams(ctypes.Structure):
+    _fields_ = [("g", ctypes.c_double), ("cfl", ctypes.c_double), ("h_dry", ctypes.c_double),
+                ("dt_max", ctypes.c_double), ("dt_min", ctypes.c_double), ("t_end", ctypes.c_double),
+                ("precision", ctypes.c_int), ("cfl_mode", ctypes.c_int), ("bc", ctypes.c_int * 4),
+                ("friction", ctypes.c_int), ("manning_n", ctypes.c_double),
+                ("friction_map", _D), ("rain_rate", ctypes.c_double),
+                ("rain_t_on", ctypes.c_double), ("rain_t_off", ctypes.c_double),
+                ("infiltration", ctypes.c_int), ("ks", ctypes.c_double), ("ks_map", _D),
+                ("psi", ctypes.c_double), ("dtheta", ctypes.c_double), ("check_cfl", ctypes.c_int),
+                ("dt_fixed", ctypes.c_double), ("stream", ctypes.c_void_p)]
+
+
+class SwofStepInfo(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("dt", ctypes.c_double), ("steps", ctypes.c_longlong),
+                ("status", ctypes.c_int)]
+
+
+class SwofDiag(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("last_dt", ctypes.c_double), ("steps", ctypes.c_longlong),
+                ("volume", ctypes.c_double), ("rain_in", ctypes.c_double),
+                ("infiltrated", ctypes.c_double), ("outflow", ctypes.c_double),
+                ("min_h", ctypes.c_double), ("cfl_viol", ctypes.c_longlong)]
+
+
+class SwofError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        msg = _lib.swof_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{what}: {msg} ({code})" if what else f"{msg} ({code})")
+
+
+_lib = None
+_lock = threading.Lock()
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "swof_default_params": (None, [ctypes.POINTER(SwofParams)]),
+    "swof_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _D,
+                                   ctypes.POINTER(SwofParams), ctypes.POINTER(ctypes.c_void_p)]),
+    "swof_destroy": (None, [ctypes.c_void_p]),
+    "swof_set_state": (ctypes.c_int, [ctypes.c_void_p, _D, _D, _D]),
+    "swof_get_state": (ctypes.c_int, [ctypes.c_void_p, _D, _D, _D]),
+    "swof_set_state_device": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 3 + [ctypes.c_int]),
+    "swof_get_state_device": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 3 + [ctypes.c_int]),
+    "swof_get_infiltrated": (ctypes.c_int, [ctypes.c_void_p, _D]),
+    "swof_set_infiltrated": (ctypes.c_int, [ctypes.c_void_p, _D]),
+    "swof_set_time": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    "swof_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(SwofStepInfo)]),
+    "swof_set_dt_sequence": (ctypes.c_int, [ctypes.c_void_p, _D, ctypes.c_int]),
+    "swof_get_dt_history": (ctypes.c_int, [ctypes.c_void_p, _D, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "swof_get_diagnostics": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(SwofDiag)]),
+    "swof_enable_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "swof_get_timing": (ctypes.c_int, [ctypes.c_void_p, _D, _D, _D, ctypes.POINTER(ctypes.c_int)]),
+    "swof_use_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "swof_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "swof_version": (ctypes.c_char_p, []),
+}
+
+
+def declared_symbols() -> list[str]:
+    return sorted(_SIGS)
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load(path: str | None = None):
+    """Load libswof.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or _LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(f"libswof is not built ({p} missing); call "
+                                   "paper_1307_4839_gb300.build() first -- there is no CPU fallback")
+            L = ctypes.CDLL(p)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _check(code: int, what: str):
+    if code != OK:
+        raise SwofError(code, what)
+
+
+def default_params(**kw) -> SwofParams:
+    p = SwofParams()
+    load().swof_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "bc":
+            for i in range(4):
+                p.bc[i] = int(v[i])
+        else:
+            setattr(p, k, v)
+    return p
+
+
+class Solver:
+    """One libswof context.  Arrays are numpy float64 [ny][nx] on the host,
+    or torch CUDA tensors for the *_device methods."""
+
+    def __init__(self, nx, ny, dx, dy, z, *, precision=FP64, g=9.81, cfl=0.5, h_dry=1e-6,
+                 dt_max=0.1, dt_min=0.0, t_end=1e30, cfl_mode=CFL_SUM, bc=(0, 0, 0, 0),
+                 friction=FRIC_NONE, manning_n=0.0, friction_map=None, rain_rate=0.0,
+                 rain_t_on=0.0, rain_t_off=0.0, infiltration=0, ks=0.0, ks_map=None, psi=0.0,
+                 dtheta=0.0, check_cfl=0, dt_fixed=0.0, stream=None):
+        L = load()
+        self.nx, self.ny, self.precision = int(nx), int(ny), int(precision)
+        self._ctx = None
+        keep = []
+        fm = km = None
+        if friction_map is not None:
+            fm = _f64(friction_map)
+            keep.append(fm)
+        if ks_map is not None:
+            km = _f64(ks_map)
+            keep.append(km)
+        p = default_params(g=g, cfl=cfl, h_dry=h_dry, dt_max=dt_max, dt_min=dt_min, t_end=t_end,
+                           precision=int(precision), cfl_mode=int(cfl_mode), bc=bc,
+                           friction=int(friction), manning_n=float(manning_n),
+                           rain_rate=float(rain_rate), rain_t_on=float(rain_t_on),
+                           rain_t_off=float(rain_t_off), infiltration=int(infiltration),
+                           ks=float(ks), psi=float(psi), dtheta=float(dtheta),
+                           check_cfl=int(check_cfl), dt_fixed=float(dt_fixed))
+        p.friction_map = _ptr(fm) if fm is not None else None
+        p.ks_map = _ptr(km) if km is not None else None
+        p.stream = stream
+        z = _f64(z)
+        if z.shape != (self.ny, self.nx):
+            raise ValueError("z must have shape (ny, nx)")
+        ctx = ctypes.c_void_p()
+        _check(L.swof_create(self.nx, self.ny, float(dx), float(dy), _ptr(z), ctypes.byref(p),
+                             ctypes.byref(ctx)), "swof_create")
+        self._ctx = ctx
+
+    @classmethod
+    def from_workload(cls, w, precision=FP64, **over):
+        kw = dict(cfl=w.cfl, h_dry=w.h_dry, dt_max=w.dt_max, t_end=w.t_end, bc=w.bc,
+                  friction=w.friction, manning_n=w.manning_n, rain_rate=w.rain_rate,
+                  rain_t_on=w.rain_t_on, rain_t_off=w.rain_t_off, infiltration=w.infiltration,
+                  ks_map=w.ks, psi=w.psi, dtheta=w.dtheta)
+        kw.update(over)
+        s = cls(w.nx, w.ny, w.dx, w.dy, w.z, precision=precision, **kw)
+        s.set_state(w.h, w.qx, w.qy)
+        return s
+
+    def close(self):
+        if self._ctx:
+            load().swof_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_state(self, h, qx, qy):
+        h, qx, qy = _f64(h), _f64(qx), _f64(qy)
+        _check(load().swof_set_state(self._ctx, _ptr(h), _ptr(qx), _ptr(qy)), "swof_set_state")
+
+    def state(self):
+        h = np.empty((self.ny, self.nx))
+        qx = np.empty_like(h)
+        qy = np.empty_like(h)
+        _check(load().swof_get_state(self._ctx, _ptr(h), _ptr(qx), _ptr(qy)), "swof_get_state")
+        return h, qx, qy
+
+    def set_state_device(self, h, qx, qy):
+        """torch CUDA tensors (float64 or float32), contiguous [ny][nx]."""
+        dt = FP64 if str(h.dtype) == "torch.float64" else FP32
+        _check(load().swof_set_state_device(self._ctx, h.data_ptr(), qx.data_ptr(), qy.data_ptr(), dt),
+               "swof_set_state_device")
+
+    def get_state_device(self, h, qx, qy):
+        dt = FP64 if str(h.dtype) == "torch.float64" else FP32
+        _check(load().swof_get_state_device(self._ctx, h.data_ptr(), qx.data_ptr(), qy.data_ptr(), dt),
+               "swof_get_state_device")
+
+    def infiltrated(self):
+        v = np.empty((self.ny, self.nx))
+        _check(load().swof_get_infiltrated(self._ctx, _ptr(v)), "swof_get_infiltrated")
+        return v
+
+    def set_infiltrated(self, v):
+        v = _f64(v)
+        _check(load().swof_set_infiltrated(self._ctx, _ptr(v)), "swof_set_infiltrated")
+
+    def set_time(self, t):
+        _check(load().swof_set_time(self._ctx, float(t)), "swof_set_time")
+
+    def step(self, n: int = 1, sync: bool = True) -> SwofStepInfo | None:
+        if not sync:
+            _check(load().swof_step(self._ctx, int(n), None), "swof_step")
+            return None
+        info = SwofStepInfo()
+        _check(load().swof_step(self._ctx, int(n), ctypes.byref(info)), "swof_step")
+        return info
+
+    def set_dt_sequence(self, dts):
+        d = _f64(dts).ravel()
+        _check(load().swof_set_dt_sequence(self._ctx, _ptr(d) if d.size else None, int(d.size)),
+               "swof_set_dt_sequence")
+
+    def dt_history(self, max_n: int | None = None) -> np.ndarray:
+        n = max_n if max_n is not None else int(self.diagnostics()["steps"])
+        out = np.zeros(max(n, 1))
+        cnt = ctypes.c_int()
+        _check(load().swof_get_dt_history(self._ctx, _ptr(out), int(n), ctypes.byref(cnt)),
+               "swof_get_dt_history")
+        return out[:cnt.value]
+
+    def diagnostics(self) -> dict:
+        d = SwofDiag()
+        _check(load().swof_get_diagnostics(self._ctx, ctypes.byref(d)), "swof_get_diagnostics")
+        return {k: getattr(d, k) for k, _ in SwofDiag._fields_}
+
+    def enable_timing(self, on=True):
+        _check(load().swof_enable_timing(self._ctx, int(bool(on))), "swof_enable_timing")
+
+    def timing(self):
+        a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        n = ctypes.c_int()
+        _check(load().swof_get_timing(self._ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                      ctypes.byref(n)), "swof_get_timing")
+        return {"lambda_ms": a.value, "stage1_ms": b.value, "stage2_ms": c.value, "launches": n.value}
+
+    def use_graph(self, on=True):
+        _check(load().swof_use_graph(self._ctx, int(bool(on))), "swof_use_graph")

@@ -1,0 +1,643 @@
+// swof_api.cu -- host side of libswof: contexts, device memory, the C ABI
+// declared in include/swof.h.  Arithmetic of the scheme lives in the
+// kernels (swof_kernels.cuh); this file only lays out memory, converts
+// host arrays and enqueues launches.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "swof_internal.h"
+
+using swof::DevCtl;
+using swof::Fields;
+using swof::Params;
+
+struct swof_ctx {
+    int device = 0;
+    int prec = SWOF_FP64;
+    size_t esize = 8;
+    Params P{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    const swof::Launch *L = nullptr;
+    Fields<double> f64{};
+    Fields<float> f32{};
+    std::vector<void *> allocs;
+    DevCtl *ctl = nullptr;
+    double *d_red = nullptr;
+    int nslots = 0;
+    double *dt_seq = nullptr;
+    int dt_seq_n = 0;
+    double *dt_hist = nullptr;
+    long long dt_cap = 0;
+    long long host_steps = 0;      // steps enqueued so far
+    // CUDA graph of an n-step sequence
+    bool use_graph = false;
+    cudaGraphExec_t gexec = nullptr;
+    int graph_n = 0;
+    unsigned gen = 1, graph_gen = 0;
+    // per-kernel timing of the last swof_step call
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;
+    int ev_used = 0;
+    int launches_last = 0;
+
+    void *fields() { return prec == SWOF_FP64 ? (void *)&f64 : (void *)&f32; }
+};
+
+namespace {
+
+int cuda_err(cudaError_t e) { return e == cudaSuccess ? SWOF_OK : SWOF_ECUDA; }
+
+template <typename T>
+T *dalloc(swof_ctx *c, size_t n, int *st)
+{
+    void *p = nullptr;
+    if (*st) return nullptr;
+    if (cudaMalloc(&p, n * sizeof(T) > 0 ? n * sizeof(T) : 16) != cudaSuccess) {
+        *st = SWOF_ENOMEM;
+        return nullptr;
+    }
+    c->allocs.push_back(p);
+    if (cudaMemsetAsync(p, 0, n * sizeof(T), c->stream) != cudaSuccess) *st = SWOF_ECUDA;
+    return static_cast<T *>(p);
+}
+
+size_t padded_elems(const swof_ctx *c) { return (size_t)(c->P.ny + 4) * (size_t)c->P.pitch; }
+
+// Host padded copy (double) of an interior [ny][nx] array, ghosts by the
+// boundary rule (scalar fields: mirror at walls, extension at outflow).
+std::vector<double> host_padded(const swof_ctx *c, const double *a)
+{
+    const Params &P = c->P;
+    std::vector<double> out(padded_elems(c), 0.0);
+    auto at = [&](int i, int j) -> double & {
+        return out[(size_t)(j + 2) * P.pitch + (size_t)(i + P.lpad)];
+    };
+    for (int j = 0; j < P.ny; ++j)
+        for (int i = 0; i < P.nx; ++i) at(i, j) = a[(size_t)j * P.nx + i];
+    for (int j = 0; j < P.ny; ++j)
+        for (int k = 0; k < 2; ++k) {
+            at(-1 - k, j) = (P.bc[0] == SWOF_BC_WALL) ? at(k, j) : at(0, j);
+            at(P.nx + k, j) = (P.bc[1] == SWOF_BC_WALL) ? at(P.nx - 1 - k, j) : at(P.nx - 1, j);
+        }
+    for (int i = 0; i < P.nx; ++i)
+        for (int k = 0; k < 2; ++k) {
+            at(i, -1 - k) = (P.bc[2] == SWOF_BC_WALL) ? at(i, k) : at(i, 0);
+            at(i, P.ny + k) = (P.bc[3] == SWOF_BC_WALL) ? at(i, P.ny - 1 - k) : at(i, P.ny - 1);
+        }
+    return out;
+}
+
+template <typename T>
+int upload_padded(swof_ctx *c, T *dst, const std::vector<double> &src)
+{
+    std::vector<T> tmp(src.size());
+    for (size_t k = 0; k < src.size(); ++k) tmp[k] = (T)src[k];
+    cudaError_t e = cudaMemcpyAsync(dst, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return cuda_err(e);
+}
+
+// Interior [ny][nx] host doubles -> padded device array of T (no ghosts).
+template <typename T>
+int upload_interior(swof_ctx *c, T *dst, const double *src)
+{
+    const Params &P = c->P;
+    std::vector<T> tmp((size_t)P.nx * P.ny);
+    for (size_t k = 0; k < tmp.size(); ++k) tmp[k] = (T)src[k];
+    cudaError_t e = cudaMemcpy2DAsync(dst + 2 * (size_t)P.pitch + P.lpad, (size_t)P.pitch * sizeof(T),
+                                      tmp.data(), (size_t)P.nx * sizeof(T), (size_t)P.nx * sizeof(T),
+                                      (size_t)P.ny, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return cuda_err(e);
+}
+
+template <typename T>
+int download_interior(swof_ctx *c, const T *src, double *dst)
+{
+    const Params &P = c->P;
+    std::vector<T> tmp((size_t)P.nx * P.ny);
+    cudaError_t e = cudaMemcpy2DAsync(tmp.data(), (size_t)P.nx * sizeof(T),
+                                      src + 2 * (size_t)P.pitch + P.lpad, (size_t)P.pitch * sizeof(T),
+                                      (size_t)P.nx * sizeof(T), (size_t)P.ny, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return SWOF_ECUDA;
+    for (size_t k = 0; k < tmp.size(); ++k) dst[k] = (double)tmp[k];
+    return SWOF_OK;
+}
+
+int read_ctl(swof_ctx *c, DevCtl *h)
+{
+    cudaError_t e = cudaMemcpyAsync(h, c->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return cuda_err(e);
+}
+
+template <typename T>
+int alloc_fields(swof_ctx *c, Fields<T> &F, const double *z, const swof_params *p)
+{
+    int st = SWOF_OK;
+    size_t n = padded_elems(c);
+    F.h = dalloc<T>(c, n, &st);
+    F.qx = dalloc<T>(c, n, &st);
+    F.qy = dalloc<T>(c, n, &st);
+    F.h1 = dalloc<T>(c, n, &st);
+    F.qx1 = dalloc<T>(c, n, &st);
+    F.qy1 = dalloc<T>(c, n, &st);
+    F.vinf = dalloc<T>(c, n, &st);
+    c->nslots = c->L->slots(c->P);
+    F.outflow_slots = dalloc<double>(c, (size_t)c->nslots, &st);
+    F.infil_slots = dalloc<double>(c, (size_t)c->nslots, &st);
+    if (st) return st;
+    std::vector<double> zp = host_padded(c, z);
+    const Params &P = c->P;
+    if (c->prec == SWOF_FP64) {
+        F.z = dalloc<T>(c, n, &st);
+        if (st) return st;
+        st = upload_padded<T>(c, F.z, zp);
+    } else {
+        // per-face differences, computed in FP64 then rounded
+        std::vector<double> dzx(n, 0.0), dzy(n, 0.0);
+        auto id = [&](int i, int j) { return (size_t)(j + 2) * P.pitch + (size_t)(i + P.lpad); };
+        for (int j = 0; j < P.ny; ++j)
+            for (int i = -2; i <= P.nx; ++i) dzx[id(i, j)] = zp[id(i + 1, j)] - zp[id(i, j)];
+        for (int j = -2; j <= P.ny; ++j)
+            for (int i = 0; i < P.nx; ++i) dzy[id(i, j)] = zp[id(i, j + 1)] - zp[id(i, j)];
+        F.dzx = dalloc<T>(c, n, &st);
+        F.dzy = dalloc<T>(c, n, &st);
+        if (st) return st;
+        st = upload_padded<T>(c, F.dzx, dzx);
+        if (!st) st = upload_padded<T>(c, F.dzy, dzy);
+    }
+    if (st) return st;
+    if (p->friction_map) {
+        std::vector<double> n2((size_t)P.nx * P.ny);
+        for (size_t k = 0; k < n2.size(); ++k) n2[k] = p->friction_map[k] * p->friction_map[k];
+        F.n2map = dalloc<T>(c, n, &st);
+        if (!st) st = upload_interior<T>(c, F.n2map, n2.data());
+    }
+    if (!st && p->ks_map) {
+        F.ksmap = dalloc<T>(c, n, &st);
+        if (!st) st = upload_interior<T>(c, F.ksmap, p->ks_map);
+    }
+    F.ctl = c->ctl;
+    F.dt_seq = nullptr;
+    F.dt_hist = nullptr;
+    F.dt_hist_cap = 0;
+    return st;
+}
+
+void set_hist(swof_ctx *c)
+{
+    c->f64.dt_hist = c->dt_hist;
+    c->f32.dt_hist = c->dt_hist;
+    c->f64.dt_hist_cap = c->dt_cap;
+    c->f32.dt_hist_cap = c->dt_cap;
+    c->f64.dt_seq = c->dt_seq_n > 0 ? c->dt_seq : nullptr;
+    c->f32.dt_seq = c->dt_seq_n > 0 ? c->dt_seq : nullptr;
+    c->gen++;
+}
+
+// Make room in the dt history for `more` further steps.
+int ensure_hist(swof_ctx *c, long long more)
+{
+    long long need = c->host_steps + more;
+    if (need <= c->dt_cap) return SWOF_OK;
+    long long cap = c->dt_cap ? c->dt_cap : 1024;
+    while (cap < need) cap *= 2;
+    double *p = nullptr;
+    if (cudaMalloc(&p, (size_t)cap * sizeof(double)) != cudaSuccess) return SWOF_ENOMEM;
+    cudaError_t e = cudaSuccess;
+    if (c->dt_hist) {
+        e = cudaMemcpyAsync(p, c->dt_hist, (size_t)c->dt_cap * sizeof(double), cudaMemcpyDeviceToDevice,
+                            c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        cudaFree(c->dt_hist);
+    }
+    c->dt_hist = p;
+    c->dt_cap = cap;
+    set_hist(c);
+    return cuda_err(e);
+}
+
+int enqueue_steps(swof_ctx *c, int n)
+{
+    void *f = c->fields();
+    int r = 0;
+    c->launches_last = 0;
+    for (int s = 0; s < n && !r; ++s) {
+        if (c->timing) {
+            while ((int)c->ev.size() < c->ev_used + 4) {
+                cudaEvent_t e;
+                if (cudaEventCreate(&e) != cudaSuccess) return SWOF_ECUDA;
+                c->ev.push_back(e);
+            }
+            cudaEventRecord(c->ev[c->ev_used + 0], c->stream);
+            r = c->L->lambda(c->P, f, c->stream);
+            cudaEventRecord(c->ev[c->ev_used + 1], c->stream);
+            if (!r) r = c->L->stage1(c->P, f, c->stream);
+            cudaEventRecord(c->ev[c->ev_used + 2], c->stream);
+            if (!r) r = c->L->stage2(c->P, f, c->stream);
+            cudaEventRecord(c->ev[c->ev_used + 3], c->stream);
+            c->ev_used += 4;
+        } else {
+            r = c->L->lambda(c->P, f, c->stream);
+            if (!r) r = c->L->stage1(c->P, f, c->stream);
+            if (!r) r = c->L->stage2(c->P, f, c->stream);
+        }
+        c->launches_last += 3;
+    }
+    return r ? SWOF_ECUDA : SWOF_OK;
+}
+
+bool all_finite(const double *a, size_t n)
+{
+    for (size_t k = 0; k < n; ++k)
+        if (!std::isfinite(a[k])) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+void swof_default_params(swof_params *p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->g = 9.81;
+    p->cfl = 0.5;
+    p->h_dry = 1e-6;
+    p->dt_max = 0.1;
+    p->dt_min = 0.0;
+    p->t_end = 1e30;
+    p->precision = SWOF_FP64;
+    p->cfl_mode = SWOF_CFL_SUM;
+    p->friction = SWOF_FRIC_NONE;
+}
+
+int swof_create(int nx, int ny, double dx, double dy, const double *z, const swof_params *p, swof_ctx **out)
+{
+    if (!out) return SWOF_EINVAL;
+    *out = nullptr;
+    if (!z || !p || nx < 2 || ny < 2 || !(dx > 0) || !(dy > 0) || !std::isfinite(dx) || !std::isfinite(dy))
+        return SWOF_EINVAL;
+    if ((long long)nx * (long long)ny > (1LL << 33) || nx > (1 << 28) || ny > (1 << 25)) return SWOF_EINVAL;
+    if (p->precision != SWOF_FP64 && p->precision != SWOF_FP32) return SWOF_EINVAL;
+    if (p->cfl_mode != SWOF_CFL_SUM && p->cfl_mode != SWOF_CFL_MIN) return SWOF_EINVAL;
+    if (p->friction != SWOF_FRIC_NONE && p->friction != SWOF_FRIC_MANNING) return SWOF_EINVAL;
+    for (int k = 0; k < 4; ++k)
+        if (p->bc[k] != SWOF_BC_WALL && p->bc[k] != SWOF_BC_OUTFLOW) return SWOF_EINVAL;
+    if (!(p->g > 0) || !(p->cfl > 0) || !(p->h_dry >= 0) || !(p->dt_max > 0) || !(p->dt_min >= 0)) return SWOF_EINVAL;
+    if (p->infiltration && !(p->dtheta > 0)) return SWOF_EINVAL;
+    if (p->rain_rate < 0 || !(p->dt_fixed >= 0)) return SWOF_EINVAL;
+    if (!all_finite(z, (size_t)nx * ny)) return SWOF_ENONFINITE;
+
+    swof_ctx *c = new (std::nothrow) swof_ctx();
+    if (!c) return SWOF_ENOMEM;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        delete c;
+        return SWOF_ECUDA;
+    }
+    c->prec = p->precision;
+    c->esize = c->prec == SWOF_FP64 ? 8 : 4;
+    c->L = c->prec == SWOF_FP64 ? &swof::launch_fp64() : &swof::launch_fp32();
+    Params &P = c->P;
+    P.nx = nx;
+    P.ny = ny;
+    P.lpad = c->prec == SWOF_FP64 ? 2 : 4;
+    int align = 128 / (int)c->esize;
+    P.pitch = ((P.lpad + nx + 2) + align - 1) / align * align;
+    P.dx = dx;
+    P.dy = dy;
+    P.g = p->g;
+    P.cfl = p->cfl;
+    P.h_dry = p->h_dry;
+    P.dt_max = p->dt_max;
+    P.dt_min = p->dt_min;
+    P.t_end = p->t_end;
+    P.cfl_mode = p->cfl_mode;
+    P.friction = p->friction;
+    P.infiltration = p->infiltration ? 1 : 0;
+    P.check_cfl = p->check_cfl ? 1 : 0;
+    for (int k = 0; k < 4; ++k) P.bc[k] = p->bc[k];
+    P.n2 = p->manning_n * p->manning_n;
+    P.rain_rate = p->rain_rate;
+    P.rain_t_on = p->rain_t_on;
+    P.rain_t_off = p->rain_t_off;
+    P.ks = p->ks;
+    P.psi = p->psi;
+    P.dtheta = p->dtheta;
+    P.dt_fixed = p->dt_fixed;
+    P.area = dx * dy;
+
+    if (p->stream) {
+        c->stream = (cudaStream_t)p->stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return SWOF_ECUDA;
+        }
+        c->own_stream = true;
+    }
+    int st = cuda_err((cudaError_t)c->L->configure());
+    if (!st) {
+        c->ctl = dalloc<DevCtl>(c, 1, &st);
+        c->d_red = dalloc<double>(c, 4 * 240, &st);
+    }
+    if (!st) st = c->prec == SWOF_FP64 ? alloc_fields<double>(c, c->f64, z, p) : alloc_fields<float>(c, c->f32, z, p);
+    if (!st) st = ensure_hist(c, 1024);
+    if (!st) st = cuda_err(cudaStreamSynchronize(c->stream));
+    if (st) {
+        swof_destroy(c);
+        return st;
+    }
+    *out = c;
+    return SWOF_OK;
+}
+
+void swof_destroy(swof_ctx *c)
+{
+    if (!c) return;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    for (void *p : c->allocs) cudaFree(p);
+    if (c->dt_seq) cudaFree(c->dt_seq);
+    if (c->dt_hist) cudaFree(c->dt_hist);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    cudaSetDevice(dev);
+    delete c;
+}
+
+static int clear_status(swof_ctx *c)
+{
+    int zero = 0;
+    return cuda_err(cudaMemcpyAsync(&c->ctl->status, &zero, sizeof zero, cudaMemcpyHostToDevice, c->stream));
+}
+
+int swof_set_state(swof_ctx *c, const double *h, const double *hu, const double *hv)
+{
+    if (!c || !h || !hu || !hv) return SWOF_EINVAL;
+    size_t n = (size_t)c->P.nx * c->P.ny;
+    if (!all_finite(h, n) || !all_finite(hu, n) || !all_finite(hv, n)) return SWOF_ENONFINITE;
+    for (size_t k = 0; k < n; ++k)
+        if (h[k] < 0.0) return SWOF_ENEGATIVE;
+    int st;
+    if (c->prec == SWOF_FP64) {
+        st = upload_interior<double>(c, c->f64.h, h);
+        if (!st) st = upload_interior<double>(c, c->f64.qx, hu);
+        if (!st) st = upload_interior<double>(c, c->f64.qy, hv);
+    } else {
+        st = upload_interior<float>(c, c->f32.h, h);
+        if (!st) st = upload_interior<float>(c, c->f32.qx, hu);
+        if (!st) st = upload_interior<float>(c, c->f32.qy, hv);
+    }
+    if (!st) st = cuda_err((cudaError_t)c->L->ghosts(c->P, c->fields(), c->stream));
+    if (!st) st = clear_status(c);
+    return st;
+}
+
+int swof_get_state(swof_ctx *c, double *h, double *hu, double *hv)
+{
+    if (!c || !h || !hu || !hv) return SWOF_EINVAL;
+    int st;
+    if (c->prec == SWOF_FP64) {
+        st = download_interior<double>(c, c->f64.h, h);
+        if (!st) st = download_interior<double>(c, c->f64.qx, hu);
+        if (!st) st = download_interior<double>(c, c->f64.qy, hv);
+    } else {
+        st = download_interior<float>(c, c->f32.h, h);
+        if (!st) st = download_interior<float>(c, c->f32.qx, hu);
+        if (!st) st = download_interior<float>(c, c->f32.qy, hv);
+    }
+    if (st) return st;
+    DevCtl d;
+    st = read_ctl(c, &d);
+    return st ? st : d.status;
+}
+
+int swof_set_state_device(swof_ctx *c, const void *h, const void *hu, const void *hv, int dtype)
+{
+    if (!c || !h || !hu || !hv || (dtype != SWOF_FP64 && dtype != SWOF_FP32)) return SWOF_EINVAL;
+    int st = cuda_err((cudaError_t)c->L->unpack(c->P, c->fields(), h, hu, hv, dtype, c->stream));
+    if (!st) st = cuda_err((cudaError_t)c->L->ghosts(c->P, c->fields(), c->stream));
+    if (!st) st = clear_status(c);
+    return st;
+}
+
+int swof_get_state_device(swof_ctx *c, void *h, void *hu, void *hv, int dtype)
+{
+    if (!c || !h || !hu || !hv || (dtype != SWOF_FP64 && dtype != SWOF_FP32)) return SWOF_EINVAL;
+    return cuda_err((cudaError_t)c->L->pack(c->P, c->fields(), h, hu, hv, dtype, c->stream));
+}
+
+int swof_get_infiltrated(swof_ctx *c, double *v)
+{
+    if (!c || !v) return SWOF_EINVAL;
+    return c->prec == SWOF_FP64 ? download_interior<double>(c, c->f64.vinf, v)
+                                : download_interior<float>(c, c->f32.vinf, v);
+}
+
+int swof_set_infiltrated(swof_ctx *c, const double *v)
+{
+    if (!c || !v) return SWOF_EINVAL;
+    size_t n = (size_t)c->P.nx * c->P.ny;
+    if (!all_finite(v, n)) return SWOF_ENONFINITE;
+    for (size_t k = 0; k < n; ++k)
+        if (v[k] < 0.0) return SWOF_ENEGATIVE;
+    return c->prec == SWOF_FP64 ? upload_interior<double>(c, c->f64.vinf, v)
+                                : upload_interior<float>(c, c->f32.vinf, v);
+}
+
+int swof_set_time(swof_ctx *c, double t)
+{
+    if (!c || !std::isfinite(t)) return SWOF_EINVAL;
+    cudaError_t e = cudaMemcpyAsync(&c->ctl->t, &t, sizeof t, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return cuda_err(e);
+}
+
+int swof_step(swof_ctx *c, int n, swof_step_info *info)
+{
+    if (!c || n < 0) return SWOF_EINVAL;
+    int st = ensure_hist(c, n);
+    if (st) return st;
+    c->ev_used = 0;
+    if (n > 0) {
+        if (c->use_graph && !c->timing) {
+            if (!(c->gexec && c->graph_n == n && c->graph_gen == c->gen)) {
+                if (c->gexec) cudaGraphExecDestroy(c->gexec);
+                c->gexec = nullptr;
+                cudaGraph_t g = nullptr;
+                if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+                    return SWOF_ECUDA;
+                int r = enqueue_steps(c, n);
+                cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+                if (r || e != cudaSuccess) {
+                    if (g) cudaGraphDestroy(g);
+                    return SWOF_ECUDA;
+                }
+                e = cudaGraphInstantiate(&c->gexec, g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) return SWOF_ECUDA;
+                c->graph_n = n;
+                c->graph_gen = c->gen;
+            }
+            if (cudaGraphLaunch(c->gexec, c->stream) != cudaSuccess) return SWOF_ECUDA;
+            c->launches_last = 3 * n;
+        } else {
+            st = enqueue_steps(c, n);
+            if (st) return st;
+        }
+        c->host_steps += n;
+    }
+    if (info) {
+        DevCtl d;
+        st = read_ctl(c, &d);
+        if (st) return st;
+        info->t = d.t;
+        info->dt = d.last_dt;
+        info->steps = d.steps;
+        info->status = d.status;
+        return d.status;
+    }
+    return SWOF_OK;
+}
+
+int swof_set_dt_sequence(swof_ctx *c, const double *dts, int n)
+{
+    if (!c || n < 0 || (n > 0 && !dts)) return SWOF_EINVAL;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SWOF_ECUDA;
+    if (c->dt_seq) cudaFree(c->dt_seq);
+    c->dt_seq = nullptr;
+    c->dt_seq_n = 0;
+    if (n > 0) {
+        if (!all_finite(dts, (size_t)n)) return SWOF_ENONFINITE;
+        if (cudaMalloc(&c->dt_seq, (size_t)n * sizeof(double)) != cudaSuccess) return SWOF_ENOMEM;
+        if (cudaMemcpy(c->dt_seq, dts, (size_t)n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+            return SWOF_ECUDA;
+        c->dt_seq_n = n;
+    }
+    int v[2] = {0, n};
+    cudaError_t e = cudaMemcpyAsync(&c->ctl->dt_seq_pos, v, sizeof v, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    set_hist(c);
+    return cuda_err(e);
+}
+
+int swof_get_dt_history(swof_ctx *c, double *out, int max, int *count)
+{
+    if (!c || !out || max < 0 || !count) return SWOF_EINVAL;
+    DevCtl d;
+    int st = read_ctl(c, &d);
+    if (st) return st;
+    long long n = d.steps < c->dt_cap ? d.steps : c->dt_cap;
+    if (n > max) n = max;
+    if (n > 0 && cudaMemcpy(out, c->dt_hist, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return SWOF_ECUDA;
+    *count = (int)n;
+    return SWOF_OK;
+}
+
+int swof_get_diagnostics(swof_ctx *c, swof_diag *d)
+{
+    if (!c || !d) return SWOF_EINVAL;
+    int st = cuda_err((cudaError_t)c->L->reduce(c->P, c->fields(), c->d_red, c->nslots, c->stream));
+    if (st) return st;
+    std::vector<double> part(4 * 240);
+    cudaError_t e = cudaMemcpyAsync(part.data(), c->d_red, part.size() * sizeof(double),
+                                    cudaMemcpyDeviceToHost, c->stream);
+    DevCtl ctl;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ctl, c->ctl, sizeof ctl, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return SWOF_ECUDA;
+    double s = 0.0, mn = INFINITY, so = 0.0, si = 0.0;
+    for (int b = 0; b < 240; ++b) {
+        s += part[4 * b];
+        mn = std::fmin(mn, part[4 * b + 1]);
+        so += part[4 * b + 2];
+        si += part[4 * b + 3];
+    }
+    d->t = ctl.t;
+    d->last_dt = ctl.last_dt;
+    d->steps = ctl.steps;
+    d->volume = s * c->P.dx * c->P.dy;
+    d->rain_in = ctl.rain_in;
+    d->infiltrated = si * c->P.dx * c->P.dy;
+    d->outflow = so;
+    d->min_h = mn;
+    d->cfl_viol = ctl.cfl_viol;
+    return ctl.status;
+}
+
+int swof_enable_timing(swof_ctx *c, int on)
+{
+    if (!c) return SWOF_EINVAL;
+    c->timing = on != 0;
+    return SWOF_OK;
+}
+
+int swof_get_timing(swof_ctx *c, double *ms_l, double *ms_1, double *ms_2, int *launches)
+{
+    if (!c) return SWOF_EINVAL;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SWOF_ECUDA;
+    double a = 0, b = 0, d = 0;
+    for (int k = 0; k + 3 < c->ev_used; k += 4) {
+        float x = 0, y = 0, z = 0;
+        cudaEventElapsedTime(&x, c->ev[k], c->ev[k + 1]);
+        cudaEventElapsedTime(&y, c->ev[k + 1], c->ev[k + 2]);
+        cudaEventElapsedTime(&z, c->ev[k + 2], c->ev[k + 3]);
+        a += x;
+        b += y;
+        d += z;
+    }
+    if (ms_l) *ms_l = a;
+    if (ms_1) *ms_1 = b;
+    if (ms_2) *ms_2 = d;
+    if (launches) *launches = c->launches_last;
+    return SWOF_OK;
+}
+
+int swof_use_graph(swof_ctx *c, int on)
+{
+    if (!c) return SWOF_EINVAL;
+    c->use_graph = on != 0;
+    if (!on && c->gexec) {
+        cudaStreamSynchronize(c->stream);
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    return SWOF_OK;
+}
+
+const char *swof_strerror(int code)
+{
+    switch (code) {
+    case SWOF_OK: return "ok";
+    case SWOF_EINVAL: return "invalid argument";
+    case SWOF_ENOMEM: return "device allocation failed";
+    case SWOF_ECUDA: return "CUDA runtime error";
+    case SWOF_ENONFINITE: return "non-finite value in the state or wave speeds";
+    case SWOF_ENEGATIVE: return "negative water depth";
+    case SWOF_ECFL: return "fixed dt exceeds the CFL bound";
+    case SWOF_EDTSEQ: return "replayed dt sequence exhausted";
+    case SWOF_ETIMEOUT: return "bounded device wait timed out";
+    case SWOF_EDTUNDERFLOW: return "time step below dt_min";
+    case SWOF_ESTATE: return "call not valid in this state";
+    default: return "unknown status";
+    }
+}
+
+const char *swof_version(void) { return "libswof 0.1 (sm_103a; FP64 exact-order + FP32 bulk)"; }
+
+}  // extern "C"

@@ -1,0 +1,17 @@
+// swof_fp64.cu -- FP64 instantiation of the stencil kernels.  Built with
+// -fmad=false (no contraction of a*b+c) and IEEE division / square root so
+// that every value matches the FP64 oracle's operation order bit for bit.
+#include "swof_kernels.cuh"
+
+namespace swof {
+
+const Launch &launch_fp64()
+{
+    static const Launch L = {configure_t<double>, launch_ghosts_t<double>, launch_lambda_t<double>,
+                             launch_stage_t<double, 1>, launch_stage_t<double, 2>,
+                             launch_reduce_t<double>, stage_slots, launch_unpack_t<double>,
+                             launch_pack_t<double>};
+    return L;
+}
+
+}  // namespace swof

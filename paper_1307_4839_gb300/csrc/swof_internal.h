@@ -1,0 +1,89 @@
+// swof_internal.h -- device-side data layout and launcher declarations of
+// libswof (not part of the public ABI; see include/swof.h).
+//
+// Layout in HBM (padded SoA, one array per field):
+//   (ny + 4) rows of `pitch` elements; row r holds grid row j = r - 2
+//   (2 ghost rows below and above, Sec. 6.1: two layers at second order).
+//   Within a row, element lpad + i is cell i, i in [-2, nx + 1]; lpad is 2
+//   for FP64 and 4 for FP32 so the first interior cell sits on a 16-byte
+//   boundary (double2 / float4 aligned).  pitch is a multiple of 128 bytes.
+//   Corner ghosts are never read and stay zero.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/swof.h"
+
+namespace swof {
+
+// Per-context control block in device memory: the CFL reduction words, the
+// dt of the step being taken, simulated time and latched status.
+struct DevCtl {
+    unsigned long long lam_bits[2];   // max wave speed x, y (bits of a double >= 0)
+    unsigned long long lam2_bits[2];  // same at U* (CFL check)
+    unsigned int done;                // blocks finished in the wave-speed kernel
+    unsigned int done2;               // blocks finished in the U* check
+    int status;                       // latched SWOF_E* (0 = ok)
+    int rain_active;                  // rain falls during the current step
+    double t;                         // simulated time (start of next step)
+    double dt, dtdx, dtdy, rdt;       // current step: dt, dt/dx, dt/dy, dt*R
+    double last_dt;
+    long long steps;
+    long long cfl_viol;
+    double rain_in;                   // FP64 budget: rain volume
+    int dt_seq_pos, dt_seq_n;
+    int pad_[2];
+};
+
+// Scalar parameters (by value into every kernel).
+struct Params {
+    int nx, ny, pitch, lpad;
+    double dx, dy;
+    double g, cfl, h_dry, dt_max, dt_min, t_end;
+    int cfl_mode, friction, infiltration, check_cfl;
+    int bc[4];
+    double n2;                 // Manning n^2 (scalar)
+    double rain_rate, rain_t_on, rain_t_off;
+    double ks, psi, dtheta;
+    double dt_fixed;
+    double area;               // unused by the arithmetic; dx*dy
+};
+
+// Device pointers of one context.  T = double (FP64) or float (FP32).
+template <typename T>
+struct Fields {
+    T *h, *qx, *qy;            // U^n (updated in place by stage 2)
+    T *h1, *qx1, *qy1;         // U* (stage-1 output)
+    T *z;                      // FP64 path: topography (padded)
+    T *dzx, *dzy;              // FP32 path: z(i+1)-z(i), z(j+1)-z(j) per face (padded)
+    T *n2map;                  // per-cell n^2 (padded) or nullptr
+    T *ksmap;                  // per-cell K_s (padded) or nullptr
+    T *vinf;                   // infiltrated depth (padded)
+    double *outflow_slots;     // per-block FP64 budget accumulators
+    double *infil_slots;
+    const double *dt_seq;      // replayed dt values or nullptr
+    double *dt_hist;           // dt of every step
+    long long dt_hist_cap;
+    DevCtl *ctl;
+};
+
+// Launchers, one set per precision (swof_fp64.cu, swof_fp32.cu).  All
+// enqueue on `stream` and return cudaError_t as int.
+struct Launch {
+    int (*configure)();              // per-device kernel attributes
+    int (*ghosts)(const Params &, void *fields, void *stream);
+    int (*lambda)(const Params &, void *fields, void *stream);
+    int (*stage1)(const Params &, void *fields, void *stream);
+    int (*stage2)(const Params &, void *fields, void *stream);
+    int (*reduce)(const Params &, void *fields, double *out, int nslots, void *stream);
+    int (*slots)(const Params &);    // number of per-block slots the stage kernels use
+    // dense [ny][nx] device arrays (dtype SWOF_FP64/FP32) <-> padded state
+    int (*unpack)(const Params &, void *fields, const void *h, const void *qx, const void *qy,
+                  int dtype, void *stream);
+    int (*pack)(const Params &, void *fields, void *h, void *qx, void *qy, int dtype, void *stream);
+};
+
+const Launch &launch_fp64();
+const Launch &launch_fp32();
+
+}  // namespace swof
