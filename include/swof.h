@@ -166,6 +166,31 @@ SWOF_API int swof_get_dt_history(swof_ctx *ctx, double *out, int max, int *count
  * Synchronises. */
 SWOF_API int swof_get_diagnostics(swof_ctx *ctx, swof_diag *d);
 
+/* Water volume sum(h) dx dy and minimum depth of a caller-owned depth
+ * field, computed without allocating any device memory.  The paper has no
+ * counterpart: this is a service for callers that may not call cudaMalloc
+ * (code recording into a CUDA graph it captures itself, hosts whose device
+ * memory all belongs to their own pool allocator, real-time loops where an
+ * allocation could synchronise the device).
+ *   h      : device pointer, dense row-major [ny][nx] of dtype (SWOF_FP64
+ *            double or SWOF_FP32 float) on the current device; caller-owned.
+ *   out    : device pointer to 2 doubles, caller-owned: out[0] = volume
+ *            [m^3], out[1] = min h.
+ *   stream : cudaStream_t to enqueue on (NULL = the default stream); the
+ *            call is asynchronous and returns once the kernels are queued.
+ * Scratch is one fixed file-scope device array of 2 * SWOF_NOALLOC_MAX_ROWS
+ * doubles (1 MiB), held by every GPU that loads the library until the
+ * process exits; ny > SWOF_NOALLOC_MAX_ROWS is rejected with SWOF_EINVAL.
+ * The first call on a device looks up that array's device address (once per
+ * device), so make the first call on each device before any stream capture.
+ * All calls share the array: calls that overlap on the GPU race and must be
+ * serialised by the caller.  The sum is a fixed-order reduction (per row,
+ * then over rows), so repeated calls on the same data agree bit for bit.
+ * Errors: SWOF_EINVAL (NULL, size, dtype), SWOF_ECUDA. */
+#define SWOF_NOALLOC_MAX_ROWS 65536
+SWOF_API int swof_volume_noalloc(const void *h, int nx, int ny, int dtype, double dx, double dy,
+                                 double *out, void *stream);
+
 /* Device time of the last swof_step call's kernels, split per kernel
  * family (wave-speed/dt, stage 1, stage 2) in milliseconds, when timing was
  * switched on with swof_enable_timing(ctx, 1).  Synchronises. */

@@ -26,6 +26,7 @@ FP64, FP32 = 0, 1
 CFL_SUM, CFL_MIN = 0, 1
 BC_WALL, BC_OUTFLOW = 0, 1
 FRIC_NONE, FRIC_MANNING = 0, 1
+NOALLOC_MAX_ROWS = 65536
 
 _D = ctypes.POINTER(ctypes.c_double)
 
@@ -84,6 +85,9 @@ _SIGS = {
     "swof_enable_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "swof_get_timing": (ctypes.c_int, [ctypes.c_void_p, _D, _D, _D, ctypes.POINTER(ctypes.c_int)]),
     "swof_use_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "swof_volume_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
+                                           ctypes.c_void_p]),
     "swof_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "swof_version": (ctypes.c_char_p, []),
 }
