@@ -51,7 +51,7 @@ STEP_BYTES = {"fp32": 68, "fp64": 136}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=4096)
@@ -59,6 +59,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
+                    help="precision of the headline measurement (fp64: no variants)")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tile", type=int, default=-1, help="fixed tile shape (skips the autotuner)")
     return ap.parse_args()
 
 
@@ -227,13 +231,21 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
-def measure(sw, torch, w, precision: str, steps: int, warmup: int, ws: int, clocks: Clocks | None):
+def measure(sw, torch, w, precision: str, steps: int, warmup: int, ws: int, clocks: Clocks | None,
+            autotune: bool = True, tile: int = -1):
     prec = sw.FP32 if precision == "fp32" else sw.FP64
     # a dedicated (non-null) stream: the kernels and the timing events share it
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     s = sw.Solver.from_workload(w, prec, stream=stream.cuda_stream)
     s.step(warmup)
+    if tile >= 0 or not autotune:
+        shape = max(tile, 0)
+        s.set_tile_shape(shape)
+        ntx, rows = sw.tile_shapes()[shape]
+        tune = {"ntx": ntx, "rows": rows, "ms": None}
+    else:
+        tune = s.autotune(reps=3, cache=os.path.join(ROOT, "paper_1307_4839_gb300", "_build", "autotune.json"))
     torch.cuda.synchronize()
     barrier(ws)
     e0 = torch.cuda.Event(enable_timing=True)
@@ -256,6 +268,7 @@ def measure(sw, torch, w, precision: str, steps: int, warmup: int, ws: int, cloc
     t = s.timing()
     s.enable_timing(False)
     d = s.diagnostics()
+    d["tile"] = {"ntx": tune["ntx"], "rows": tune["rows"], "ms_per_shape": tune["ms"]}
     return ms, t, clk, d, s
 
 
@@ -276,7 +289,9 @@ def main():
     hbm, peak_kind = peaks()
 
     clocks = Clocks(local)
-    ms, t, clk, diag, solver = measure(sw, torch, w, "fp32", args.steps, args.warmup, ws, clocks)
+    P = args.precision
+    ms, t, clk, diag, solver = measure(sw, torch, w, P, args.steps, args.warmup, ws, clocks,
+                                       not args.no_autotune, args.tile)
     ms_max = max_over_ranks(ms, ws)
     ms_step = ms_max / args.steps
     value = ws * cells / (ms_step * 1e-3) * 1e-9
@@ -284,19 +299,21 @@ def main():
     k = args.steps
     avg = {"lambda": t["lambda_ms"] / k, "stage1": t["stage1_ms"] / k, "stage2": t["stage2_ms"] / k}
     dom = max(avg, key=avg.get)
-    achieved = BYTES["fp32"][dom] * cells / (avg[dom] * 1e-3) * 1e-9
-    roofline = {"bound": "hbm", "kernel": f"k_stage<float,{dom[-1]}>" if dom != "lambda" else "k_lambda<float>",
+    achieved = BYTES[P][dom] * cells / (avg[dom] * 1e-3) * 1e-9
+    tname = "float" if P == "fp32" else "double"
+    roofline = {"bound": "hbm", "kernel": f"k_sweep<{tname},{dom[-1]}>" if dom != "lambda" else f"k_lambda<{tname}>",
                 "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "peak_kind": f"{peak_kind} copy bandwidth (burst)",
-                "traffic": recorded_traffic(dom, "fp32"),
-                "algorithmic_bytes_per_cell": BYTES["fp32"][dom],
+                "traffic": recorded_traffic(dom, P),
+                "algorithmic_bytes_per_cell": BYTES[P][dom],
                 "kernel_ms": {kk: round(v, 5) for kk, v in avg.items()},
-                "step_frac_of_hbm": STEP_BYTES["fp32"] * cells / (ms_step * 1e-3) * 1e-9 / hbm}
+                "step_frac_of_hbm": STEP_BYTES[P] * cells / (ms_step * 1e-3) * 1e-9 / hbm}
 
     variants = {}
-    if not args.no_fp64:
+    if not args.no_fp64 and P == "fp32":
         k64 = max(5, args.steps // 4)
-        ms64, t64, _, _, s64 = measure(sw, torch, w, "fp64", k64, args.warmup, ws, None)
+        ms64, t64, _, d64, s64 = measure(sw, torch, w, "fp64", k64, args.warmup, ws, None,
+                                         not args.no_autotune, args.tile)
         ms64 = max_over_ranks(ms64, ws)
         v64 = ws * cells / (ms64 / k64 * 1e-3) * 1e-9
         avg64 = {"lambda": t64["lambda_ms"] / k64, "stage1": t64["stage1_ms"] / k64,
@@ -305,7 +322,7 @@ def main():
                             "fp32_over_fp64": value / v64,
                             "kernel_ms": {kk: round(v, 4) for kk, v in avg64.items()},
                             "hbm_frac_algorithmic": STEP_BYTES["fp64"] * cells / (ms64 / k64 * 1e-3) * 1e-9 / hbm,
-                            "bound": "alu (FP64 pipe)"}
+                            "bound": "alu (FP64 pipe)", "tile": d64["tile"]}
         del s64
 
     e2e = None
@@ -340,11 +357,12 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_name(w), "grid": [w.nx, w.ny], "precision": "fp32 bulk, fp64 dt/time/budgets",
+        "vs_baseline": None, "dtype": "f32" if P == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": workload_name(w), "grid": [w.nx, w.ny], "precision": "fp32 bulk, fp64 dt/time/budgets" if P == "fp32" else "fp64",
                    "l2": f"inputs larger than L2 (working set {(9 * (w.ny + 4) * (w.nx + 8) * 4) / 1e6:.0f} MB)",
                    "parallelism": "replicas" if ws > 1 else "single GPU",
-                   "counted": "all interior cells, dry cells included"},
+                   "counted": "all interior cells, dry cells included",
+                   "tile": diag["tile"]},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -202,6 +202,19 @@ SWOF_API int swof_get_timing(swof_ctx *ctx, double *ms_lambda, double *ms_stage1
  * small grids gain the most. */
 SWOF_API int swof_use_graph(swof_ctx *ctx, int on);
 
+/* Stage-kernel tile shapes.  The stage kernels walk columns down the grid;
+ * a shape is (threads per CTA along x, rows per CTA).  swof_tile_shapes
+ * writes up to max shapes (ntx[k], rows[k]) and returns how many exist.
+ * swof_set_tile_shape selects one for a context (results do not depend on
+ * it).  swof_autotune times the stage-1 kernel of every shape `reps` times
+ * on the context's current state (the state, time and budgets are left as
+ * they are), selects the fastest, and writes the average milliseconds per
+ * shape to ms (nullable, one entry per shape) and the choice to *best.
+ * Synchronises.  Not in the paper: a GB300 launch-shape choice. */
+SWOF_API int swof_tile_shapes(int *ntx, int *rows, int max);
+SWOF_API int swof_set_tile_shape(swof_ctx *ctx, int shape);
+SWOF_API int swof_autotune(swof_ctx *ctx, int reps, double *ms, int *best);
+
 /* Human-readable text for a status code (static storage). */
 SWOF_API const char *swof_strerror(int code);
 

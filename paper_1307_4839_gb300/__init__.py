@@ -88,6 +88,9 @@ _SIGS = {
     "swof_volume_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
                                            ctypes.c_void_p]),
+    "swof_tile_shapes": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+    "swof_set_tile_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "swof_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_int)]),
     "swof_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "swof_version": (ctypes.c_char_p, []),
 }
@@ -282,3 +285,55 @@ class Solver:
 
     def use_graph(self, on=True):
         _check(load().swof_use_graph(self._ctx, int(bool(on))), "swof_use_graph")
+
+    def set_tile_shape(self, shape: int):
+        _check(load().swof_set_tile_shape(self._ctx, int(shape)), "swof_set_tile_shape")
+
+    def autotune(self, reps: int = 5, cache: str | None = None, key: str | None = None) -> dict:
+        """Pick the fastest stage-kernel tile shape for this grid and
+        precision.  With `cache`, a JSON file maps "<gpu>|<nx>x<ny>|<prec>"
+        to the chosen shape so later runs skip the timing."""
+        import json
+        if key is None:
+            key = f"{_gpu_name()}|{self.nx}x{self.ny}|{'fp64' if self.precision == FP64 else 'fp32'}"
+        data = {}
+        if cache and os.path.exists(cache):
+            try:
+                data = json.load(open(cache))
+            except (OSError, ValueError):
+                data = {}
+        if key in data:
+            self.set_tile_shape(int(data[key]["shape"]))
+            return dict(data[key], cached=True)
+        n = tile_shapes()
+        ms = (ctypes.c_double * len(n))()
+        best = ctypes.c_int()
+        _check(load().swof_autotune(self._ctx, int(reps), ms, ctypes.byref(best)), "swof_autotune")
+        rec = {"shape": best.value, "ntx": n[best.value][0], "rows": n[best.value][1],
+               "ms": [ms[k] for k in range(len(n))]}
+        if cache:
+            data[key] = rec
+            tmp = cache + ".tmp"
+            os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
+            with open(tmp, "w") as f:
+                json.dump(data, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return dict(rec, cached=False)
+
+
+def tile_shapes() -> list[tuple[int, int]]:
+    """(threads along x, rows) of each stage-kernel shape."""
+    L = load()
+    n = L.swof_tile_shapes(None, None, 0)
+    a = (ctypes.c_int * n)()
+    b = (ctypes.c_int * n)()
+    L.swof_tile_shapes(a, b, n)
+    return [(a[k], b[k]) for k in range(n)]
+
+
+def _gpu_name() -> str:
+    try:
+        import torch
+        return torch.cuda.get_device_name()
+    except Exception:
+        return "gpu"

@@ -41,6 +41,10 @@ struct swof_ctx {
     cudaGraphExec_t gexec = nullptr;
     int graph_n = 0;
     unsigned gen = 1, graph_gen = 0;
+    // wave speeds: after a fused stage 2 the next step needs only the ring
+    bool lam_valid = false;
+    bool graph_lam = false;
+    int *d_ring_cols = nullptr, *d_ring_rows = nullptr;
     // per-kernel timing of the last swof_step call
     bool timing = false;
     std::vector<cudaEvent_t> ev;
@@ -226,6 +230,40 @@ int ensure_hist(swof_ctx *c, long long more)
     return cuda_err(e);
 }
 
+// Forget the partial wave-speed maximum a fused stage 2 left behind (the
+// state or the tile shape changed): the next step runs the full pass.
+int invalidate_lambda(swof_ctx *c)
+{
+    c->lam_valid = false;
+    return cuda_err(cudaMemsetAsync(c->ctl->lam_bits, 0, sizeof c->ctl->lam_bits, c->stream));
+}
+
+// Tile-edge columns and rows of the current tile shape (plus the last
+// column/row), whose wave speeds the ring kernel computes.
+int update_rings(swof_ctx *c)
+{
+    const Params &P = c->P;
+    int w = swof::TILE_SHAPES[P.tile_cfg].ntx - 4, h = swof::TILE_SHAPES[P.tile_cfg].h;
+    std::vector<int> cols, rows;
+    for (int i = 0; i < P.nx; ++i)
+        if (i % w == 0 || i % w == w - 1 || i == P.nx - 1) cols.push_back(i);
+    for (int j = 0; j < P.ny; ++j)
+        if (j % h == 0 || j % h == h - 1 || j == P.ny - 1) rows.push_back(j);
+    cudaError_t e = cudaMemcpyAsync(c->d_ring_cols, cols.data(), cols.size() * sizeof(int),
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_ring_rows, rows.data(), rows.size() * sizeof(int), cudaMemcpyHostToDevice,
+                            c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    c->f64.ring_cols = c->f32.ring_cols = c->d_ring_cols;
+    c->f64.ring_rows = c->f32.ring_rows = c->d_ring_rows;
+    c->f64.n_ring_cols = c->f32.n_ring_cols = (int)cols.size();
+    c->f64.n_ring_rows = c->f32.n_ring_rows = (int)rows.size();
+    c->gen++;
+    int st = cuda_err(e);
+    return st ? st : invalidate_lambda(c);
+}
+
 int enqueue_steps(swof_ctx *c, int n)
 {
     void *f = c->fields();
@@ -239,7 +277,7 @@ int enqueue_steps(swof_ctx *c, int n)
                 c->ev.push_back(e);
             }
             cudaEventRecord(c->ev[c->ev_used + 0], c->stream);
-            r = c->L->lambda(c->P, f, c->stream);
+            r = c->lam_valid ? c->L->lambda_ring(c->P, f, c->stream) : c->L->lambda(c->P, f, c->stream);
             cudaEventRecord(c->ev[c->ev_used + 1], c->stream);
             if (!r) r = c->L->stage1(c->P, f, c->stream);
             cudaEventRecord(c->ev[c->ev_used + 2], c->stream);
@@ -247,10 +285,11 @@ int enqueue_steps(swof_ctx *c, int n)
             cudaEventRecord(c->ev[c->ev_used + 3], c->stream);
             c->ev_used += 4;
         } else {
-            r = c->L->lambda(c->P, f, c->stream);
+            r = c->lam_valid ? c->L->lambda_ring(c->P, f, c->stream) : c->L->lambda(c->P, f, c->stream);
             if (!r) r = c->L->stage1(c->P, f, c->stream);
             if (!r) r = c->L->stage2(c->P, f, c->stream);
         }
+        c->lam_valid = c->P.fuse_lambda != 0;
         c->launches_last += 3;
     }
     return r ? SWOF_ECUDA : SWOF_OK;
@@ -336,6 +375,13 @@ int swof_create(int nx, int ny, double dx, double dy, const double *z, const swo
     P.dtheta = p->dtheta;
     P.dt_fixed = p->dt_fixed;
     P.area = dx * dy;
+    P.fg = (float)P.g;
+    P.fh_dry = (float)P.h_dry;
+    P.fn2 = (float)P.n2;
+    P.fpsi = (float)P.psi;
+    P.fdtheta = (float)P.dtheta;
+    P.fks = (float)P.ks;
+    P.fuse_lambda = 1;
 
     if (p->stream) {
         c->stream = (cudaStream_t)p->stream;
@@ -352,6 +398,11 @@ int swof_create(int nx, int ny, double dx, double dy, const double *z, const swo
         c->d_red = dalloc<double>(c, 4 * 240, &st);
     }
     if (!st) st = c->prec == SWOF_FP64 ? alloc_fields<double>(c, c->f64, z, p) : alloc_fields<float>(c, c->f32, z, p);
+    if (!st) {
+        c->d_ring_cols = dalloc<int>(c, (size_t)nx, &st);
+        c->d_ring_rows = dalloc<int>(c, (size_t)ny, &st);
+    }
+    if (!st) st = update_rings(c);
     if (!st) st = ensure_hist(c, 1024);
     if (!st) st = cuda_err(cudaStreamSynchronize(c->stream));
     if (st) {
@@ -404,6 +455,7 @@ int swof_set_state(swof_ctx *c, const double *h, const double *hu, const double 
     }
     if (!st) st = cuda_err((cudaError_t)c->L->ghosts(c->P, c->fields(), c->stream));
     if (!st) st = clear_status(c);
+    if (!st) st = invalidate_lambda(c);
     return st;
 }
 
@@ -432,6 +484,7 @@ int swof_set_state_device(swof_ctx *c, const void *h, const void *hu, const void
     int st = cuda_err((cudaError_t)c->L->unpack(c->P, c->fields(), h, hu, hv, dtype, c->stream));
     if (!st) st = cuda_err((cudaError_t)c->L->ghosts(c->P, c->fields(), c->stream));
     if (!st) st = clear_status(c);
+    if (!st) st = invalidate_lambda(c);
     return st;
 }
 
@@ -475,10 +528,11 @@ int swof_step(swof_ctx *c, int n, swof_step_info *info)
     c->ev_used = 0;
     if (n > 0) {
         if (c->use_graph && !c->timing) {
-            if (!(c->gexec && c->graph_n == n && c->graph_gen == c->gen)) {
+            if (!(c->gexec && c->graph_n == n && c->graph_gen == c->gen && c->graph_lam == c->lam_valid)) {
                 if (c->gexec) cudaGraphExecDestroy(c->gexec);
                 c->gexec = nullptr;
                 cudaGraph_t g = nullptr;
+                c->graph_lam = c->lam_valid;
                 if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
                     return SWOF_ECUDA;
                 int r = enqueue_steps(c, n);
@@ -495,6 +549,7 @@ int swof_step(swof_ctx *c, int n, swof_step_info *info)
             }
             if (cudaGraphLaunch(c->gexec, c->stream) != cudaSuccess) return SWOF_ECUDA;
             c->launches_last = 3 * n;
+            c->lam_valid = c->P.fuse_lambda != 0;
         } else {
             st = enqueue_steps(c, n);
             if (st) return st;
@@ -618,6 +673,63 @@ int swof_use_graph(swof_ctx *c, int on)
         c->gexec = nullptr;
     }
     return SWOF_OK;
+}
+
+int swof_tile_shapes(int *ntx, int *rows, int max)
+{
+    for (int k = 0; k < swof::N_TILE_SHAPES && k < max; ++k) {
+        if (ntx) ntx[k] = swof::TILE_SHAPES[k].ntx;
+        if (rows) rows[k] = swof::TILE_SHAPES[k].h;
+    }
+    return swof::N_TILE_SHAPES;
+}
+
+int swof_set_tile_shape(swof_ctx *c, int shape)
+{
+    if (!c || shape < 0 || shape >= swof::N_TILE_SHAPES) return SWOF_EINVAL;
+    if (c->P.tile_cfg == shape) return SWOF_OK;
+    c->P.tile_cfg = shape;
+    return update_rings(c);
+}
+
+int swof_autotune(swof_ctx *c, int reps, double *ms, int *best)
+{
+    if (!c || reps < 1 || !best) return SWOF_EINVAL;
+    Params P = c->P;
+    P.no_budget = 1;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return SWOF_ECUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return SWOF_ECUDA;
+    }
+    int st = SWOF_OK, bk = 0;
+    double bms = INFINITY;
+    for (int k = 0; k < swof::N_TILE_SHAPES && !st; ++k) {
+        P.tile_cfg = k;
+        // one untimed launch (first-use cost), then `reps` timed ones
+        if (c->L->stage1(P, c->fields(), c->stream)) st = SWOF_ECUDA;
+        cudaEventRecord(e0, c->stream);
+        for (int r = 0; r < reps && !st; ++r)
+            if (c->L->stage1(P, c->fields(), c->stream)) st = SWOF_ECUDA;
+        cudaEventRecord(e1, c->stream);
+        float t = 0.0f;
+        if (!st && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess) {
+            double m = (double)t / reps;
+            if (ms) ms[k] = m;
+            if (m < bms) {
+                bms = m;
+                bk = k;
+            }
+        } else {
+            st = SWOF_ECUDA;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    *best = bk;
+    return swof_set_tile_shape(c, bk);
 }
 
 const char *swof_strerror(int code)

@@ -6,7 +6,7 @@ namespace swof {
 
 const Launch &launch_fp32()
 {
-    static const Launch L = {configure_t<float>, launch_ghosts_t<float>, launch_lambda_t<float>,
+    static const Launch L = {configure_t<float>, launch_ghosts_t<float>, launch_lambda_t<float>, launch_lambda_ring_t<float>,
                              launch_stage_t<float, 1>, launch_stage_t<float, 2>,
                              launch_reduce_t<float>, stage_slots, launch_unpack_t<float>,
                              launch_pack_t<float>};

@@ -7,7 +7,7 @@ namespace swof {
 
 const Launch &launch_fp64()
 {
-    static const Launch L = {configure_t<double>, launch_ghosts_t<double>, launch_lambda_t<double>,
+    static const Launch L = {configure_t<double>, launch_ghosts_t<double>, launch_lambda_t<double>, launch_lambda_ring_t<double>,
                              launch_stage_t<double, 1>, launch_stage_t<double, 2>,
                              launch_reduce_t<double>, stage_slots, launch_unpack_t<double>,
                              launch_pack_t<double>};

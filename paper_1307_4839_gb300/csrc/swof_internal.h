@@ -32,7 +32,7 @@ struct DevCtl {
     long long cfl_viol;
     double rain_in;                   // FP64 budget: rain volume
     int dt_seq_pos, dt_seq_n;
-    int pad_[2];
+    float fdt, fdtdx, fdtdy, frdt;    // the same four in FP32 for the FP32 kernels
 };
 
 // Scalar parameters (by value into every kernel).
@@ -47,7 +47,30 @@ struct Params {
     double ks, psi, dtheta;
     double dt_fixed;
     double area;               // unused by the arithmetic; dx*dy
+    // FP32 copies of the scalars the FP32 kernels use (no FP64 on their path)
+    float fg, fh_dry, fn2, fpsi, fdtheta, fks;
+    int tile_cfg;              // stage-kernel shape, index into the sweep shapes
+    int no_budget;             // 1: stage kernels leave the budget slots alone (timing runs)
+    int fuse_lambda;           // 1: stage 2 adds the wave speeds of U^{n+1} of its tile interiors
 };
+
+// Stage-kernel shapes (threads per CTA along x, rows per CTA); the last two
+// fields bound the number of per-block budget slots any shape can need.
+struct TileShape {
+    int ntx, h;
+};
+constexpr int N_TILE_SHAPES = 4;
+constexpr TileShape TILE_SHAPES[N_TILE_SHAPES] = {{128, 32}, {128, 64}, {256, 32}, {64, 64}};
+inline int max_stage_blocks(int nx, int ny)
+{
+    int m = 0;
+    for (int k = 0; k < N_TILE_SHAPES; ++k) {
+        int w = TILE_SHAPES[k].ntx - 4, h = TILE_SHAPES[k].h;
+        int b = ((nx + w - 1) / w) * ((ny + h - 1) / h);
+        m = b > m ? b : m;
+    }
+    return m;
+}
 
 // Device pointers of one context.  T = double (FP64) or float (FP32).
 template <typename T>
@@ -61,6 +84,9 @@ struct Fields {
     T *vinf;                   // infiltrated depth (padded)
     double *outflow_slots;     // per-block FP64 budget accumulators
     double *infil_slots;
+    const int *ring_cols;      // columns / rows whose wave speeds stage 2 leaves out
+    const int *ring_rows;      //   (tile-edge columns/rows for the current tile shape)
+    int n_ring_cols, n_ring_rows;
     const double *dt_seq;      // replayed dt values or nullptr
     double *dt_hist;           // dt of every step
     long long dt_hist_cap;
@@ -73,6 +99,7 @@ struct Launch {
     int (*configure)();              // per-device kernel attributes
     int (*ghosts)(const Params &, void *fields, void *stream);
     int (*lambda)(const Params &, void *fields, void *stream);
+    int (*lambda_ring)(const Params &, void *fields, void *stream);
     int (*stage1)(const Params &, void *fields, void *stream);
     int (*stage2)(const Params &, void *fields, void *stream);
     int (*reduce)(const Params &, void *fields, double *out, int nslots, void *stream);

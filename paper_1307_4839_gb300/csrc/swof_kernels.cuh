@@ -5,16 +5,15 @@
 //               warp-shuffle + block max, one atomicMax per block on the
 //               bits of a non-negative double; the last block computes dt
 //               (FP64) and advances the control block.
-//   k_stage<1>: U* = U^n + dt Phi(U^n) -- boundary values, MUSCL-minmod
+//   k_sweep<1>: U* = U^n + dt Phi(U^n) -- boundary values, MUSCL-minmod
 //               (Sec. 3.4), hydrostatic reconstruction + HLL + S_L/S_R/Fc
 //               (Sec. 3.1, 3.3), scheme Eq. (SW1Dscheme) in x and y,
 //               semi-implicit Manning friction (Sec. 3.2).  Writes U* and
 //               its ghost cells.
-//   k_stage<2>: the same on U*, then the Heun average with U^n (in place),
+//   k_sweep<2>: the same on U*, then the Heun average with U^n (in place),
 //               rain, Green-Ampt (Sec. 3.5), the dry clean-up and ghosts.
-// Each CTA owns a BX x BY tile; it stages the tile plus a 2-cell halo of
-// (h, q, z) in shared memory, reconstructs every cell that touches one of
-// its faces once, computes every face flux once and updates its cells.
+// The stage kernels walk columns down the grid (swof_sweep.cuh): every cell
+// is reconstructed once per direction, every face flux computed once.
 //
 // FP64 (T = double): every expression follows the oracle's operation order
 // and is compiled with -fmad=false, so results match it bit for bit.
@@ -33,25 +32,20 @@
 
 namespace swof {
 
-constexpr int BX = 32, BY = 8, NT = BX * BY;
-constexpr int AX = BX + 4, AY = BY + 4, SA = AX * AY;   // tile + 2-halo
-constexpr int RXW = BX + 2, RXN = RXW * BY;              // x-recon cells
-constexpr int RYW = BX, RYN = RYW * (BY + 2);            // y-recon cells
-constexpr int FXW = BX + 1, FXN = FXW * BY;              // x faces
-constexpr int FYW = BX, FYN = FYW * (BY + 1);            // y faces
+constexpr int BX = 32, BY = 8, NT = BX * BY;              // wave-speed kernel tile
 constexpr int LX = BX + 2, LY = BY + 2, LA = LX * LY;    // wave-speed tile + 1-halo
 constexpr int NW = NT / 32;
 constexpr int REDUCE_BLOCKS = 240;
 
+// 4-vectors for shared memory: one 128-bit (FP32) or 2 x 128-bit (FP64)
+// access per 4 values.
 template <typename T>
-struct StageSmem {
-    T h[SA], za[SA], zb[SA], u[SA], v[SA], rh[SA], qx[SA], qy[SA];
-    T xhm[RXN], xhp[RXN], xzm[RXN], xzp[RXN], xum[RXN], xup[RXN], xvm[RXN], xvp[RXN];
-    T yhm[RYN], yhp[RYN], yzm[RYN], yzp[RYN], yum[RYN], yup[RYN], yvm[RYN], yvp[RYN];
-    T fx1[FXN], fx2l[FXN], fx2r[FXN], fx3[FXN];
-    T fy1[FYN], fy2l[FYN], fy2r[FYN], fy3[FYN];
-    double red[NW];
-    unsigned long long redb[2][NW];
+struct alignas(4 * sizeof(T)) V4 {
+    T x, y, z, w;
+};
+template <typename T>
+struct alignas(2 * sizeof(T)) V2 {
+    T x, y;
 };
 
 __device__ __forceinline__ double mn(double a, double b) { return fmin(a, b); }
@@ -60,21 +54,79 @@ __device__ __forceinline__ double mx(double a, double b) { return fmax(a, b); }
 __device__ __forceinline__ float mx(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double ab(double a) { return fabs(a); }
 __device__ __forceinline__ float ab(float a) { return fabsf(a); }
+// FP64: IEEE square root and division (the oracle's).  FP32: the PTX
+// approximate forms (sqrt.approx: relative error ~2^-23, sqrt(+0) = +0;
+// rcp.approx: 1 ulp), never applied to a zero divisor.
 __device__ __forceinline__ double sq(double a) { return sqrt(a); }
-__device__ __forceinline__ float sq(float a) { return sqrtf(a); }
-
-// minmod limiter (Sec. 3.4)
-template <typename T>
-__device__ __forceinline__ T minmod(T a, T b)
+__device__ __forceinline__ float sq(float a)
 {
-    if (a >= T(0) && b >= T(0)) return mn(a, b);
-    if (a <= T(0) && b <= T(0)) return mx(a, b);
-    return T(0);
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
 }
+__device__ __forceinline__ double rcp(double a) { return 1.0 / a; }
+__device__ __forceinline__ float rcp(float a)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+
+// Scalar parameters in the kernel's precision (no conversions on the path).
+template <typename T>
+struct Scal {
+    T g, hdry, n2, psi, dtheta, ks;
+};
+template <typename T>
+__device__ __forceinline__ Scal<T> scal(const Params &P)
+{
+    if constexpr (std::is_same<T, double>::value)
+        return {P.g, P.h_dry, P.n2, P.psi, P.dtheta, P.ks};
+    else
+        return {P.fg, P.fh_dry, P.fn2, P.fpsi, P.fdtheta, P.fks};
+}
+
+// minmod limiter (Sec. 3.4): the value of smaller magnitude when a and b
+// have the same sign, else 0.
+//  FP64: decided on the IEEE bit patterns with integer operations (sign bits
+//  differ -> 0, else the smaller magnitude); this returns exactly the value
+//  of the comparison-based definition (up to the sign of a zero result) and
+//  keeps the work off GB300's narrow FP64 pipe.
+//  FP32: branch-free, a*b > 0 selects min(|a|,|b|) with the sign of a.
+__device__ __forceinline__ double minmod(double a, double b)
+{
+    long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+    if ((ia ^ ib) < 0) return 0.0;
+    long long ma = ia & 0x7fffffffffffffffLL, mb = ib & 0x7fffffffffffffffLL;
+    return ma <= mb ? a : b;
+}
+__device__ __forceinline__ float minmod(float a, float b)
+{
+    return (a * b > 0.0f) ? copysignf(fminf(fabsf(a), fabsf(b)), a) : 0.0f;
+}
+
+// max(0, x) (the hydrostatic cut, Sec. 3.1); FP64 by the sign bit.
+__device__ __forceinline__ double pos(double x)
+{
+    return (__double_as_longlong(x) < 0) ? 0.0 : x;
+}
+__device__ __forceinline__ float pos(float x) { return fmaxf(0.0f, x); }
+
+// max / min of two doubles through order-preserving integer keys (same value
+// as fmax / fmin for finite inputs, again off the FP64 pipe).
+__device__ __forceinline__ long long okey(double x)
+{
+    long long i = __double_as_longlong(x);
+    return i ^ ((i >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double dmax(double a, double b) { return okey(a) >= okey(b) ? a : b; }
+__device__ __forceinline__ double dmin(double a, double b) { return okey(a) <= okey(b) ? a : b; }
+__device__ __forceinline__ float dmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ float dmin(float a, float b) { return fminf(a, b); }
 
 // x^{-1/3}: FP64 by Newton's method on y^{-3} - x with a start value from
 // the exponent bits (x = m 2^e, e = 3k + r: y0 = 2^-k 2^{-r/3} (1 - 0.2063
-// (m - 1))), four steps y <- y + y (1 - x y^3)/3.  FP32 calls rcbrtf.
+// (m - 1))), four steps y <- y + y (1 - x y^3)/3.  FP32: 2^{-log2(x)/3} (PTX approximations).
 __device__ __forceinline__ double icbrt(double x)
 {
     long long bits = __double_as_longlong(x);
@@ -93,7 +145,15 @@ __device__ __forceinline__ double icbrt(double x)
     }
     return y;
 }
-__device__ __forceinline__ float icbrt(float x) { return rcbrtf(x); }
+__device__ __forceinline__ float icbrt(float x)
+{
+    // x^{-1/3} = 2^{-log2(x)/3} with the PTX approximate log2 / exp2
+    float l, r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(x));
+    l = l * (-1.0f / 3.0f);
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(l));
+    return r;
+}
 
 template <typename T>
 struct Rec {
@@ -165,14 +225,27 @@ __device__ __forceinline__ T cell_speed(T h0, T h1, T h2, T un0, T un1, T un2, T
     return mx(ab(unm) + sq(g * hm), ab(unp) + sq(g * hp));
 }
 
-// Ordered 64-bit key of a non-negative speed (NaN sorts above everything).
-template <typename T>
-__device__ __forceinline__ unsigned long long speed_key(T a)
+// Ordered key of a non-negative speed: the bits of the value (NaN sorts
+// above everything, -0 maps to 0).  FP32 keys are 32-bit so the FP32 path
+// needs no FP64 instruction per cell; key64() widens one winner per block.
+__device__ __forceinline__ unsigned long long speed_key(double a)
 {
-    double d = (double)a;
-    if (d == 0.0) return 0ull;
-    return (unsigned long long)__double_as_longlong(d);
+    unsigned long long k = (unsigned long long)__double_as_longlong(a);
+    return (k == 0x8000000000000000ull) ? 0ull : k;
 }
+__device__ __forceinline__ unsigned int speed_key(float a)
+{
+    unsigned int k = __float_as_uint(a);
+    return (k == 0x80000000u) ? 0u : k;
+}
+__device__ __forceinline__ unsigned long long key64(unsigned long long k) { return k; }
+__device__ __forceinline__ unsigned long long key64(unsigned int k)
+{
+    float f = __uint_as_float(k);
+    return k == 0u ? 0ull : (unsigned long long)__double_as_longlong((double)f);
+}
+template <typename K>
+__device__ __forceinline__ K kmax(K a, K b) { return a > b ? a : b; }
 
 // HLL flux (Sec. 3.3) of one face + the well-balancing corrections
 // S_L, S_R (Sec. 3.1).  a = left cell's plus side, b = right cell's minus
@@ -185,9 +258,9 @@ __device__ __forceinline__ void face_flux(T g, T hpa, T zpa, T unpa, T utpa,
     T hL, hR;
     if constexpr (std::is_same<T, double>::value) {
         (void)dz;
-        double zmax = fmax(zpa, zmb);
-        hL = fmax(0.0, (hpa + zpa) - zmax);
-        hR = fmax(0.0, (hmb + zmb) - zmax);
+        double zmax = dmax(zpa, zmb);
+        hL = pos((hpa + zpa) - zmax);
+        hR = pos((hmb + zmb) - zmax);
     } else {
         float zb = dz + zmb;                       // z_+ relative to z_a
         hL = fmaxf(0.0f, hpa - fmaxf(0.0f, zb - zpa));
@@ -201,8 +274,8 @@ __device__ __forceinline__ void face_flux(T g, T hpa, T zpa, T unpa, T utpa,
         F2 = T(0);
     } else {
         T cL = sq(g * hL), cR = sq(g * hR);
-        T c1 = mn(unpa - cL, unmb - cR);
-        T c2 = mx(unpa + cL, unmb + cR);
+        T c1 = dmin(unpa - cL, unmb - cR);
+        T c2 = dmax(unpa + cL, unmb + cR);
         T qL = hL * unpa, qR = hR * unmb;
         T FL0 = qL, FL1 = qL * unpa + T(0.5) * g * hL * hL, FL2 = qL * utpa;
         T FR0 = qR, FR1 = qR * unmb + T(0.5) * g * hR * hR, FR2 = qR * utmb;
@@ -211,7 +284,7 @@ __device__ __forceinline__ void face_flux(T g, T hpa, T zpa, T unpa, T utpa,
         } else if (c2 <= T(0)) {
             F0 = FR0; F1 = FR1; F2 = FR2;
         } else {
-            T r = T(1) / (c2 - c1);
+            T r = rcp(c2 - c1);
             T w = c1 * c2 * r;
             F0 = (c2 * FL0 - c1 * FR0) * r + w * (hR - hL);
             F1 = (c2 * FL1 - c1 * FR1) * r + w * (qR - qL);
@@ -243,18 +316,32 @@ __device__ __forceinline__ double block_sum(double v, double *red)
     return s;
 }
 
-__device__ __forceinline__ unsigned long long block_max(unsigned long long v, unsigned long long *red)
+template <typename K>
+__device__ __forceinline__ K block_max(K v, K *red)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
-        v = w > v ? w : v;
-    }
+    for (int o = 16; o > 0; o >>= 1) v = kmax(v, (K)__shfl_xor_sync(0xffffffffu, v, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
-    unsigned long long s = 0;
+    K s = 0;
     if (threadIdx.x == 0)
-        for (int w = 0; w < NW; ++w) s = red[w] > s ? red[w] : s;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = kmax(s, red[w]);
+    __syncthreads();
+    return s;
+}
+
+// Sum of one value per thread of T, returned in FP64 to thread 0: FP32 warps
+// reduce in FP32 and widen one value per warp (fixed order throughout).
+template <typename T>
+__device__ __forceinline__ double block_sum_t(T v, double *red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
     __syncthreads();
     return s;
 }
@@ -322,6 +409,10 @@ __device__ void control(const Params &P, const Fields<T> &F)
     int rain = P.rain_rate > 0.0 && t >= P.rain_t_on && t < P.rain_t_off;
     c->rain_active = rain;
     c->rdt = dt * P.rain_rate;
+    c->fdt = (float)c->dt;
+    c->fdtdx = (float)c->dtdx;
+    c->fdtdy = (float)c->dtdy;
+    c->frdt = (float)c->rdt;
     if (rain) c->rain_in += c->rdt * (double)P.nx * (double)P.ny * P.dx * P.dy;
     if (F.dt_hist && c->steps < F.dt_hist_cap) F.dt_hist[c->steps] = dt;
     c->t = tn;
@@ -334,15 +425,16 @@ __device__ void control(const Params &P, const Fields<T> &F)
 template <typename T>
 __global__ void __launch_bounds__(NT) k_lambda(Params P, Fields<T> F)
 {
-    __shared__ T sh[LA], su[LA], sv[LA], srh[LA];
-    __shared__ unsigned long long red[2][NW];
+    using K = decltype(speed_key(T(0)));
+    __shared__ V4<T> st[LA];   // {h, u, v, 1/h}
+    __shared__ K red[2][NW];
     DevCtl *ctl = F.ctl;
     if (ctl->status) return;
-    const T hdry = (T)P.h_dry, g = (T)P.g;
+    const Scal<T> C = scal<T>(P);
     const int tid = threadIdx.x;
     const int tx = (P.nx + BX - 1) / BX, ty = (P.ny + BY - 1) / BY;
     const int ntiles = tx * ty;
-    unsigned long long kx = 0ull, ky = 0ull;
+    K kx = 0, ky = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int i0 = (tile % tx) * BX, j0 = (tile / tx) * BY;
         for (int idx = tid; idx < LA; idx += NT) {
@@ -354,16 +446,13 @@ __global__ void __launch_bounds__(NT) k_lambda(Params P, Fields<T> F)
                 qx = F.qx[o];
                 qy = F.qy[o];
             }
-            T rh = T(0), u = T(0), v = T(0);
-            if (h > hdry) {
-                rh = T(1) / h;
-                u = qx * rh;
-                v = qy * rh;
+            V4<T> e = {h, T(0), T(0), T(0)};
+            if (h > C.hdry) {
+                e.w = rcp(h);
+                e.y = qx * e.w;
+                e.z = qy * e.w;
             }
-            sh[idx] = h;
-            su[idx] = u;
-            sv[idx] = v;
-            srh[idx] = rh;
+            st[idx] = e;
         }
         __syncthreads();
         {
@@ -371,11 +460,11 @@ __global__ void __launch_bounds__(NT) k_lambda(Params P, Fields<T> F)
             int gi = i0 + ti, gj = j0 + tj;
             if (gi < P.nx && gj < P.ny) {
                 int c = (tj + 1) * LX + (ti + 1);
-                T ax = cell_speed(sh[c - 1], sh[c], sh[c + 1], su[c - 1], su[c], su[c + 1], srh[c], hdry, g);
-                T ay = cell_speed(sh[c - LX], sh[c], sh[c + LX], sv[c - LX], sv[c], sv[c + LX], srh[c], hdry, g);
-                unsigned long long a = speed_key(ax), b = speed_key(ay);
-                kx = a > kx ? a : kx;
-                ky = b > ky ? b : ky;
+                V4<T> m = st[c], w = st[c - 1], e = st[c + 1], s_ = st[c - LX], n = st[c + LX];
+                T ax = cell_speed(w.x, m.x, e.x, w.y, m.y, e.y, m.w, C.hdry, C.g);
+                T ay = cell_speed(s_.x, m.x, n.x, s_.z, m.z, n.z, m.w, C.hdry, C.g);
+                kx = kmax(kx, speed_key(ax));
+                ky = kmax(ky, speed_key(ay));
             }
         }
         __syncthreads();
@@ -383,8 +472,63 @@ __global__ void __launch_bounds__(NT) k_lambda(Params P, Fields<T> F)
     kx = block_max(kx, red[0]);
     ky = block_max(ky, red[1]);
     if (tid == 0) {
-        atomicMax(&ctl->lam_bits[0], kx);
-        atomicMax(&ctl->lam_bits[1], ky);
+        atomicMax(&ctl->lam_bits[0], key64(kx));
+        atomicMax(&ctl->lam_bits[1], key64(ky));
+        __threadfence();
+        unsigned int ticket = atomicAdd(&ctl->done, 1u);
+        if (ticket == gridDim.x - 1) control(P, F);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Wave speeds of U^n on the tile-edge columns and rows the fused stage-2
+// kernel of the previous step left out (x speeds on ring columns, y speeds
+// on ring rows, read back from the stored U^n and its ghosts), merged into
+// the same reduction words; the last block computes dt.
+template <typename T>
+__device__ __forceinline__ V4<T> cell_rec(const Params &P, const Fields<T> &F, int gi, int gj, T hdry)
+{
+    size_t o = pidx(P, gi, gj);
+    T h = F.h[o];
+    V4<T> e = {h, T(0), T(0), T(0)};
+    if (h > hdry) {
+        e.w = rcp(h);
+        e.y = F.qx[o] * e.w;
+        e.z = F.qy[o] * e.w;
+    }
+    return e;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_lambda_ring(Params P, Fields<T> F)
+{
+    using K = decltype(speed_key(T(0)));
+    __shared__ K red[2][NW];
+    DevCtl *ctl = F.ctl;
+    if (ctl->status) return;
+    const Scal<T> C = scal<T>(P);
+    K kx = 0, ky = 0;
+    const long long nxr = (long long)F.n_ring_cols * P.ny;
+    const long long total = nxr + (long long)F.n_ring_rows * P.nx;
+    for (long long k = blockIdx.x * (long long)NT + threadIdx.x; k < total; k += (long long)gridDim.x * NT) {
+        if (k < nxr) {
+            int gj = (int)(k / F.n_ring_cols), gi = F.ring_cols[k % F.n_ring_cols];
+            V4<T> w = cell_rec(P, F, gi - 1, gj, C.hdry), m = cell_rec(P, F, gi, gj, C.hdry),
+                  e = cell_rec(P, F, gi + 1, gj, C.hdry);
+            kx = kmax(kx, speed_key(cell_speed(w.x, m.x, e.x, w.y, m.y, e.y, m.w, C.hdry, C.g)));
+        } else {
+            long long q = k - nxr;
+            int gj = F.ring_rows[q / P.nx], gi = (int)(q % P.nx);
+            V4<T> s_ = cell_rec(P, F, gi, gj - 1, C.hdry), m = cell_rec(P, F, gi, gj, C.hdry),
+                  n = cell_rec(P, F, gi, gj + 1, C.hdry);
+            ky = kmax(ky, speed_key(cell_speed(s_.x, m.x, n.x, s_.z, m.z, n.z, m.w, C.hdry, C.g)));
+        }
+    }
+    kx = block_max(kx, red[0]);
+    ky = block_max(ky, red[1]);
+    if (threadIdx.x == 0) {
+        atomicMax(&ctl->lam_bits[0], key64(kx));
+        atomicMax(&ctl->lam_bits[1], key64(ky));
         __threadfence();
         unsigned int ticket = atomicAdd(&ctl->done, 1u);
         if (ticket == gridDim.x - 1) control(P, F);
@@ -441,229 +585,6 @@ __device__ __forceinline__ void store_cell(const Params &P, T *h, T *qx, T *qy, 
             size_t g1 = pidx(P, gi, P.ny), g2 = pidx(P, gi, P.ny + 1);
             h[g1] = hv; qx[g1] = qxv; qy[g1] = qyv;
             h[g2] = hv; qx[g2] = qxv; qy[g2] = qyv;
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// One Heun stage over a BX x BY tile.
-template <typename T, int STAGE>
-__global__ void __launch_bounds__(NT) k_stage(Params P, Fields<T> F)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    StageSmem<T> &S = *reinterpret_cast<StageSmem<T> *>(smem_raw);
-    const DevCtl *ctl = F.ctl;
-    if (ctl->status) return;
-    constexpr bool fp64 = std::is_same<T, double>::value;
-    const T hdry = (T)P.h_dry, g = (T)P.g;
-    const int tid = threadIdx.x;
-    const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY;
-    const T *hin = (STAGE == 1) ? F.h : F.h1;
-    const T *qxin = (STAGE == 1) ? F.qx : F.qx1;
-    const T *qyin = (STAGE == 1) ? F.qy : F.qy1;
-
-    // (A) boundary-filled input tile with halo; velocities u = q/h
-    for (int idx = tid; idx < SA; idx += NT) {
-        int gi = i0 + idx % AX - 2, gj = j0 + idx / AX - 2;
-        T h = T(0), qx = T(0), qy = T(0), za = T(0), zb = T(0);
-        if (gi <= P.nx + 1 && gj <= P.ny + 1) {
-            size_t o = pidx(P, gi, gj);
-            h = hin[o];
-            qx = qxin[o];
-            qy = qyin[o];
-            if constexpr (fp64) {
-                za = F.z[o];
-            } else {
-                za = F.dzx[o];
-                zb = F.dzy[o];
-            }
-        }
-        T rh = T(0), u = T(0), v = T(0);
-        if (h > hdry) {
-            rh = T(1) / h;
-            u = qx * rh;
-            v = qy * rh;
-        }
-        S.h[idx] = h; S.za[idx] = za; S.zb[idx] = zb;
-        S.u[idx] = u; S.v[idx] = v; S.rh[idx] = rh;
-        S.qx[idx] = qx; S.qy[idx] = qy;
-    }
-    __syncthreads();
-
-    // (B) second-order reconstruction of every cell touching a tile face
-    for (int idx = tid; idx < RXN + RYN; idx += NT) {
-        if (idx < RXN) {
-            int r = idx / RXW, cx = idx % RXW;           // cell (cx - 1, r)
-            int c = (r + 2) * AX + (cx + 1);
-            Rec<T> q;
-            if constexpr (fp64)
-                q = muscl<T>(S.h[c - 1], S.h[c], S.h[c + 1], S.za[c - 1], S.za[c], S.za[c + 1],
-                             S.u[c - 1], S.u[c], S.u[c + 1], S.v[c - 1], S.v[c], S.v[c + 1], S.rh[c], hdry);
-            else
-                q = muscl<T>(S.h[c - 1], S.h[c], S.h[c + 1], S.za[c - 1], S.za[c], T(0),
-                             S.u[c - 1], S.u[c], S.u[c + 1], S.v[c - 1], S.v[c], S.v[c + 1], S.rh[c], hdry);
-            S.xhm[idx] = q.hm; S.xhp[idx] = q.hp; S.xzm[idx] = q.zm; S.xzp[idx] = q.zp;
-            S.xum[idx] = q.unm; S.xup[idx] = q.unp; S.xvm[idx] = q.utm; S.xvp[idx] = q.utp;
-        } else {
-            int k = idx - RXN;
-            int r = k / RYW, cx = k % RYW;               // cell (cx, r - 1)
-            int c = (r + 1) * AX + (cx + 2);
-            Rec<T> q;
-            if constexpr (fp64)
-                q = muscl<T>(S.h[c - AX], S.h[c], S.h[c + AX], S.za[c - AX], S.za[c], S.za[c + AX],
-                             S.v[c - AX], S.v[c], S.v[c + AX], S.u[c - AX], S.u[c], S.u[c + AX], S.rh[c], hdry);
-            else
-                q = muscl<T>(S.h[c - AX], S.h[c], S.h[c + AX], S.zb[c - AX], S.zb[c], T(0),
-                             S.v[c - AX], S.v[c], S.v[c + AX], S.u[c - AX], S.u[c], S.u[c + AX], S.rh[c], hdry);
-            S.yhm[k] = q.hm; S.yhp[k] = q.hp; S.yzm[k] = q.zm; S.yzp[k] = q.zp;
-            S.yvm[k] = q.unm; S.yvp[k] = q.unp; S.yum[k] = q.utm; S.yup[k] = q.utp;
-        }
-    }
-    __syncthreads();
-
-    // (C) hydrostatic reconstruction + HLL at every face of the tile;
-    // boundary faces also feed the outflow budget
-    double outacc = 0.0;
-    const bool any_out = (P.bc[0] | P.bc[1] | P.bc[2] | P.bc[3]) != 0;
-    for (int idx = tid; idx < FXN + FYN; idx += NT) {
-        if (idx < FXN) {
-            int r = idx / FXW, f = idx % FXW;            // face between (f-1, r) and (f, r)
-            int a = r * RXW + f, b = a + 1;
-            T dz = T(0);
-            if constexpr (!fp64) dz = S.za[(r + 2) * AX + (f + 1)];
-            T f1, f2l, f2r, f3;
-            face_flux<T>(g, S.xhp[a], S.xzp[a], S.xup[a], S.xvp[a],
-                         S.xhm[b], S.xzm[b], S.xum[b], S.xvm[b], dz, f1, f2l, f2r, f3);
-            S.fx1[idx] = f1; S.fx2l[idx] = f2l; S.fx2r[idx] = f2r; S.fx3[idx] = f3;
-            if (any_out) {
-                int gl = i0 + f - 1, gj = j0 + r;
-                if (gj < P.ny) {
-                    if (gl == -1) outacc -= (double)f1 * P.dy;
-                    if (gl == P.nx - 1) outacc += (double)f1 * P.dy;
-                }
-            }
-        } else {
-            int k = idx - FXN;
-            int f = k / FYW, cx = k % FYW;               // face between (cx, f-1) and (cx, f)
-            int a = f * RYW + cx, b = a + RYW;
-            T dz = T(0);
-            if constexpr (!fp64) dz = S.zb[(f + 1) * AX + (cx + 2)];
-            T f1, f2l, f2r, f3;
-            face_flux<T>(g, S.yhp[a], S.yzp[a], S.yvp[a], S.yup[a],
-                         S.yhm[b], S.yzm[b], S.yvm[b], S.yum[b], dz, f1, f2l, f2r, f3);
-            S.fy1[k] = f1; S.fy2l[k] = f2l; S.fy2r[k] = f2r; S.fy3[k] = f3;
-            if (any_out) {
-                int gl = j0 + f - 1, gi = i0 + cx;
-                if (gi < P.nx) {
-                    if (gl == -1) outacc -= (double)f1 * P.dx;
-                    if (gl == P.ny - 1) outacc += (double)f1 * P.dx;
-                }
-            }
-        }
-    }
-    __syncthreads();
-
-    // (D) scheme + friction (+ Heun average and sources in stage 2)
-    const double dtd = ctl->dt;
-    const T dt = (T)dtd, dtdx = (T)ctl->dtdx, dtdy = (T)ctl->dtdy;
-    const T hg = T(0.5) * g;
-    double infacc = 0.0;
-    unsigned long long k2x = 0ull, k2y = 0ull;
-    {
-        int ti = tid % BX, tj = tid / BX;
-        int gi = i0 + ti, gj = j0 + tj;
-        if (gi < P.nx && gj < P.ny) {
-            int c = (tj + 2) * AX + (ti + 2);
-            int rx = tj * RXW + (ti + 1);                // x-recon index of the cell
-            int ry = (tj + 1) * RYW + ti;                // y-recon index of the cell
-            int fe = tj * FXW + (ti + 1), fw = fe - 1;   // x faces E, W
-            int fn = (tj + 1) * FYW + ti, fs = fn - FYW; // y faces N, S
-            T fcx = hg * (S.xhm[rx] + S.xhp[rx]) * (S.xzp[rx] - S.xzm[rx]);
-            T fcy = hg * (S.yhm[ry] + S.yhp[ry]) * (S.yzp[ry] - S.yzm[ry]);
-            T hs = S.h[c] - dtdx * (S.fx1[fe] - S.fx1[fw]) - dtdy * (S.fy1[fn] - S.fy1[fs]);
-            T qxs = S.qx[c] - dtdx * ((S.fx2l[fe] - S.fx2r[fw]) + fcx) - dtdy * (S.fy3[fn] - S.fy3[fs]);
-            T qys = S.qy[c] - dtdx * (S.fx3[fe] - S.fx3[fw]) - dtdy * ((S.fy2l[fn] - S.fy2r[fs]) + fcy);
-            if (hs > hdry) {
-                if (P.friction == SWOF_FRIC_MANNING) {
-                    size_t o = pidx(P, gi, gj);
-                    T n2 = F.n2map ? F.n2map[o] : (T)P.n2;
-                    T speed = sq(S.u[c] * S.u[c] + S.v[c] * S.v[c]);
-                    T y = icbrt(hs);
-                    T hinv43 = (y * y) * (y * y);
-                    T den = T(1) + (dt * g * n2) * speed * hinv43;
-                    T rden = T(1) / den;
-                    qxs = qxs * rden;
-                    qys = qys * rden;
-                }
-            } else {
-                qxs = T(0);
-                qys = T(0);
-            }
-            if (STAGE == 1) {
-                store_cell<T>(P, F.h1, F.qx1, F.qy1, gi, gj, hs, qxs, qys);
-            } else {
-                if (P.check_cfl) {
-                    T sx = mx(ab(S.xum[rx]) + sq(g * S.xhm[rx]), ab(S.xup[rx]) + sq(g * S.xhp[rx]));
-                    T sy = mx(ab(S.yvm[ry]) + sq(g * S.yhm[ry]), ab(S.yvp[ry]) + sq(g * S.yhp[ry]));
-                    k2x = speed_key(sx);
-                    k2y = speed_key(sy);
-                }
-                size_t o = pidx(P, gi, gj);
-                T h = T(0.5) * (F.h[o] + hs);
-                T qx = T(0.5) * (F.qx[o] + qxs);
-                T qy = T(0.5) * (F.qy[o] + qys);
-                if (ctl->rain_active) h = h + (T)ctl->rdt;
-                if (P.infiltration) {
-                    T vi = F.vinf[o];
-                    T ks = F.ksmap ? F.ksmap[o] : (T)P.ks;
-                    T d;
-                    if (vi > T(0)) {
-                        T ic = ks * (T(1) + (((T)P.psi + h) * (T)P.dtheta) / vi);
-                        d = mn(h, dt * ic);
-                    } else {
-                        d = h;
-                    }
-                    h = h - d;
-                    F.vinf[o] = vi + d;
-                    infacc = (double)d;
-                }
-                if (h <= hdry) {
-                    qx = T(0);
-                    qy = T(0);
-                }
-                store_cell<T>(P, F.h, F.qx, F.qy, gi, gj, h, qx, qy);
-            }
-        }
-    }
-
-    // per-block FP64 budget slots (fixed order: deterministic)
-    const int blk = blockIdx.y * gridDim.x + blockIdx.x;
-    if (any_out) {
-        double s = block_sum(outacc, S.red);
-        if (tid == 0) F.outflow_slots[blk] += 0.5 * dtd * s;
-    }
-    if (STAGE == 2 && P.infiltration) {
-        double s = block_sum(infacc, S.red);
-        if (tid == 0) F.infil_slots[blk] += s;
-    }
-    if (STAGE == 2 && P.check_cfl) {
-        k2x = block_max(k2x, S.redb[0]);
-        k2y = block_max(k2y, S.redb[1]);
-        if (tid == 0) {
-            DevCtl *c = F.ctl;
-            atomicMax(&c->lam2_bits[0], k2x);
-            atomicMax(&c->lam2_bits[1], k2y);
-            __threadfence();
-            unsigned int nb = gridDim.x * gridDim.y;
-            if (atomicAdd(&c->done2, 1u) == nb - 1) {
-                __threadfence();
-                double lx = __longlong_as_double((long long)atomicAdd(&c->lam2_bits[0], 0ull));
-                double ly = __longlong_as_double((long long)atomicAdd(&c->lam2_bits[1], 0ull));
-                c->lam2_bits[0] = 0ull;
-                c->lam2_bits[1] = 0ull;
-                c->done2 = 0u;
-                if (dtd * (lx / P.dx + ly / P.dy) > P.cfl) c->cfl_viol++;
-            }
         }
     }
 }
@@ -745,6 +666,10 @@ __global__ void __launch_bounds__(NT) k_reduce(Params P, Fields<T> F, double *ou
     }
 }
 
+}  // namespace swof
+#include "swof_sweep.cuh"
+namespace swof {
+
 // ---------------------------------------------------------------------------
 // Launchers
 template <typename T>
@@ -772,23 +697,41 @@ int launch_lambda_t(const Params &P, void *f, void *stream)
 }
 
 template <typename T>
+int launch_lambda_ring_t(const Params &P, void *f, void *stream)
+{
+    const Fields<T> &F = *static_cast<const Fields<T> *>(f);
+    long long total = (long long)F.n_ring_cols * P.ny + (long long)F.n_ring_rows * P.nx;
+    long long b = (total + NT - 1) / NT;
+    int grid = (int)(b < 152 * 8 ? (b > 0 ? b : 1) : 152 * 8);
+    k_lambda_ring<T><<<grid, NT, 0, (cudaStream_t)stream>>>(P, F);
+    return (int)cudaGetLastError();
+}
+
+template <typename T>
 int configure_t()
 {
-    int smem = (int)sizeof(StageSmem<T>);
-    cudaError_t e = cudaFuncSetAttribute(k_stage<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_stage<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    return (int)e;
+    return (int)cudaSuccess;
+}
+
+template <typename T, int STAGE, int NTX, int H>
+int launch_sweep(const Params &P, const Fields<T> &F, cudaStream_t s)
+{
+    dim3 grid((P.nx + NTX - 5) / (NTX - 4), (P.ny + H - 1) / H);
+    k_sweep<T, STAGE, NTX, H><<<grid, NTX, 0, s>>>(P, F);
+    return (int)cudaGetLastError();
 }
 
 template <typename T, int STAGE>
 int launch_stage_t(const Params &P, void *f, void *stream)
 {
     const Fields<T> &F = *static_cast<const Fields<T> *>(f);
-    size_t smem = sizeof(StageSmem<T>);
-    dim3 grid((P.nx + BX - 1) / BX, (P.ny + BY - 1) / BY);
-    k_stage<T, STAGE><<<grid, NT, smem, (cudaStream_t)stream>>>(P, F);
-    return (int)cudaGetLastError();
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (P.tile_cfg) {
+    case 1: return launch_sweep<T, STAGE, 128, 64>(P, F, s);
+    case 2: return launch_sweep<T, STAGE, 256, 32>(P, F, s);
+    case 3: return launch_sweep<T, STAGE, 64, 64>(P, F, s);
+    default: return launch_sweep<T, STAGE, 128, 32>(P, F, s);
+    }
 }
 
 template <typename T>
@@ -851,9 +794,6 @@ int launch_pack_t(const Params &P, void *f, void *h, void *qx, void *qy, int dty
     return (int)cudaGetLastError();
 }
 
-inline int stage_slots(const Params &P)
-{
-    return ((P.nx + BX - 1) / BX) * ((P.ny + BY - 1) / BY);
-}
+inline int stage_slots(const Params &P) { return max_stage_blocks(P.nx, P.ny); }
 
 }  // namespace swof

@@ -1,0 +1,324 @@
+// swof_sweep.cuh -- the Heun-stage kernel as a column sweep (sm_103a).
+//
+// A CTA of NTX threads owns NTX - 4 output columns (2 halo columns on each
+// side) and H output rows.  Each thread owns one column and walks down the
+// rows j0-2 .. j0+H+1 once:
+//   * y direction: the column's last three rows live in registers, so the
+//     y-reconstruction (Sec. 3.4), the y-face hydrostatic reconstruction +
+//     HLL (Sec. 3.1, 3.3) and the update of row r-2 need no shared memory;
+//     each y-face is computed once (the face above row r-2 becomes the face
+//     below row r-1 in the next iteration);
+//   * x direction: the current row goes through a one-row shared buffer
+//     (3 barriers per row): x-reconstruction, then each thread's east face
+//     flux, then its west neighbour's; the x flux differences of a row wait
+//     two iterations in registers until that row is updated.
+// Every input cell is read from HBM once (next row prefetched), every output
+// written once.  The per-cell arithmetic is exactly the one of the oracle
+// (same functions, same operation order), so the FP64 instantiation stays
+// bit-identical to it.
+#pragma once
+
+namespace swof {
+
+template <typename T>
+struct Cell {
+    T h, u, v, rh, qx, qy, zy;
+};
+
+template <typename T>
+__device__ __forceinline__ Cell<T> make_cell(T h, T qx, T qy, T zy, T hdry)
+{
+    Cell<T> c = {h, T(0), T(0), T(0), qx, qy, zy};
+    if (h > hdry) {
+        c.rh = rcp(h);
+        c.u = qx * c.rh;
+        c.v = qy * c.rh;
+    }
+    return c;
+}
+
+template <typename T, int STAGE, int NTX, int H>
+__global__ void __launch_bounds__(NTX) k_sweep(Params P, Fields<T> F)
+{
+    constexpr bool fp64 = std::is_same<T, double>::value;
+    constexpr int W = NTX - 4;
+    using K = decltype(speed_key(T(0)));
+    __shared__ V4<T> s_st[NTX];   // {h, u, v, 1/h} of the current row
+    __shared__ T s_zx[NTX];       // FP64: z; FP32: dz_x
+    __shared__ V4<T> s_m[NTX];    // x-recon minus side {h, z, u, v}
+    __shared__ V4<T> s_f[NTX];    // flux through the cell's east face
+    __shared__ V4<T> s_nw[2][NTX]; // U^{n+1} {h, u, v, 1/h} of the finished row
+    __shared__ double s_red[NTX / 32];
+    __shared__ K s_redk[2][NTX / 32];
+
+    const DevCtl *ctl = F.ctl;
+    if (ctl->status) return;
+    const Scal<T> C = scal<T>(P);
+    const int t = threadIdx.x;
+    const int gi = blockIdx.x * W - 2 + t;
+    const int j0 = blockIdx.y * H;
+    const bool col_in = gi <= P.nx + 1;
+    const bool out_col = t >= 2 && t < NTX - 2 && gi < P.nx;
+    const T *hin = (STAGE == 1) ? F.h : F.h1;
+    const T *qxin = (STAGE == 1) ? F.qx : F.qx1;
+    const T *qyin = (STAGE == 1) ? F.qy : F.qy1;
+    T dt, dtdx, dtdy, rdt;
+    if constexpr (fp64) {
+        dt = ctl->dt; dtdx = ctl->dtdx; dtdy = ctl->dtdy; rdt = ctl->rdt;
+    } else {
+        dt = ctl->fdt; dtdx = ctl->fdtdx; dtdy = ctl->fdtdy; rdt = ctl->frdt;
+    }
+    const bool rain = ctl->rain_active != 0;
+    const T hg = T(0.5) * C.g;
+
+    // row loader (zeros outside the padded array)
+    auto load = [&](int r, T &h, T &qx, T &qy, T &zx, T &zy) {
+        h = qx = qy = zx = zy = T(0);
+        if (col_in && r <= P.ny + 1) {
+            size_t o = pidx(P, gi, r);
+            h = hin[o];
+            qx = qxin[o];
+            qy = qyin[o];
+            if constexpr (fp64) {
+                zx = F.z[o];
+                zy = zx;
+            } else {
+                zx = F.dzx[o];
+                zy = F.dzy[o];
+            }
+        }
+    };
+
+    Cell<T> ra{}, rb{};                 // rows r-2, r-1
+    V4<T> ypa{};                        // y-recon plus side of row r-2 {h, z, v, u}
+    T fcya = T(0);                      // centred y source term of row r-2
+    V4<T> gs{};                         // y-face flux below row r-2
+    T a1q[2] = {T(0), T(0)}, a2q[2] = {T(0), T(0)}, a3q[2] = {T(0), T(0)};  // x parts, rows r-1, r
+    T outacc = T(0), infacc = T(0);
+    K k2x = 0, k2y = 0;
+    K lx = 0, ly = 0;                   // wave speeds of U^{n+1} (stage 2, fused)
+    T y1h = T(0), y1v = T(0), y1rh = T(0), y2h = T(0), y2v = T(0);   // U^{n+1} rows ro-1, ro-2
+    const bool xlam = t >= 3 && t <= NTX - 4 && gi <= P.nx - 2;
+
+    // per-cell data of the row updated in the next iteration, fetched one
+    // iteration ahead: U^n (stage 2), n^2 map, V_inf and K_s
+    T un_h = T(0), un_qx = T(0), un_qy = T(0), pn2 = C.n2, pvi = T(0), pks = C.ks;
+    auto prefetch = [&](int ro) {
+        if (!(out_col && ro >= j0 && ro < j0 + H && ro < P.ny)) return;
+        size_t o = pidx(P, gi, ro);
+        if (STAGE == 2) {
+            un_h = F.h[o];
+            un_qx = F.qx[o];
+            un_qy = F.qy[o];
+            if (P.infiltration) {
+                pvi = F.vinf[o];
+                if (F.ksmap) pks = F.ksmap[o];
+            }
+        }
+        if (F.n2map) pn2 = F.n2map[o];
+    };
+
+    T nh, nqx, nqy, nzx, nzy;
+    load(j0 - 2, nh, nqx, nqy, nzx, nzy);
+    for (int k = 0; k < H + 4; ++k) {
+        const int r = j0 - 2 + k;
+        T h = nh, qx = nqx, qy = nqy, zx = nzx, zy = nzy;
+        if (k + 1 < H + 4) load(r + 1, nh, nqx, nqy, nzx, nzy);
+        T c_h = un_h, c_qx = un_qx, c_qy = un_qy, c_n2 = pn2, c_vi = pvi, c_ks = pks;
+        prefetch(r - 1);
+        Cell<T> rc = make_cell(h, qx, qy, zy, C.hdry);
+
+        // ---- x part of row r (only rows this CTA updates) ----
+        T a1 = T(0), a2 = T(0), a3 = T(0);
+        if (r >= j0 && r < j0 + H && r < P.ny) {     // uniform over the CTA
+            s_st[t] = {rc.h, rc.u, rc.v, rc.rh};
+            s_zx[t] = zx;
+            __syncthreads();
+            Rec<T> q{};
+            const bool rec = t >= 1 && t <= NTX - 2;
+            if (rec) {
+                V4<T> L = s_st[t - 1], R = s_st[t + 1];
+                if constexpr (fp64)
+                    q = muscl<T>(L.x, rc.h, R.x, s_zx[t - 1], zx, s_zx[t + 1],
+                                 L.y, rc.u, R.y, L.z, rc.v, R.z, rc.rh, C.hdry);
+                else
+                    q = muscl<T>(L.x, rc.h, R.x, s_zx[t - 1], zx, T(0),
+                                 L.y, rc.u, R.y, L.z, rc.v, R.z, rc.rh, C.hdry);
+                s_m[t] = {q.hm, q.zm, q.unm, q.utm};
+            }
+            __syncthreads();
+            V4<T> fe{};
+            if (t >= 1 && t <= NTX - 3) {
+                V4<T> R = s_m[t + 1];
+                face_flux<T>(C.g, q.hp, q.zp, q.unp, q.utp, R.x, R.y, R.z, R.w, fp64 ? T(0) : zx,
+                             fe.x, fe.y, fe.z, fe.w);
+                s_f[t] = fe;
+            }
+            __syncthreads();
+            if (out_col) {
+                if (STAGE == 2 && P.check_cfl)
+                    k2x = kmax(k2x, speed_key(mx(ab(q.unm) + sq(C.g * q.hm), ab(q.unp) + sq(C.g * q.hp))));
+                V4<T> fw = s_f[t - 1];
+                T fcx = hg * (q.hm + q.hp) * (q.zp - q.zm);
+                a1 = fe.x - fw.x;
+                a2 = (fe.y - fw.z) + fcx;
+                a3 = fe.w - fw.w;
+                if (gi == 0 && P.bc[0] == SWOF_BC_OUTFLOW) outacc -= fw.x * (T)P.dy;
+                if (gi == P.nx - 1 && P.bc[1] == SWOF_BC_OUTFLOW) outacc += fe.x * (T)P.dy;
+            }
+        }
+
+        // ---- y part: recon of row r-1, face between r-2 and r-1, update of r-2 ----
+        if (k >= 2) {
+            Rec<T> qb;
+            if constexpr (fp64)
+                qb = muscl<T>(ra.h, rb.h, rc.h, ra.zy, rb.zy, rc.zy, ra.v, rb.v, rc.v, ra.u, rb.u, rc.u,
+                              rb.rh, C.hdry);
+            else
+                qb = muscl<T>(ra.h, rb.h, rc.h, ra.zy, rb.zy, T(0), ra.v, rb.v, rc.v, ra.u, rb.u, rc.u,
+                              rb.rh, C.hdry);
+            if (STAGE == 2 && P.check_cfl && out_col && r - 1 >= j0 && r - 1 < j0 + H && r - 1 < P.ny)
+                k2y = kmax(k2y, speed_key(mx(ab(qb.unm) + sq(C.g * qb.hm), ab(qb.unp) + sq(C.g * qb.hp))));
+            V4<T> gn{};
+            if (k >= 3)
+                face_flux<T>(C.g, ypa.x, ypa.y, ypa.z, ypa.w, qb.hm, qb.zm, qb.unm, qb.utm,
+                             fp64 ? T(0) : ra.zy, gn.x, gn.y, gn.z, gn.w);
+            const int ro = r - 2;                      // row updated now
+            T fh = T(0), fu = T(0), fv = T(0), frh = T(0);
+            if (k >= 4 && ro < P.ny && out_col) {
+                T b1 = gn.x - gs.x;
+                T b2 = (gn.y - gs.z) + fcya;
+                T b3 = gn.w - gs.w;
+                T hs = ra.h - dtdx * a1q[0] - dtdy * b1;
+                T qxs = ra.qx - dtdx * a2q[0] - dtdy * b3;
+                T qys = ra.qy - dtdx * a3q[0] - dtdy * b2;
+                size_t o = pidx(P, gi, ro);
+                if (hs > C.hdry) {
+                    if (P.friction == SWOF_FRIC_MANNING) {
+                        T n2 = c_n2;
+                        T speed = sq(ra.u * ra.u + ra.v * ra.v);
+                        T y = icbrt(hs);
+                        T hinv43 = (y * y) * (y * y);
+                        T den = T(1) + (dt * C.g * n2) * speed * hinv43;
+                        T rden = rcp(den);
+                        qxs = qxs * rden;
+                        qys = qys * rden;
+                    }
+                } else {
+                    qxs = T(0);
+                    qys = T(0);
+                }
+                if (ro == 0 && P.bc[2] == SWOF_BC_OUTFLOW) outacc -= gs.x * (T)P.dx;
+                if (ro == P.ny - 1 && P.bc[3] == SWOF_BC_OUTFLOW) outacc += gn.x * (T)P.dx;
+                if (STAGE == 1) {
+                    store_cell<T>(P, F.h1, F.qx1, F.qy1, gi, ro, hs, qxs, qys);
+                } else {
+                    T hn = T(0.5) * (c_h + hs);
+                    T qxn = T(0.5) * (c_qx + qxs);
+                    T qyn = T(0.5) * (c_qy + qys);
+                    if (rain) hn = hn + rdt;
+                    if (P.infiltration) {
+                        T vi = c_vi;
+                        T ks = c_ks;
+                        T d;
+                        if (vi > T(0)) {
+                            T ic = ks * (T(1) + ((C.psi + hn) * C.dtheta) / vi);
+                            d = mn(hn, dt * ic);
+                        } else {
+                            d = hn;
+                        }
+                        hn = hn - d;
+                        F.vinf[o] = vi + d;
+                        infacc += d;
+                    }
+                    if (hn <= C.hdry) {
+                        qxn = T(0);
+                        qyn = T(0);
+                    }
+                    store_cell<T>(P, F.h, F.qx, F.qy, gi, ro, hn, qxn, qyn);
+                    fh = hn;
+                    if (hn > C.hdry) {
+                        frh = rcp(hn);
+                        fu = qxn * frh;
+                        fv = qyn * frh;
+                    }
+                }
+            }
+            // wave speeds of U^{n+1} (Eq. (cfl)) for cells whose neighbours
+            // this CTA owns; the tile-edge columns/rows are left to the ring
+            // kernel of the next step
+            if (STAGE == 2 && P.fuse_lambda && k >= 4) {       // uniform over the CTA
+                V4<T> *buf = s_nw[k & 1];
+                buf[t] = {fh, fu, fv, frh};
+                __syncthreads();
+                if (out_col && ro < P.ny) {
+                    if (xlam) {
+                        V4<T> L = buf[t - 1], R = buf[t + 1];
+                        lx = kmax(lx, speed_key(cell_speed(L.x, fh, R.x, L.y, fu, R.y, frh, C.hdry, C.g)));
+                    }
+                    const int rr = ro - 1;
+                    if (rr >= j0 + 1 && rr <= j0 + H - 2 && rr <= P.ny - 2)
+                        ly = kmax(ly, speed_key(cell_speed(y2h, y1h, fh, y2v, y1v, fv, y1rh, C.hdry, C.g)));
+                }
+                y2h = y1h;
+                y2v = y1v;
+                y1h = fh;
+                y1v = fv;
+                y1rh = frh;
+            }
+            // shift the y pipeline
+            ypa = {qb.hp, qb.zp, qb.unp, qb.utp};
+            fcya = hg * (qb.hm + qb.hp) * (qb.zp - qb.zm);
+            gs = gn;
+        }
+        a1q[0] = a1q[1]; a2q[0] = a2q[1]; a3q[0] = a3q[1];
+        a1q[1] = a1; a2q[1] = a2; a3q[1] = a3;
+        ra = rb;
+        rb = rc;
+    }
+
+    // FP64 budget slots, fixed order
+    const int blk = blockIdx.y * gridDim.x + blockIdx.x;
+    const bool edge = (blockIdx.x == 0 && P.bc[0] == SWOF_BC_OUTFLOW) ||
+                      (blockIdx.x == gridDim.x - 1 && P.bc[1] == SWOF_BC_OUTFLOW) ||
+                      (blockIdx.y == 0 && P.bc[2] == SWOF_BC_OUTFLOW) ||
+                      (blockIdx.y == gridDim.y - 1 && P.bc[3] == SWOF_BC_OUTFLOW);
+    if (edge && !P.no_budget) {
+        double s = block_sum_t(outacc, s_red);
+        if (t == 0) F.outflow_slots[blk] += 0.5 * ctl->dt * s;
+    }
+    if (STAGE == 2 && P.infiltration && !P.no_budget) {
+        double s = block_sum_t(infacc, s_red);
+        if (t == 0) F.infil_slots[blk] += s;
+    }
+    if (STAGE == 2 && P.fuse_lambda) {
+        lx = block_max(lx, s_redk[0]);
+        ly = block_max(ly, s_redk[1]);
+        if (t == 0) {
+            atomicMax(&F.ctl->lam_bits[0], key64(lx));
+            atomicMax(&F.ctl->lam_bits[1], key64(ly));
+        }
+    }
+    if (STAGE == 2 && P.check_cfl) {
+        k2x = block_max(k2x, s_redk[0]);
+        k2y = block_max(k2y, s_redk[1]);
+        if (t == 0) {
+            DevCtl *c = F.ctl;
+            atomicMax(&c->lam2_bits[0], key64(k2x));
+            atomicMax(&c->lam2_bits[1], key64(k2y));
+            __threadfence();
+            unsigned int nb = gridDim.x * gridDim.y;
+            if (atomicAdd(&c->done2, 1u) == nb - 1) {
+                __threadfence();
+                double lx = __longlong_as_double((long long)atomicAdd(&c->lam2_bits[0], 0ull));
+                double ly = __longlong_as_double((long long)atomicAdd(&c->lam2_bits[1], 0ull));
+                c->lam2_bits[0] = 0ull;
+                c->lam2_bits[1] = 0ull;
+                c->done2 = 0u;
+                if (c->dt * (lx / P.dx + ly / P.dy) > P.cfl) c->cfl_viol++;
+            }
+        }
+    }
+}
+
+}  // namespace swof

@@ -278,3 +278,36 @@ def test_fp32_valley_512_rel_l1():
     s.step(200)
     for a, b, name in zip(s.state(), o.state(), ("h", "qx", "qy")):
         assert rel_l1(a, b) <= 1e-4, (name, rel_l1(a, b))
+
+
+@pytest.mark.parametrize("shape", range(4))
+def test_fp64_every_tile_shape_bitwise(shape):
+    w = si.random_state(300, 150, seed=40 + shape, dry_frac=0.2)
+    w.bc = (1, 0, 0, 1)
+    o = oracle.Oracle.from_workload(w)
+    dts = o.step(12)
+    s = sw.Solver.from_workload(w, sw.FP64)
+    s.set_tile_shape(shape)
+    s.step(12)
+    assert np.array_equal(s.dt_history(), dts)
+    assert_state_equal(s, o)
+
+
+def test_autotune_leaves_state_time_and_budgets_alone(tmp_path):
+    w = si.random_state(257, 190, seed=5, dry_frac=0.2)
+    w.bc = (1, 1, 1, 1)
+    a = sw.Solver.from_workload(w, sw.FP64)
+    b = sw.Solver.from_workload(w, sw.FP64)
+    a.step(5)
+    b.step(5)
+    d0 = b.diagnostics()
+    cache = str(tmp_path / "tune.json")
+    rec = b.autotune(reps=2, cache=cache)
+    assert 0 <= rec["shape"] < len(sw.tile_shapes()) and not rec["cached"]
+    assert b.autotune(cache=cache)["cached"]
+    assert b.diagnostics() == d0
+    a.step(5)
+    b.step(5)
+    for x, y in zip(a.state(), b.state()):
+        assert np.array_equal(x, y)
+    assert a.diagnostics()["outflow"] == b.diagnostics()["outflow"]
