@@ -242,8 +242,8 @@ def measure(sw, torch, w, precision: str, steps: int, warmup: int, ws: int, cloc
     if tile >= 0 or not autotune:
         shape = max(tile, 0)
         s.set_tile_shape(shape)
-        ntx, rows = sw.tile_shapes()[shape]
-        tune = {"ntx": ntx, "rows": rows, "ms": None}
+        tune = {"shape": [shape, shape], "stage1": list(sw.tile_shapes()[shape]),
+                "stage2": list(sw.tile_shapes()[shape])}
     else:
         tune = s.autotune(reps=3, cache=os.path.join(ROOT, "paper_1307_4839_gb300", "_build", "autotune.json"))
     torch.cuda.synchronize()
@@ -268,7 +268,7 @@ def measure(sw, torch, w, precision: str, steps: int, warmup: int, ws: int, cloc
     t = s.timing()
     s.enable_timing(False)
     d = s.diagnostics()
-    d["tile"] = {"ntx": tune["ntx"], "rows": tune["rows"], "ms_per_shape": tune["ms"]}
+    d["tile"] = {k: tune[k] for k in ("stage1", "stage2", "ms_stage1", "ms_stage2") if k in tune}
     return ms, t, clk, d, s
 
 

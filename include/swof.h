@@ -205,14 +205,17 @@ SWOF_API int swof_use_graph(swof_ctx *ctx, int on);
 /* Stage-kernel tile shapes.  The stage kernels walk columns down the grid;
  * a shape is (threads per CTA along x, rows per CTA).  swof_tile_shapes
  * writes up to max shapes (ntx[k], rows[k]) and returns how many exist.
- * swof_set_tile_shape selects one for a context (results do not depend on
- * it).  swof_autotune times the stage-1 kernel of every shape `reps` times
- * on the context's current state (the state, time and budgets are left as
- * they are), selects the fastest, and writes the average milliseconds per
- * shape to ms (nullable, one entry per shape) and the choice to *best.
+ * swof_set_tile_shape(s) select the shape of both stages, or of stage 1 and
+ * stage 2 separately (results do not depend on it).  swof_autotune times
+ * each stage kernel with every shape `reps` times on the context's current
+ * state (stage 2 on scratch copies, which it allocates and frees: the
+ * state, time and budgets are left as they are), selects the fastest per
+ * stage, writes the average ms to ms (nullable; 2 x shapes entries, stage 1
+ * first) and the choices to best[0] (stage 1) and best[1] (stage 2).
  * Synchronises.  Not in the paper: a GB300 launch-shape choice. */
 SWOF_API int swof_tile_shapes(int *ntx, int *rows, int max);
 SWOF_API int swof_set_tile_shape(swof_ctx *ctx, int shape);
+SWOF_API int swof_set_tile_shapes(swof_ctx *ctx, int shape1, int shape2);
 SWOF_API int swof_autotune(swof_ctx *ctx, int reps, double *ms, int *best);
 
 /* Human-readable text for a status code (static storage). */

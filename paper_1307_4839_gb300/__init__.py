@@ -90,6 +90,7 @@ _SIGS = {
                                            ctypes.c_void_p]),
     "swof_tile_shapes": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     "swof_set_tile_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "swof_set_tile_shapes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "swof_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_int)]),
     "swof_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "swof_version": (ctypes.c_char_p, []),
@@ -286,8 +287,12 @@ class Solver:
     def use_graph(self, on=True):
         _check(load().swof_use_graph(self._ctx, int(bool(on))), "swof_use_graph")
 
-    def set_tile_shape(self, shape: int):
-        _check(load().swof_set_tile_shape(self._ctx, int(shape)), "swof_set_tile_shape")
+    def set_tile_shape(self, shape: int, shape2: int | None = None):
+        """Tile shape of both stage kernels, or of stage 1 and stage 2."""
+        if shape2 is None:
+            _check(load().swof_set_tile_shape(self._ctx, int(shape)), "swof_set_tile_shape")
+        else:
+            _check(load().swof_set_tile_shapes(self._ctx, int(shape), int(shape2)), "swof_set_tile_shapes")
 
     def autotune(self, reps: int = 5, cache: str | None = None, key: str | None = None) -> dict:
         """Pick the fastest stage-kernel tile shape for this grid and
@@ -303,14 +308,15 @@ class Solver:
             except (OSError, ValueError):
                 data = {}
         if key in data:
-            self.set_tile_shape(int(data[key]["shape"]))
+            self.set_tile_shape(int(data[key]["shape"][0]), int(data[key]["shape"][1]))
             return dict(data[key], cached=True)
         n = tile_shapes()
-        ms = (ctypes.c_double * len(n))()
-        best = ctypes.c_int()
-        _check(load().swof_autotune(self._ctx, int(reps), ms, ctypes.byref(best)), "swof_autotune")
-        rec = {"shape": best.value, "ntx": n[best.value][0], "rows": n[best.value][1],
-               "ms": [ms[k] for k in range(len(n))]}
+        ms = (ctypes.c_double * (2 * len(n)))()
+        best = (ctypes.c_int * 2)()
+        _check(load().swof_autotune(self._ctx, int(reps), ms, best), "swof_autotune")
+        rec = {"shape": [best[0], best[1]], "stage1": list(n[best[0]]), "stage2": list(n[best[1]]),
+               "ms_stage1": [ms[k] for k in range(len(n))],
+               "ms_stage2": [ms[len(n) + k] for k in range(len(n))]}
         if cache:
             data[key] = rec
             tmp = cache + ".tmp"

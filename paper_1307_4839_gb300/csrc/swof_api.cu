@@ -243,7 +243,7 @@ int invalidate_lambda(swof_ctx *c)
 int update_rings(swof_ctx *c)
 {
     const Params &P = c->P;
-    int w = swof::TILE_SHAPES[P.tile_cfg].ntx - 4, h = swof::TILE_SHAPES[P.tile_cfg].h;
+    int w = swof::TILE_SHAPES[P.tile_cfg2].ntx - 4, h = swof::TILE_SHAPES[P.tile_cfg2].h;
     std::vector<int> cols, rows;
     for (int i = 0; i < P.nx; ++i)
         if (i % w == 0 || i % w == w - 1 || i == P.nx - 1) cols.push_back(i);
@@ -686,50 +686,105 @@ int swof_tile_shapes(int *ntx, int *rows, int max)
 
 int swof_set_tile_shape(swof_ctx *c, int shape)
 {
-    if (!c || shape < 0 || shape >= swof::N_TILE_SHAPES) return SWOF_EINVAL;
-    if (c->P.tile_cfg == shape) return SWOF_OK;
-    c->P.tile_cfg = shape;
+    return swof_set_tile_shapes(c, shape, shape);
+}
+
+int swof_set_tile_shapes(swof_ctx *c, int shape1, int shape2)
+{
+    if (!c || shape1 < 0 || shape1 >= swof::N_TILE_SHAPES || shape2 < 0 || shape2 >= swof::N_TILE_SHAPES)
+        return SWOF_EINVAL;
+    c->P.tile_cfg = shape1;
+    c->gen++;
+    if (c->P.tile_cfg2 == shape2) return SWOF_OK;
+    c->P.tile_cfg2 = shape2;
     return update_rings(c);
 }
+
+}  // extern "C"
+
+namespace {
+
+// Average ms of `reps` launches of one stage kernel with shape k (after one
+// untimed launch).
+int time_stage(swof_ctx *c, const Params &P0, void *fields, int stage, int k, int reps, cudaEvent_t e0,
+               cudaEvent_t e1, double *out)
+{
+    Params P = P0;
+    P.tile_cfg = k;
+    P.tile_cfg2 = k;
+    auto launch = [&]() { return stage == 1 ? c->L->stage1(P, fields, c->stream) : c->L->stage2(P, fields, c->stream); };
+    if (launch()) return SWOF_ECUDA;
+    if (cudaEventRecord(e0, c->stream) != cudaSuccess) return SWOF_ECUDA;
+    for (int r = 0; r < reps; ++r)
+        if (launch()) return SWOF_ECUDA;
+    if (cudaEventRecord(e1, c->stream) != cudaSuccess) return SWOF_ECUDA;
+    float t = 0.0f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) return SWOF_ECUDA;
+    *out = (double)t / reps;
+    return SWOF_OK;
+}
+
+template <typename T>
+int autotune_t(swof_ctx *c, Fields<T> &F, int reps, double *ms, int *best)
+{
+    // Stage 1 only reads U^n and writes U*: it is timed in place.  Stage 2
+    // updates U^n and V_inf in place, so it is timed on scratch copies.
+    Params P = c->P;
+    P.no_budget = 1;
+    P.check_cfl = 0;
+    size_t n = padded_elems(c);
+    std::vector<void *> scratch;
+    int st = SWOF_OK;
+    Fields<T> G = F;
+    for (T **dst : {&G.h, &G.qx, &G.qy, &G.vinf}) {
+        void *p = nullptr;
+        if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) {
+            st = SWOF_ENOMEM;
+            break;
+        }
+        scratch.push_back(p);
+        const T *src = (dst == &G.h) ? F.h : (dst == &G.qx) ? F.qx : (dst == &G.qy) ? F.qy : F.vinf;
+        if (cudaMemcpyAsync(p, src, n * sizeof(T), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+            st = SWOF_ECUDA;
+        *dst = static_cast<T *>(p);
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!st && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) st = SWOF_ECUDA;
+    int bk[2] = {0, 0};
+    for (int stage = 1; stage <= 2 && !st; ++stage) {
+        double bms = INFINITY;
+        for (int k = 0; k < swof::N_TILE_SHAPES && !st; ++k) {
+            double m = 0.0;
+            st = time_stage(c, P, stage == 1 ? (void *)&F : (void *)&G, stage, k, reps, e0, e1, &m);
+            if (st) break;
+            if (ms) ms[(stage - 1) * swof::N_TILE_SHAPES + k] = m;
+            if (m < bms) {
+                bms = m;
+                bk[stage - 1] = k;
+            }
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(c->stream);
+    for (void *p : scratch) cudaFree(p);
+    if (st) return st;
+    best[0] = bk[0];
+    best[1] = bk[1];
+    // the timed stage-2 launches added to the wave-speed words: start over
+    st = swof_set_tile_shapes(c, bk[0], bk[1]);
+    return st ? st : invalidate_lambda(c);
+}
+
+}  // namespace
+
+extern "C" {
 
 int swof_autotune(swof_ctx *c, int reps, double *ms, int *best)
 {
     if (!c || reps < 1 || !best) return SWOF_EINVAL;
-    Params P = c->P;
-    P.no_budget = 1;
-    cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess) return SWOF_ECUDA;
-    if (cudaEventCreate(&e1) != cudaSuccess) {
-        cudaEventDestroy(e0);
-        return SWOF_ECUDA;
-    }
-    int st = SWOF_OK, bk = 0;
-    double bms = INFINITY;
-    for (int k = 0; k < swof::N_TILE_SHAPES && !st; ++k) {
-        P.tile_cfg = k;
-        // one untimed launch (first-use cost), then `reps` timed ones
-        if (c->L->stage1(P, c->fields(), c->stream)) st = SWOF_ECUDA;
-        cudaEventRecord(e0, c->stream);
-        for (int r = 0; r < reps && !st; ++r)
-            if (c->L->stage1(P, c->fields(), c->stream)) st = SWOF_ECUDA;
-        cudaEventRecord(e1, c->stream);
-        float t = 0.0f;
-        if (!st && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess) {
-            double m = (double)t / reps;
-            if (ms) ms[k] = m;
-            if (m < bms) {
-                bms = m;
-                bk = k;
-            }
-        } else {
-            st = SWOF_ECUDA;
-        }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (st) return st;
-    *best = bk;
-    return swof_set_tile_shape(c, bk);
+    return c->prec == SWOF_FP64 ? autotune_t<double>(c, c->f64, reps, ms, best)
+                                : autotune_t<float>(c, c->f32, reps, ms, best);
 }
 
 const char *swof_strerror(int code)

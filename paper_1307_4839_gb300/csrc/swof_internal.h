@@ -49,7 +49,8 @@ struct Params {
     double area;               // unused by the arithmetic; dx*dy
     // FP32 copies of the scalars the FP32 kernels use (no FP64 on their path)
     float fg, fh_dry, fn2, fpsi, fdtheta, fks;
-    int tile_cfg;              // stage-kernel shape, index into the sweep shapes
+    int tile_cfg;              // stage-1 kernel shape, index into the sweep shapes
+    int tile_cfg2;             // stage-2 kernel shape
     int no_budget;             // 1: stage kernels leave the budget slots alone (timing runs)
     int fuse_lambda;           // 1: stage 2 adds the wave speeds of U^{n+1} of its tile interiors
 };

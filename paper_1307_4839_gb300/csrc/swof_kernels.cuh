@@ -92,7 +92,7 @@ __device__ __forceinline__ Scal<T> scal(const Params &P)
 //  differ -> 0, else the smaller magnitude); this returns exactly the value
 //  of the comparison-based definition (up to the sign of a zero result) and
 //  keeps the work off GB300's narrow FP64 pipe.
-//  FP32: branch-free, a*b > 0 selects min(|a|,|b|) with the sign of a.
+//  FP32: the same on 32-bit patterns.
 __device__ __forceinline__ double minmod(double a, double b)
 {
     long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
@@ -102,7 +102,10 @@ __device__ __forceinline__ double minmod(double a, double b)
 }
 __device__ __forceinline__ float minmod(float a, float b)
 {
-    return (a * b > 0.0f) ? copysignf(fminf(fabsf(a), fabsf(b)), a) : 0.0f;
+    int ia = __float_as_int(a), ib = __float_as_int(b);
+    if ((ia ^ ib) < 0) return 0.0f;
+    int ma = ia & 0x7fffffff, mb = ib & 0x7fffffff;
+    return ma <= mb ? a : b;
 }
 
 // max(0, x) (the hydrostatic cut, Sec. 3.1); FP64 by the sign bit.
@@ -726,7 +729,7 @@ int launch_stage_t(const Params &P, void *f, void *stream)
 {
     const Fields<T> &F = *static_cast<const Fields<T> *>(f);
     cudaStream_t s = (cudaStream_t)stream;
-    switch (P.tile_cfg) {
+    switch (STAGE == 1 ? P.tile_cfg : P.tile_cfg2) {
     case 1: return launch_sweep<T, STAGE, 128, 64>(P, F, s);
     case 2: return launch_sweep<T, STAGE, 256, 32>(P, F, s);
     case 3: return launch_sweep<T, STAGE, 64, 64>(P, F, s);

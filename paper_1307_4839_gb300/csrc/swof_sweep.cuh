@@ -38,6 +38,9 @@ __device__ __forceinline__ Cell<T> make_cell(T h, T qx, T qy, T zy, T hdry)
 }
 
 template <typename T, int STAGE, int NTX, int H>
+// (No minimum-blocks hint: capping registers that way made the compiler
+// route work through the FP64 pipe, which on GB300 costs more than the
+// occupancy it buys.)
 __global__ void __launch_bounds__(NTX) k_sweep(Params P, Fields<T> F)
 {
     constexpr bool fp64 = std::is_same<T, double>::value;
@@ -103,8 +106,9 @@ __global__ void __launch_bounds__(NTX) k_sweep(Params P, Fields<T> F)
     // per-cell data of the row updated in the next iteration, fetched one
     // iteration ahead: U^n (stage 2), n^2 map, V_inf and K_s
     T un_h = T(0), un_qx = T(0), un_qy = T(0), pn2 = C.n2, pvi = T(0), pks = C.ks;
+    const bool want_prefetch = STAGE == 2 || F.n2map != nullptr;
     auto prefetch = [&](int ro) {
-        if (!(out_col && ro >= j0 && ro < j0 + H && ro < P.ny)) return;
+        if (!want_prefetch || !(out_col && ro >= j0 && ro < j0 + H && ro < P.ny)) return;
         size_t o = pidx(P, gi, ro);
         if (STAGE == 2) {
             un_h = F.h[o];
