@@ -218,6 +218,52 @@ SWOF_API int swof_set_tile_shape(swof_ctx *ctx, int shape);
 SWOF_API int swof_set_tile_shapes(swof_ctx *ctx, int shape1, int shape2);
 SWOF_API int swof_autotune(swof_ctx *ctx, int reps, double *ms, int *best);
 
+/* ---- batched ensemble ---------------------------------------------------
+ * A batch of independent grids of uneven sizes, each with its own dt (the
+ * paper's scheme per member, Sec. 2-3), advanced together by ONE persistent
+ * kernel launch per swof_ensemble_step call, replayed from a CUDA graph.
+ * The launch works through a queue of (step, phase, member, tile) items;
+ * an item waits (bounded) only for earlier phases of its own member, so
+ * members never wait on each other.  Each member is an ordinary context
+ * (swof_ensemble_member) whose results equal what its own swof_step would
+ * give, bit for bit.  Not in the paper: the GB300 batching of its method. */
+typedef struct swof_ens swof_ens;
+
+typedef struct swof_scenario {
+    int nx, ny;                    /* grid (>= 2 x 2) */
+    double dx, dy;
+    const double *z;               /* [ny][nx] host, copied */
+    const double *h, *hu, *hv;     /* initial state [ny][nx] host, copied */
+    double manning_n;              /* > 0: Manning friction with this n */
+    double rain_rate, rain_t_on, rain_t_off;
+    int bc[4];                     /* W, E, S, N */
+} swof_scenario;
+
+/* Create `count` members from specs; every other parameter (precision, g,
+ * cfl, h_dry, dt_max, t_end, infiltration off...) comes from *common.
+ * Errors: as swof_create / swof_set_state. */
+SWOF_API int swof_ensemble_create(int count, const swof_scenario *specs, const swof_params *common,
+                                  swof_ens **out);
+SWOF_API void swof_ensemble_destroy(swof_ens *e);   /* NULL-safe; destroys the members */
+SWOF_API int swof_ensemble_size(const swof_ens *e);
+/* Borrow member k's context (state, diagnostics, dt history; owned by e). */
+SWOF_API int swof_ensemble_member(swof_ens *e, int k, swof_ctx **ctx);
+/* Advance every member by n steps in one launch.  Asynchronous when status
+ * is NULL; otherwise synchronises and reports SWOF_OK, a member's latched
+ * status, or SWOF_ETIMEOUT when a bounded wait ran out (latched: later
+ * calls return it). */
+SWOF_API int swof_ensemble_step(swof_ens *e, int n, int *status);
+/* Kernel shapes the ensemble launch can use, the choice, and a tuner that
+ * times `steps` steps with each shape and restores every member afterwards
+ * (ms: one entry per shape, nullable). */
+SWOF_API int swof_ensemble_shapes(int *ntx, int *rows, int max);
+SWOF_API int swof_ensemble_set_shape(swof_ens *e, int shape);
+SWOF_API int swof_ensemble_autotune(swof_ens *e, int steps, double *ms, int *best);
+/* Bound on the polls of each wait (default 4M, about a second), and a test
+ * hook: block_member >= 0 makes that member's waits impossible so the
+ * bound is exercised (-1: off). */
+SWOF_API int swof_ensemble_set_wait_limit(swof_ens *e, long long polls, int block_member);
+
 /* Human-readable text for a status code (static storage). */
 SWOF_API const char *swof_strerror(int code);
 

@@ -55,6 +55,13 @@ class SwofDiag(ctypes.Structure):
                 ("min_h", ctypes.c_double), ("cfl_viol", ctypes.c_longlong)]
 
 
+class SwofScenario(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+                ("z", _D), ("h", _D), ("hu", _D), ("hv", _D), ("manning_n", ctypes.c_double),
+                ("rain_rate", ctypes.c_double), ("rain_t_on", ctypes.c_double),
+                ("rain_t_off", ctypes.c_double), ("bc", ctypes.c_int * 4)]
+
+
 class SwofError(RuntimeError):
     def __init__(self, code: int, what: str = ""):
         self.code = code
@@ -92,6 +99,16 @@ _SIGS = {
     "swof_set_tile_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "swof_set_tile_shapes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "swof_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_int)]),
+    "swof_ensemble_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(SwofScenario),
+                                            ctypes.POINTER(SwofParams), ctypes.POINTER(ctypes.c_void_p)]),
+    "swof_ensemble_destroy": (None, [ctypes.c_void_p]),
+    "swof_ensemble_size": (ctypes.c_int, [ctypes.c_void_p]),
+    "swof_ensemble_member": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "swof_ensemble_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "swof_ensemble_shapes": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+    "swof_ensemble_set_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "swof_ensemble_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_int)]),
+    "swof_ensemble_set_wait_limit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int]),
     "swof_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "swof_version": (ctypes.c_char_p, []),
 }
@@ -343,3 +360,95 @@ def _gpu_name() -> str:
         return torch.cuda.get_device_name()
     except Exception:
         return "gpu"
+
+
+class _Member(Solver):
+    """A member context borrowed from an Ensemble (not destroyed here)."""
+
+    def __init__(self, ctx, nx, ny, precision):
+        self._ctx = ctx
+        self.nx, self.ny, self.precision = nx, ny, precision
+
+    def close(self):
+        self._ctx = None
+
+
+class Ensemble:
+    """A batch of independent grids advanced by one persistent kernel.
+
+    `workloads` are swof_inputs.Workload objects (z, initial state, Manning
+    n, rain, boundaries are taken from each); the remaining parameters are
+    common to all members."""
+
+    def __init__(self, workloads, precision=FP32, cfl=0.5, h_dry=1e-6, dt_max=0.1, t_end=1e30,
+                 stream=None):
+        L = load()
+        self._e = None
+        self._keep = []
+        specs = (SwofScenario * len(workloads))()
+        for k, w in enumerate(workloads):
+            arrs = [_f64(a) for a in (w.z, w.h, w.qx, w.qy)]
+            self._keep.extend(arrs)
+            sc = specs[k]
+            sc.nx, sc.ny, sc.dx, sc.dy = w.nx, w.ny, w.dx, w.dy
+            sc.z, sc.h, sc.hu, sc.hv = (_ptr(a) for a in arrs)
+            sc.manning_n = w.manning_n if w.friction else 0.0
+            sc.rain_rate, sc.rain_t_on, sc.rain_t_off = w.rain_rate, w.rain_t_on, w.rain_t_off
+            for b in range(4):
+                sc.bc[b] = int(w.bc[b])
+        p = default_params(precision=int(precision), cfl=cfl, h_dry=h_dry, dt_max=dt_max, t_end=t_end)
+        p.stream = stream
+        e = ctypes.c_void_p()
+        _check(L.swof_ensemble_create(len(workloads), specs, ctypes.byref(p), ctypes.byref(e)),
+               "swof_ensemble_create")
+        self._e = e
+        self._keep = None
+        self.precision = int(precision)
+        self.sizes = [(w.nx, w.ny) for w in workloads]
+        self.cells = sum(nx * ny for nx, ny in self.sizes)
+
+    def close(self):
+        if self._e:
+            load().swof_ensemble_destroy(self._e)
+            self._e = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __len__(self):
+        return len(self.sizes)
+
+    def member(self, k: int) -> Solver:
+        c = ctypes.c_void_p()
+        _check(load().swof_ensemble_member(self._e, int(k), ctypes.byref(c)), "swof_ensemble_member")
+        nx, ny = self.sizes[k]
+        return _Member(c, nx, ny, self.precision)
+
+    def step(self, n: int = 1, sync: bool = True) -> int | None:
+        if not sync:
+            _check(load().swof_ensemble_step(self._e, int(n), None), "swof_ensemble_step")
+            return None
+        st = ctypes.c_int()
+        _check(load().swof_ensemble_step(self._e, int(n), ctypes.byref(st)), "swof_ensemble_step")
+        return st.value
+
+    def set_shape(self, shape: int):
+        _check(load().swof_ensemble_set_shape(self._e, int(shape)), "swof_ensemble_set_shape")
+
+    def autotune(self, steps: int = 2) -> dict:
+        L = load()
+        n = L.swof_ensemble_shapes(None, None, 0)
+        ms = (ctypes.c_double * n)()
+        best = ctypes.c_int()
+        _check(L.swof_ensemble_autotune(self._e, int(steps), ms, ctypes.byref(best)), "swof_ensemble_autotune")
+        a = (ctypes.c_int * n)()
+        b = (ctypes.c_int * n)()
+        L.swof_ensemble_shapes(a, b, n)
+        return {"shape": best.value, "ntx": a[best.value], "rows": b[best.value], "ms": [ms[k] for k in range(n)]}
+
+    def set_wait_limit(self, polls: int, block_member: int = -1):
+        _check(load().swof_ensemble_set_wait_limit(self._e, int(polls), int(block_member)),
+               "swof_ensemble_set_wait_limit")

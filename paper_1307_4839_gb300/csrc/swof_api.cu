@@ -11,48 +11,7 @@
 #include <new>
 #include <vector>
 
-#include "swof_internal.h"
-
-using swof::DevCtl;
-using swof::Fields;
-using swof::Params;
-
-struct swof_ctx {
-    int device = 0;
-    int prec = SWOF_FP64;
-    size_t esize = 8;
-    Params P{};
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    const swof::Launch *L = nullptr;
-    Fields<double> f64{};
-    Fields<float> f32{};
-    std::vector<void *> allocs;
-    DevCtl *ctl = nullptr;
-    double *d_red = nullptr;
-    int nslots = 0;
-    double *dt_seq = nullptr;
-    int dt_seq_n = 0;
-    double *dt_hist = nullptr;
-    long long dt_cap = 0;
-    long long host_steps = 0;      // steps enqueued so far
-    // CUDA graph of an n-step sequence
-    bool use_graph = false;
-    cudaGraphExec_t gexec = nullptr;
-    int graph_n = 0;
-    unsigned gen = 1, graph_gen = 0;
-    // wave speeds: after a fused stage 2 the next step needs only the ring
-    bool lam_valid = false;
-    bool graph_lam = false;
-    int *d_ring_cols = nullptr, *d_ring_rows = nullptr;
-    // per-kernel timing of the last swof_step call
-    bool timing = false;
-    std::vector<cudaEvent_t> ev;
-    int ev_used = 0;
-    int launches_last = 0;
-
-    void *fields() { return prec == SWOF_FP64 ? (void *)&f64 : (void *)&f32; }
-};
+#include "swof_ctx.h"
 
 namespace {
 
@@ -263,6 +222,13 @@ int update_rings(swof_ctx *c)
     int st = cuda_err(e);
     return st ? st : invalidate_lambda(c);
 }
+
+}  // namespace
+
+int swof_ctx_invalidate_lambda(swof_ctx *c) { return invalidate_lambda(c); }
+int swof_ctx_ensure_hist(swof_ctx *c, long long more) { return ensure_hist(c, more); }
+
+namespace {
 
 int enqueue_steps(swof_ctx *c, int n)
 {

@@ -53,6 +53,7 @@ struct Params {
     int tile_cfg2;             // stage-2 kernel shape
     int no_budget;             // 1: stage kernels leave the budget slots alone (timing runs)
     int fuse_lambda;           // 1: stage 2 adds the wave speeds of U^{n+1} of its tile interiors
+    int lam_partial;           // 1: the wave-speed kernel only reduces (no dt control)
 };
 
 // Stage-kernel shapes (threads per CTA along x, rows per CTA); the last two

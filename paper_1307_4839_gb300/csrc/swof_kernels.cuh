@@ -477,6 +477,7 @@ __global__ void __launch_bounds__(NT) k_lambda(Params P, Fields<T> F)
     if (tid == 0) {
         atomicMax(&ctl->lam_bits[0], key64(kx));
         atomicMax(&ctl->lam_bits[1], key64(ky));
+        if (P.lam_partial) return;
         __threadfence();
         unsigned int ticket = atomicAdd(&ctl->done, 1u);
         if (ticket == gridDim.x - 1) control(P, F);

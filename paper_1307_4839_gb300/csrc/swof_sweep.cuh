@@ -37,29 +37,39 @@ __device__ __forceinline__ Cell<T> make_cell(T h, T qx, T qy, T zy, T hdry)
     return c;
 }
 
+template <typename T, int NTX>
+struct SweepSmem {
+    using K = decltype(speed_key(T(0)));
+    V4<T> st[NTX];        // {h, u, v, 1/h} of the current row
+    T zx[NTX];            // FP64: z; FP32: dz_x
+    V4<T> m[NTX];         // x-recon minus side {h, z, u, v}
+    V4<T> f[NTX];         // flux through the cell's east face
+    V4<T> nw[2][NTX];     // U^{n+1} {h, u, v, 1/h} of the finished row
+    double red[NTX / 32];
+    K redk[2][NTX / 32];
+};
+
+// One stage over the tile (bx, by) of a (gdx x gdy) tiling; the kernel
+// below maps it to its block index, the ensemble kernel to a queue item.
 template <typename T, int STAGE, int NTX, int H>
-// (No minimum-blocks hint: capping registers that way made the compiler
-// route work through the FP64 pipe, which on GB300 costs more than the
-// occupancy it buys.)
-__global__ void __launch_bounds__(NTX) k_sweep(Params P, Fields<T> F)
+__device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, int bx, int by, int gdx, int gdy,
+                                           SweepSmem<T, NTX> &S)
 {
     constexpr bool fp64 = std::is_same<T, double>::value;
     constexpr int W = NTX - 4;
     using K = decltype(speed_key(T(0)));
-    __shared__ V4<T> s_st[NTX];   // {h, u, v, 1/h} of the current row
-    __shared__ T s_zx[NTX];       // FP64: z; FP32: dz_x
-    __shared__ V4<T> s_m[NTX];    // x-recon minus side {h, z, u, v}
-    __shared__ V4<T> s_f[NTX];    // flux through the cell's east face
-    __shared__ V4<T> s_nw[2][NTX]; // U^{n+1} {h, u, v, 1/h} of the finished row
-    __shared__ double s_red[NTX / 32];
-    __shared__ K s_redk[2][NTX / 32];
+    V4<T> *s_st = S.st;
+    T *s_zx = S.zx;
+    V4<T> *s_m = S.m;
+    V4<T> *s_f = S.f;
+    double *s_red = S.red;
 
     const DevCtl *ctl = F.ctl;
     if (ctl->status) return;
     const Scal<T> C = scal<T>(P);
     const int t = threadIdx.x;
-    const int gi = blockIdx.x * W - 2 + t;
-    const int j0 = blockIdx.y * H;
+    const int gi = bx * W - 2 + t;
+    const int j0 = by * H;
     const bool col_in = gi <= P.nx + 1;
     const bool out_col = t >= 2 && t < NTX - 2 && gi < P.nx;
     const T *hin = (STAGE == 1) ? F.h : F.h1;
@@ -252,7 +262,7 @@ __global__ void __launch_bounds__(NTX) k_sweep(Params P, Fields<T> F)
             // this CTA owns; the tile-edge columns/rows are left to the ring
             // kernel of the next step
             if (STAGE == 2 && P.fuse_lambda && k >= 4) {       // uniform over the CTA
-                V4<T> *buf = s_nw[k & 1];
+                V4<T> *buf = S.nw[k & 1];
                 buf[t] = {fh, fu, fv, frh};
                 __syncthreads();
                 if (out_col && ro < P.ny) {
@@ -282,11 +292,9 @@ __global__ void __launch_bounds__(NTX) k_sweep(Params P, Fields<T> F)
     }
 
     // FP64 budget slots, fixed order
-    const int blk = blockIdx.y * gridDim.x + blockIdx.x;
-    const bool edge = (blockIdx.x == 0 && P.bc[0] == SWOF_BC_OUTFLOW) ||
-                      (blockIdx.x == gridDim.x - 1 && P.bc[1] == SWOF_BC_OUTFLOW) ||
-                      (blockIdx.y == 0 && P.bc[2] == SWOF_BC_OUTFLOW) ||
-                      (blockIdx.y == gridDim.y - 1 && P.bc[3] == SWOF_BC_OUTFLOW);
+    const int blk = by * gdx + bx;
+    const bool edge = (bx == 0 && P.bc[0] == SWOF_BC_OUTFLOW) || (bx == gdx - 1 && P.bc[1] == SWOF_BC_OUTFLOW) ||
+                      (by == 0 && P.bc[2] == SWOF_BC_OUTFLOW) || (by == gdy - 1 && P.bc[3] == SWOF_BC_OUTFLOW);
     if (edge && !P.no_budget) {
         double s = block_sum_t(outacc, s_red);
         if (t == 0) F.outflow_slots[blk] += 0.5 * ctl->dt * s;
@@ -296,22 +304,22 @@ __global__ void __launch_bounds__(NTX) k_sweep(Params P, Fields<T> F)
         if (t == 0) F.infil_slots[blk] += s;
     }
     if (STAGE == 2 && P.fuse_lambda) {
-        lx = block_max(lx, s_redk[0]);
-        ly = block_max(ly, s_redk[1]);
+        lx = block_max(lx, S.redk[0]);
+        ly = block_max(ly, S.redk[1]);
         if (t == 0) {
             atomicMax(&F.ctl->lam_bits[0], key64(lx));
             atomicMax(&F.ctl->lam_bits[1], key64(ly));
         }
     }
     if (STAGE == 2 && P.check_cfl) {
-        k2x = block_max(k2x, s_redk[0]);
-        k2y = block_max(k2y, s_redk[1]);
+        k2x = block_max(k2x, S.redk[0]);
+        k2y = block_max(k2y, S.redk[1]);
         if (t == 0) {
             DevCtl *c = F.ctl;
             atomicMax(&c->lam2_bits[0], key64(k2x));
             atomicMax(&c->lam2_bits[1], key64(k2y));
             __threadfence();
-            unsigned int nb = gridDim.x * gridDim.y;
+            unsigned int nb = (unsigned int)(gdx * gdy);
             if (atomicAdd(&c->done2, 1u) == nb - 1) {
                 __threadfence();
                 double lx = __longlong_as_double((long long)atomicAdd(&c->lam2_bits[0], 0ull));
@@ -323,6 +331,16 @@ __global__ void __launch_bounds__(NTX) k_sweep(Params P, Fields<T> F)
             }
         }
     }
+}
+
+// (No minimum-blocks hint: capping registers that way made the compiler
+// route work through the FP64 pipe, which on GB300 costs more than the
+// occupancy it buys.)
+template <typename T, int STAGE, int NTX, int H>
+__global__ void __launch_bounds__(NTX) k_sweep(Params P, Fields<T> F)
+{
+    __shared__ SweepSmem<T, NTX> S;
+    sweep_tile<T, STAGE, NTX, H>(P, F, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y, S);
 }
 
 }  // namespace swof

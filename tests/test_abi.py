@@ -57,6 +57,7 @@ int main(void) {
          offsetof(swof_params, dt_fixed), offsetof(swof_params, stream));
   printf("%zu %zu\\n", sizeof(swof_step_info), offsetof(swof_step_info, status));
   printf("%zu %zu %zu\\n", sizeof(swof_diag), offsetof(swof_diag, min_h), offsetof(swof_diag, cfl_viol));
+  printf("%zu %zu %zu\\n", sizeof(swof_scenario), offsetof(swof_scenario, manning_n), offsetof(swof_scenario, bc));
   return 0;
 }
 """)
@@ -69,6 +70,7 @@ int main(void) {
                        P.dt_fixed.offset, P.stream.offset]
     assert vals[1] == [ctypes.sizeof(sw.SwofStepInfo), sw.SwofStepInfo.status.offset]
     assert vals[2] == [ctypes.sizeof(sw.SwofDiag), sw.SwofDiag.min_h.offset, sw.SwofDiag.cfl_viol.offset]
+    assert vals[3] == [ctypes.sizeof(sw.SwofScenario), sw.SwofScenario.manning_n.offset, sw.SwofScenario.bc.offset]
 
 
 def test_host_only_calls(lib):

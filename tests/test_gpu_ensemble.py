@@ -1,0 +1,127 @@
+"""Batched ensemble (one persistent launch over many grids) vs its members
+stepped one by one and vs the FP64 oracle (needs a GPU).
+
+FP64 members are compiled without contraction, so the ensemble must equal
+both the single-grid path and the oracle bit for bit.  FP32 members may be
+contracted differently in the two kernels (the arithmetic is inlined in
+different places), so they are compared to rounding.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1307_4839_gb300 as sw
+import swof_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+SIDES = [32, 48, 64, 96, 130, 160, 40, 72]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    assert torch.cuda.is_available()
+    sw.build()
+    sw.load()
+    oracle.build()
+
+
+def members(seed=4, sides=SIDES):
+    rng = np.random.default_rng(seed)
+    out = []
+    for k, n in enumerate(sides):
+        spec = si.Scenario(side=n, reservoir=float(rng.uniform(5, 40)), manning_n=float(rng.uniform(0.02, 0.06)),
+                           rain_mm_h=float(rng.uniform(0, 80)), seed=500 + k)
+        out.append(si.ensemble_member(spec))
+    return out
+
+
+def test_fp64_ensemble_equals_members_and_oracle():
+    ws = members()
+    ens = sw.Ensemble(ws, precision=sw.FP64)
+    assert ens.step(25) == 0
+    for k, w in enumerate(ws):
+        m = ens.member(k)
+        solo = sw.Solver.from_workload(w, sw.FP64)
+        solo.step(25)
+        for a, b in zip(m.state(), solo.state()):
+            assert np.array_equal(a, b), k
+        assert np.array_equal(m.dt_history(), solo.dt_history()), k
+        if k in (0, 4, 5):
+            o = oracle.Oracle.from_workload(w)
+            dts = o.step(25)
+            assert np.array_equal(m.dt_history(), dts), k
+            for a, b in zip(m.state(), o.state()):
+                assert np.array_equal(a, b), k
+
+
+def test_fp32_ensemble_matches_members_and_graph_replay():
+    ws = members(seed=9)
+    ens = sw.Ensemble(ws, precision=sw.FP32)
+    for _ in range(3):
+        assert ens.step(10) == 0       # the second and third calls replay the graph
+    for k, w in enumerate(ws):
+        m = ens.member(k)
+        solo = sw.Solver.from_workload(w, sw.FP32)
+        solo.step(30)
+        d1, d2 = m.diagnostics(), solo.diagnostics()
+        assert d1["steps"] == d2["steps"] == 30
+        assert abs(d1["t"] - d2["t"]) <= 1e-6 * d2["t"]
+        for a, b in zip(m.state(), solo.state()):
+            scale = max(np.max(np.abs(b)), 1e-30)
+            assert np.max(np.abs(a - b)) / scale <= 1e-4, k
+
+
+def test_ensemble_autotune_restores_members():
+    ws = members(seed=11, sides=[64, 130, 96])
+    a = sw.Ensemble(ws, precision=sw.FP64)
+    b = sw.Ensemble(ws, precision=sw.FP64)
+    a.step(5)
+    b.step(5)
+    rec = b.autotune(steps=2)
+    assert rec["shape"] in (0, 1)
+    a.set_shape(rec["shape"])
+    a.step(7)
+    b.step(7)
+    for k in range(len(ws)):
+        for x, y in zip(a.member(k).state(), b.member(k).state()):
+            assert np.array_equal(x, y)
+        assert a.member(k).diagnostics() == b.member(k).diagnostics()
+
+
+def test_ensemble_bounded_wait_reports_timeout():
+    """A member whose waits can never succeed (test hook): the bounded wait
+    runs out, every CTA stops, and the host reads SWOF_ETIMEOUT."""
+    ws = members(seed=13, sides=[48, 64, 80])
+    ens = sw.Ensemble(ws, precision=sw.FP32)
+    assert ens.step(2) == 0
+    ens.set_wait_limit(2000, block_member=1)
+    with pytest.raises(sw.SwofError) as e:
+        ens.step(3)
+    assert e.value.code == sw.ETIMEOUT
+    with pytest.raises(sw.SwofError):
+        ens.step(1)                     # latched
+    # the context is still usable: an unrelated solver runs fine
+    s = sw.Solver.from_workload(ws[0], sw.FP32)
+    assert s.step(3).status == 0
+
+
+def test_fp32_ensemble_members_against_fp64_oracle():
+    """FP32 bulk members with the oracle's dt replayed: relative L1 of
+    (h, hu, hv) per member after 60 steps (reported; bound 1e-5 on h)."""
+    ws = members(seed=21, sides=[64, 96, 130, 48])
+    ens = sw.Ensemble(ws, precision=sw.FP32)
+    refs = []
+    for k, w in enumerate(ws):
+        o = oracle.Oracle.from_workload(w)
+        dts = o.step(60)
+        ens.member(k).set_dt_sequence(dts)
+        refs.append(o.state())
+    assert ens.step(60) == 0
+    for k in range(len(ws)):
+        got = ens.member(k).state()
+        errs = [np.sum(np.abs(a - b)) / max(np.sum(np.abs(b)), 1e-30) for a, b in zip(got, refs[k])]
+        print(f"member {k} ({ws[k].nx}^2): rel L1 h {errs[0]:.2e} hu {errs[1]:.2e} hv {errs[2]:.2e}")
+        assert errs[0] <= 1e-5, errs
+        assert errs[1] <= 1e-4 and errs[2] <= 1e-4, errs
