@@ -264,6 +264,67 @@ SWOF_API int swof_ensemble_autotune(swof_ens *e, int steps, double *ms, int *bes
  * bound is exercised (-1: off). */
 SWOF_API int swof_ensemble_set_wait_limit(swof_ens *e, long long polls, int block_member);
 
+/* ---- tensor-core building block ------------------------------------------
+ * C[M x N] (fp32, row stride ldc) = A[M x K] . B[N x K]^T (+ bias[N]) with
+ * A, B row-major bf16 device arrays (K contiguous), on the tcgen05 tensor
+ * cores with FP32 accumulation in tensor memory.  N in {16, 32, 64, 128,
+ * 256}, K a multiple of 64, any M.  *err (device int) is set to 1 if a
+ * bounded wait inside the kernel ran out.  Enqueued on stream.  Not in the
+ * paper: the GEMM of the learned surrogate's layers. */
+SWOF_API int swof_gemm_bf16_nt(const void *A, const void *B, float *C, const float *bias, int M, int N, int K,
+                               int ldc, int *err, void *stream);
+
+/* ---- learned surrogate ---------------------------------------------------
+ * A 4-level convolutional U-Net on coarsened fields (base width `base`,
+ * 3x3 convolutions with GELU, 2x2 average pooling, 2x2 stride-2 transposed
+ * convolutions, skip concatenations, a 1x1 output convolution), trained
+ * and run on the tcgen05 tensor cores: BF16 weights and activations, FP32
+ * accumulation, FP32 master weights, gradients and AdamW moments.  It maps
+ * a coarse state (h, hu, hv, z) to the state a fixed number of solver steps
+ * later; the plain solver is its fallback and the judge of its error.  Not
+ * in the paper: the learned part built around its method.
+ *
+ * Memory is allocated at creation for batches up to max_batch of H x W
+ * (H, W multiples of 8, >= 16).  base in {16, 32, 48, 64}; in_ch, out_ch <= 16.
+ * Weights are Kaiming-normal from `seed`.  Parameters are one flat FP32
+ * array: each layer's weights as [columns][Kp] rows (K = taps x padded
+ * input channels, zero-padded to a multiple of 64), then all biases;
+ * swof_unet_layout describes layer `layer` in info[9] = {kind (0 3x3,
+ * 1 1x1, 2 transposed 2x2), cin, cin_padded, cout, columns, Kp, weight
+ * offset, bias offset, gelu} and returns the number of layers. */
+typedef struct swof_unet swof_unet;
+SWOF_API int swof_unet_create(int base, int in_ch, int out_ch, int H, int W, int max_batch,
+                              unsigned long long seed, swof_unet **out);
+SWOF_API void swof_unet_destroy(swof_unet *u);
+SWOF_API long long swof_unet_param_count(const swof_unet *u);
+SWOF_API int swof_unet_layout(const swof_unet *u, int layer, int *info);
+SWOF_API int swof_unet_get_params(swof_unet *u, float *host);
+SWOF_API int swof_unet_set_params(swof_unet *u, const float *host);
+SWOF_API int swof_unet_get_grads(swof_unet *u, float *host);
+/* Input normalisation (x - mean) / scale_in per input channel and output
+ * scale: the network predicts (next - in) / scale_out. */
+SWOF_API int swof_unet_set_norm(swof_unet *u, const float *mean, const float *scale_in, const float *scale_out);
+/* Raw network: x bf16 [B*H*W][16] NHWC device -> y fp32 [B*H*W][16]. */
+SWOF_API int swof_unet_forward_raw(swof_unet *u, const void *x, int B, float *y, void *stream);
+/* Mean-squared-error gradients (no update) for raw x and targets tgt fp32
+ * [B*H*W][out_ch]; synchronises; *loss_host = sum of squared errors, or
+ * SWOF_ETIMEOUT if a bounded tensor-core wait ran out. */
+SWOF_API int swof_unet_grads_raw(swof_unet *u, const void *x, const float *tgt, int B, double *loss_host,
+                                 void *stream);
+SWOF_API int swof_unet_adamw(swof_unet *u, float lr, float beta1, float beta2, float eps, float weight_decay,
+                             void *stream);
+/* Diagnostics: an internal activation of the last forward as fp32 on the
+ * host (which: 0 input, 1 first conv out, 2 its pre-activation, 3 concat
+ * buffer, 4 pooled input, 5/6 decoder convs, 7 bottom, 8 output; level l;
+ * n values, NHWC).  Synchronises the device. */
+SWOF_API int swof_unet_activation(swof_unet *u, int which, int level, float *host, long long n);
+/* State-level training step and prediction (FP32 NCHW device arrays):
+ * in [B][in_ch][H][W], next / out [B][out_ch][H][W]; out = in[:out_ch] +
+ * scale_out * net((in - mean) / scale_in). */
+SWOF_API int swof_surrogate_train_step(swof_unet *u, const float *in, const float *next, int B, float lr,
+                                       float weight_decay, double *loss_host, void *stream);
+SWOF_API int swof_surrogate_predict(swof_unet *u, const float *in, int B, float *out, void *stream);
+
 /* Human-readable text for a status code (static storage). */
 SWOF_API const char *swof_strerror(int code);
 

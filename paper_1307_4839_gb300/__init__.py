@@ -109,6 +109,29 @@ _SIGS = {
     "swof_ensemble_set_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "swof_ensemble_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_int)]),
     "swof_ensemble_set_wait_limit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int]),
+    "swof_gemm_bf16_nt": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_void_p, ctypes.c_void_p]),
+    "swof_unet_create": (ctypes.c_int, [ctypes.c_int] * 6 + [ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_void_p)]),
+    "swof_unet_destroy": (None, [ctypes.c_void_p]),
+    "swof_unet_param_count": (ctypes.c_longlong, [ctypes.c_void_p]),
+    "swof_unet_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "swof_unet_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "swof_unet_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "swof_unet_get_grads": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "swof_unet_set_norm": (ctypes.c_int, [ctypes.c_void_p] * 4),
+    "swof_unet_forward_raw": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                             ctypes.c_void_p]),
+    "swof_unet_grads_raw": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "swof_unet_adamw": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_float] * 5 + [ctypes.c_void_p]),
+    "swof_unet_activation": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                            ctypes.c_longlong]),
+    "swof_surrogate_train_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                                 ctypes.c_float, ctypes.c_float, ctypes.POINTER(ctypes.c_double),
+                                                 ctypes.c_void_p]),
+    "swof_surrogate_predict": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                              ctypes.c_void_p]),
     "swof_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "swof_version": (ctypes.c_char_p, []),
 }
@@ -452,3 +475,105 @@ class Ensemble:
     def set_wait_limit(self, polls: int, block_member: int = -1):
         _check(load().swof_ensemble_set_wait_limit(self._e, int(polls), int(block_member)),
                "swof_ensemble_set_wait_limit")
+
+
+class UNet:
+    """The learned surrogate's network (libswof swof_unet_*): BF16 tcgen05
+    convolutions with FP32 accumulation and FP32 AdamW master weights.
+    Device arrays are torch CUDA tensors."""
+
+    def __init__(self, base=32, in_ch=4, out_ch=3, H=256, W=256, max_batch=8, seed=0):
+        L = load()
+        self._u = None
+        u = ctypes.c_void_p()
+        _check(L.swof_unet_create(int(base), int(in_ch), int(out_ch), int(H), int(W), int(max_batch),
+                                  int(seed), ctypes.byref(u)), "swof_unet_create")
+        self._u = u
+        self.base, self.in_ch, self.out_ch, self.H, self.W, self.max_batch = base, in_ch, out_ch, H, W, max_batch
+        self.nparam = int(L.swof_unet_param_count(u))
+
+    def close(self):
+        if self._u:
+            load().swof_unet_destroy(self._u)
+            self._u = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def layout(self):
+        out = []
+        k = 0
+        while True:
+            info = (ctypes.c_int * 9)()
+            n = load().swof_unet_layout(self._u, k, info)
+            if n < 0:
+                break
+            out.append(dict(zip(("kind", "cin", "cin_p", "cout", "ncols", "Kp", "woff", "boff", "act"), info)))
+            k += 1
+            if k >= n:
+                break
+        return out
+
+    def params(self) -> np.ndarray:
+        a = np.empty(self.nparam, dtype=np.float32)
+        _check(load().swof_unet_get_params(self._u, a.ctypes.data), "swof_unet_get_params")
+        return a
+
+    def set_params(self, a):
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        assert a.size == self.nparam
+        _check(load().swof_unet_set_params(self._u, a.ctypes.data), "swof_unet_set_params")
+
+    def grads(self) -> np.ndarray:
+        a = np.empty(self.nparam, dtype=np.float32)
+        _check(load().swof_unet_get_grads(self._u, a.ctypes.data), "swof_unet_get_grads")
+        return a
+
+    def set_norm(self, mean, scale_in, scale_out):
+        m = np.ascontiguousarray(mean, dtype=np.float32)
+        si_ = np.ascontiguousarray(scale_in, dtype=np.float32)
+        so = np.ascontiguousarray(scale_out, dtype=np.float32)
+        _check(load().swof_unet_set_norm(self._u, m.ctypes.data, si_.ctypes.data, so.ctypes.data),
+               "swof_unet_set_norm")
+
+    @staticmethod
+    def _s(stream):
+        return None if stream is None else ctypes.c_void_p(stream)
+
+    def forward_raw(self, x, y, stream=None):
+        B = x.shape[0] // (self.H * self.W)
+        _check(load().swof_unet_forward_raw(self._u, ctypes.c_void_p(x.data_ptr()), B,
+                                            ctypes.c_void_p(y.data_ptr()), self._s(stream)), "swof_unet_forward_raw")
+
+    def grads_raw(self, x, tgt, stream=None) -> float:
+        B = x.shape[0] // (self.H * self.W)
+        loss = ctypes.c_double()
+        _check(load().swof_unet_grads_raw(self._u, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(tgt.data_ptr()),
+                                          B, ctypes.byref(loss), self._s(stream)), "swof_unet_grads_raw")
+        return loss.value
+
+    def activation(self, which: int, level: int, shape) -> np.ndarray:
+        a = np.empty(int(np.prod(shape)), dtype=np.float32)
+        _check(load().swof_unet_activation(self._u, int(which), int(level), a.ctypes.data, a.size),
+               "swof_unet_activation")
+        return a.reshape(shape)
+
+    def adamw(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, stream=None):
+        _check(load().swof_unet_adamw(self._u, lr, beta1, beta2, eps, weight_decay, self._s(stream)),
+               "swof_unet_adamw")
+
+    def train_step(self, state_in, state_next, lr, weight_decay=0.0, stream=None) -> float:
+        loss = ctypes.c_double()
+        _check(load().swof_surrogate_train_step(self._u, ctypes.c_void_p(state_in.data_ptr()),
+                                                ctypes.c_void_p(state_next.data_ptr()), int(state_in.shape[0]),
+                                                float(lr), float(weight_decay), ctypes.byref(loss), self._s(stream)),
+               "swof_surrogate_train_step")
+        return loss.value
+
+    def predict(self, state_in, out, stream=None):
+        _check(load().swof_surrogate_predict(self._u, ctypes.c_void_p(state_in.data_ptr()), int(state_in.shape[0]),
+                                             ctypes.c_void_p(out.data_ptr()), self._s(stream)),
+               "swof_surrogate_predict")

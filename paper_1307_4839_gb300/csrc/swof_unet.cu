@@ -1,0 +1,919 @@
+// swof_unet.cu -- the learned surrogate: a 4-level convolutional U-Net on
+// coarsened shallow-water fields, trained and run with the tcgen05 kernels of
+// swof_conv.cuh (BF16 weights and activations, FP32 accumulation, FP32
+// master weights, gradients and AdamW moments).
+//
+// Topology (base width C, levels l = 0..3 at resolution H >> l, width C << l):
+//   encoder  l: conv3x3 -> GELU -> conv3x3 -> GELU   (the second writes the
+//               first half of the level's concatenation buffer), then 2x2
+//               average pooling to the next level;
+//   bottom  (l = 3): the same two convolutions, no pooling;
+//   decoder  l = 2, 1, 0: 2x2 stride-2 transposed conv of the level below
+//               into the second half of the concatenation buffer, then
+//               conv3x3 -> GELU -> conv3x3 -> GELU;
+//   output: 1x1 conv to 16 channels (the first `out_ch` are used), FP32.
+// Inputs are NHWC bf16 with 16 channels (the first `in_ch` used, normalised
+// by the caller-given mean / scale); the network predicts the normalised
+// increment of the state over the surrogate's time span.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/swof.h"
+#include "swof_conv.cuh"
+
+namespace swof {
+
+typedef __nv_bfloat16 bf16;
+
+// ---------------------------------------------------------------------------
+// Small kernels
+__device__ __forceinline__ float gelu_grad(float z)
+{
+    const float phi = 0.39894228040143268f * __expf(-0.5f * z * z);
+    const float Phi = 0.5f * (1.0f + erff(z * 0.70710678118654752f));
+    return Phi + z * phi;
+}
+
+// dz[p][n] = dy[p][dyc0 + n] * (act ? gelu'(z[p][n]) : 1), bf16 compact output
+__global__ void k_act_bwd(const float *dy, int dyc, int dyc0, const bf16 *z, int act, bf16 *dz, long long P, int N)
+{
+    long long total = P * N;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        long long p = i / N;
+        int n = (int)(i - p * N);
+        float g = dy[p * dyc + dyc0 + n];
+        if (act) g *= gelu_grad(__bfloat162float(z[i]));
+        dz[i] = __float2bfloat16_rn(g);
+    }
+}
+
+// column sums of a bf16 [P][N] matrix into db[n % nb] (atomics)
+__global__ void k_colsum(const bf16 *dz, long long P, int N, int nb, float *db)
+{
+    // each thread owns one column n and a strided set of rows
+    int n = threadIdx.x % N;
+    int rlane = threadIdx.x / N, rlanes = blockDim.x / N;
+    float s = 0.0f;
+    for (long long p = blockIdx.x * (long long)rlanes + rlane; p < P; p += (long long)gridDim.x * rlanes)
+        s += __bfloat162float(dz[p * N + n]);
+    atomicAdd(&db[n % nb], s);
+}
+
+// 2x2 average pooling: x (channels [xc0, xc0+C) of stride cx) at H x W ->
+// y compact [B][H/2][W/2][C]
+__global__ void k_pool_fwd(const bf16 *x, int cx, int xc0, int B, int H, int W, int C, bf16 *y)
+{
+    long long total = (long long)B * (H / 2) * (W / 2) * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        int c = (int)(i % C);
+        long long q = i / C;
+        int xo = (int)(q % (W / 2));
+        long long r = q / (W / 2);
+        int yo = (int)(r % (H / 2));
+        int b = (int)(r / (H / 2));
+        long long base = ((long long)b * H + 2 * yo) * W + 2 * xo;
+        float s = __bfloat162float(x[base * cx + xc0 + c]) + __bfloat162float(x[(base + 1) * cx + xc0 + c]) +
+                  __bfloat162float(x[(base + W) * cx + xc0 + c]) + __bfloat162float(x[(base + W + 1) * cx + xc0 + c]);
+        y[i] = __float2bfloat16_rn(0.25f * s);
+    }
+}
+
+// dx[..][xc0 + c] += dy / 4 for the four fine pixels of each coarse pixel
+__global__ void k_pool_bwd_add(const float *dy, int B, int H, int W, int C, float *dx, int cx, int xc0)
+{
+    long long total = (long long)B * (H / 2) * (W / 2) * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        int c = (int)(i % C);
+        long long q = i / C;
+        int xo = (int)(q % (W / 2));
+        long long r = q / (W / 2);
+        int yo = (int)(r % (H / 2));
+        int b = (int)(r / (H / 2));
+        long long base = ((long long)b * H + 2 * yo) * W + 2 * xo;
+        float g = 0.25f * dy[i];
+        dx[base * cx + xc0 + c] += g;
+        dx[(base + 1) * cx + xc0 + c] += g;
+        dx[(base + W) * cx + xc0 + c] += g;
+        dx[(base + W + 1) * cx + xc0 + c] += g;
+    }
+}
+
+// Mean squared error over the first nch of 16 output channels; writes the
+// gradient d(pred) = 2 (pred - tgt) / (P * nch) (0 on unused channels) and
+// adds the loss sum (FP64).
+__global__ void k_mse(const float *pred, const float *tgt, long long P, int nch, float *dpred, double *loss)
+{
+    __shared__ double red[32];
+    double s = 0.0;
+    const float scale = 2.0f / (float)(P * nch);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P * 16; i += (long long)gridDim.x * blockDim.x) {
+        long long p = i >> 4;
+        int c = (int)(i & 15);
+        float g = 0.0f;
+        if (c < nch) {
+            float d = pred[i] - tgt[p * nch + c];
+            s += (double)d * d;
+            g = scale * d;
+        }
+        dpred[i] = g;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        atomicAdd(loss, t);
+    }
+}
+
+__global__ void k_adamw(float *w, const float *g, float *m, float *v, long long n, float lr, float b1, float b2,
+                        float eps, float wd, float bc1, float bc2)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float gi = g[i];
+        float mi = b1 * m[i] + (1.0f - b1) * gi;
+        float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        float upd = (mi / bc1) / (sqrtf(vi / bc2) + eps);
+        w[i] = w[i] - lr * (upd + wd * w[i]);
+    }
+}
+
+__global__ void k_to_bf16(const float *src, bf16 *dst, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = __float2bfloat16_rn(src[i]);
+}
+
+// Data-gradient weights: wd[ci][tap' * cout + co] = w[co][(taps-1-tap') * cin_p + ci]
+// (taps = 9 for 3x3, 1 for 1x1); and the transposed conv's wd[ci][n] = w[n][ci].
+__global__ void k_make_wd(const float *w, int cout, int Kp, int cin_p, int taps, int flip, bf16 *wd, int rows, int Kpd)
+{
+    long long total = (long long)rows * Kpd;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        int ci = (int)(i / Kpd), k = (int)(i % Kpd);
+        float val = 0.0f;
+        int tapd = k / cout, co = k % cout;
+        if (tapd < taps) {
+            int tap = flip ? taps - 1 - tapd : tapd;
+            val = w[(long long)co * Kp + tap * cin_p + ci];
+        }
+        wd[i] = __float2bfloat16_rn(val);
+    }
+}
+
+__global__ void k_replicate_bias(const float *b, int n, int reps, float *out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n * reps) out[i] = b[i % n];
+}
+
+// state [B][4][H][W] fp32 (h, hu, hv, z) -> x [B*H*W][16] bf16 normalised
+__global__ void k_pack_input(const float *state, int nin, int B, int H, int W, const float *mean, const float *inv,
+                             bf16 *x)
+{
+    long long P = (long long)B * H * W;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P * 16; i += (long long)gridDim.x * blockDim.x) {
+        long long p = i >> 4;
+        int c = (int)(i & 15);
+        float v = 0.0f;
+        if (c < nin) {
+            long long b = p / ((long long)H * W), r = p - b * (long long)H * W;
+            v = (state[(b * nin + c) * (long long)H * W + r] - mean[c]) * inv[c];
+        }
+        x[i] = __float2bfloat16_rn(v);
+    }
+}
+
+// out[b][c] = in[b][c] + net[p][c] * scale[c]  (c < nout), NCHW fp32
+__global__ void k_residual(const float *in, int nin, const float *net, int nout, int B, int H, int W,
+                           const float *scale, float *out)
+{
+    long long HW = (long long)H * W, total = (long long)B * nout * HW;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        long long b = i / (nout * HW), r = i - b * nout * HW;
+        int c = (int)(r / HW);
+        long long q = r - c * HW;
+        out[i] = in[(b * nin + c) * HW + q] + net[(b * HW + q) * 16 + c] * scale[c];
+    }
+}
+
+// target tgt[p][c] = (next[b][c] - in[b][c]) / scale[c]
+__global__ void k_target(const float *in, int nin, const float *next, int nout, int B, int H, int W,
+                         const float *scale, float *tgt)
+{
+    long long HW = (long long)H * W, P = (long long)B * HW;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P * nout; i += (long long)gridDim.x * blockDim.x) {
+        long long p = i / nout;
+        int c = (int)(i - p * nout);
+        long long b = p / HW, q = p - b * HW;
+        tgt[i] = (next[(b * nout + c) * HW + q] - in[(b * nin + c) * HW + q]) / scale[c];
+    }
+}
+
+inline int grid_for(long long n) { long long g = (n + 255) / 256; return (int)(g < 152 * 16 ? (g > 0 ? g : 1) : 152 * 16); }
+
+// ---------------------------------------------------------------------------
+// Launchers of the tensor-core kernels
+template <int NT>
+int conv_launch(const ConvArgs &A, cudaStream_t s)
+{
+    size_t smem = sizeof(ConvSmem) + 1024;
+    if (cudaFuncSetAttribute(k_conv<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return SWOF_ECUDA;
+    long long M = (long long)A.B * A.H * A.W;
+    dim3 grid((unsigned)((M + 127) / 128), (unsigned)(A.ntot / NT));
+    k_conv<NT><<<grid, 128, smem, s>>>(A);
+    return cudaGetLastError() == cudaSuccess ? SWOF_OK : SWOF_ECUDA;
+}
+
+int conv(const ConvArgs &A, cudaStream_t s)
+{
+    int nt = A.ntot >= 256 ? 256 : A.ntot;
+    if (A.ntot % nt) return SWOF_EINVAL;
+    switch (nt) {
+    case 16: return conv_launch<16>(A, s);
+    case 32: return conv_launch<32>(A, s);
+    case 64: return conv_launch<64>(A, s);
+    case 128: return conv_launch<128>(A, s);
+    case 256: return conv_launch<256>(A, s);
+    default: return SWOF_EINVAL;
+    }
+}
+
+template <int NT>
+int wgrad_launch(WgradArgs A, int ncols, cudaStream_t s)
+{
+    size_t smem = sizeof(ConvSmem) + 1024;
+    if (cudaFuncSetAttribute(k_wgrad<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return SWOF_ECUDA;
+    long long P = (long long)A.B * A.H * A.W;
+    long long chunks = (P + 63) / 64;
+    unsigned gx = (unsigned)((A.nrows + 127) / 128), gy = (unsigned)((ncols + NT - 1) / NT);
+    long long target = 2 * 152;      // CTAs to spread the pixel reduction over
+    long long splits = target / (gx * gy);
+    if (splits < 1) splits = 1;
+    if (splits > chunks) splits = chunks;
+    A.chunks_per_cta = (int)((chunks + splits - 1) / splits);
+    unsigned gz = (unsigned)((chunks + A.chunks_per_cta - 1) / A.chunks_per_cta);
+    k_wgrad<NT><<<dim3(gx, gy, gz), 128, smem, s>>>(A);
+    return cudaGetLastError() == cudaSuccess ? SWOF_OK : SWOF_ECUDA;
+}
+
+int wgrad(const WgradArgs &A, int ncols, cudaStream_t s)
+{
+    if (ncols % 256 == 0) return wgrad_launch<256>(A, ncols, s);
+    if (ncols % 128 == 0) return wgrad_launch<128>(A, ncols, s);
+    return wgrad_launch<64>(A, ncols, s);
+}
+
+}  // namespace swof
+
+// ---------------------------------------------------------------------------
+// The network
+using swof::bf16;
+
+namespace {
+
+enum LayerKind { K_CONV3 = 0, K_CONV1 = 1, K_CONVT = 2 };
+
+struct Layer {
+    int kind, cin, cin_p, cout, act;
+    int ncols;          // GEMM columns of the forward (cout, or 4*cout for the transposed conv)
+    int Kp;             // forward K padded (row length of w)
+    int Kpd;            // data-gradient K padded
+    size_t woff, boff;  // offsets in the flat parameter arrays
+    size_t nw, nb;
+};
+
+struct Act {            // an NHWC bf16 activation slot
+    bf16 *p;
+    int c, c0;          // channel stride / offset
+};
+
+}  // namespace
+
+struct swof_unet {
+    int C, in_ch, out_ch, H, W, maxB;
+    std::vector<Layer> layers;    // 0,1: enc0; 2,3: enc1; 4,5: enc2; 6,7: bottom; 8: up2, 9,10: dec2;
+                                  // 11: up1, 12,13: dec1; 14: up0, 15,16: dec0; 17: out
+    size_t nparam = 0;
+    float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;   // flat FP32 (weights then biases)
+    bf16 *wbf = nullptr;          // bf16 forward weights (same layout as w's weight part)
+    bf16 *wd = nullptr;           // data-gradient weights
+    size_t nwd = 0;
+    float *bias_rep = nullptr;    // replicated transposed-conv biases
+    std::vector<size_t> wd_off;
+    std::vector<std::vector<char>> dummy;
+    // activations (per level l)
+    std::vector<bf16 *> ea, ea_pre, eb_pre, cat, pool, da, da_pre, db, db_pre;
+    bf16 *x0 = nullptr, *bott = nullptr, *bott_pre = nullptr, *dz = nullptr;
+    float *out = nullptr, *tgt = nullptr, *gpred = nullptr;
+    // gradients (FP32)
+    std::vector<float *> g_ea, g_cat, g_pool, g_da, g_db;
+    float *g_bott = nullptr;
+    double *loss = nullptr;
+    int *err = nullptr;
+    float *norm = nullptr;        // mean[16], inv[16], scale[16] (device)
+    long long step = 0;
+    std::vector<void *> allocs;
+};
+
+namespace {
+
+template <typename T>
+T *dmalloc(swof_unet *u, size_t n, int *st)
+{
+    if (*st) return nullptr;
+    void *p = nullptr;
+    if (cudaMalloc(&p, (n ? n : 1) * sizeof(T)) != cudaSuccess) {
+        *st = SWOF_ENOMEM;
+        return nullptr;
+    }
+    cudaMemset(p, 0, (n ? n : 1) * sizeof(T));
+    u->allocs.push_back(p);
+    return static_cast<T *>(p);
+}
+
+int pad64(int k) { return (k + 63) / 64 * 64; }
+
+Layer make_layer(int kind, int cin, int cout, int act)
+{
+    Layer L{};
+    L.kind = kind;
+    L.cin = cin;
+    L.cin_p = cin < 16 ? 16 : cin;
+    L.cout = cout;
+    L.act = act;
+    L.ncols = kind == K_CONVT ? 4 * cout : cout;
+    int taps = kind == K_CONV3 ? 9 : 1;
+    L.Kp = pad64(taps * L.cin_p);
+    L.Kpd = kind == K_CONVT ? pad64(4 * cout) : pad64(taps * cout);
+    L.nw = (size_t)L.ncols * L.Kp;
+    L.nb = (size_t)cout;
+    return L;
+}
+
+// SplitMix64 + Box-Muller: reproducible initial weights
+struct Rng {
+    uint64_t s;
+    uint64_t next()
+    {
+        uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    }
+    double uni() { return ((next() >> 11) + 0.5) * (1.0 / 9007199254740992.0); }
+    double normal() { return std::sqrt(-2.0 * std::log(uni())) * std::cos(6.283185307179586 * uni()); }
+};
+
+cudaStream_t S(void *s) { return static_cast<cudaStream_t>(s); }
+
+float *W(swof_unet *u, int l) { return u->w + u->layers[l].woff; }
+float *Bv(swof_unet *u, int l) { return u->w + u->layers[l].boff; }
+float *GW(swof_unet *u, int l) { return u->g + u->layers[l].woff; }
+float *GB(swof_unet *u, int l) { return u->g + u->layers[l].boff; }
+bf16 *WB(swof_unet *u, int l) { return u->wbf + u->layers[l].woff; }
+
+// refresh bf16 weights, data-gradient weights and replicated biases from the FP32 master
+int refresh_weights(swof_unet *u, cudaStream_t s)
+{
+    size_t nw = u->layers.back().woff + u->layers.back().nw;
+    swof::k_to_bf16<<<swof::grid_for((long long)nw), 256, 0, s>>>(u->w, u->wbf, (long long)nw);
+    for (size_t l = 0; l < u->layers.size(); ++l) {
+        const Layer &L = u->layers[l];
+        int rows = L.cin_p, taps = L.kind == K_CONV3 ? 9 : (L.kind == K_CONV1 ? 1 : 4);
+        if (L.kind == K_CONVT) {
+            // wd[ci][n] = w[n][ci]: a 1-tap "flip" over n = (sub, co) columns
+            swof::k_make_wd<<<swof::grid_for((long long)rows * L.Kpd), 256, 0, s>>>(
+                W(u, (int)l), L.ncols, L.Kp, L.cin_p, 1, 0, u->wd + u->wd_off[l], rows, L.Kpd);
+        } else {
+            swof::k_make_wd<<<swof::grid_for((long long)rows * L.Kpd), 256, 0, s>>>(
+                W(u, (int)l), L.cout, L.Kp, L.cin_p, taps, 1, u->wd + u->wd_off[l], rows, L.Kpd);
+        }
+    }
+    // transposed-conv biases replicated over the 4 sub-positions
+    int off = 0;
+    for (size_t l = 0; l < u->layers.size(); ++l) {
+        const Layer &L = u->layers[l];
+        if (L.kind != K_CONVT) continue;
+        swof::k_replicate_bias<<<(4 * L.cout + 255) / 256, 256, 0, s>>>(Bv(u, (int)l), L.cout, 4, u->bias_rep + off);
+        off += 4 * L.cout;
+    }
+    return cudaGetLastError() == cudaSuccess ? SWOF_OK : SWOF_ECUDA;
+}
+
+float *rep_bias(swof_unet *u, int l)
+{
+    int off = 0;
+    for (int k = 0; k < l; ++k)
+        if (u->layers[k].kind == K_CONVT) off += 4 * u->layers[k].cout;
+    return u->bias_rep + off;
+}
+
+// forward of one layer on B samples at resolution h x w (output grid)
+int fwd_layer(swof_unet *u, int l, int B, int h, int w, Act in, Act out, bf16 *pre, float *outf, int outf_c,
+              cudaStream_t s)
+{
+    const Layer &L = u->layers[l];
+    swof::ConvArgs A{};
+    A.x = in.p;
+    A.B = B;
+    A.H = h;
+    A.W = w;
+    A.cx = in.c;
+    A.xc0 = in.c0;
+    A.cin = L.cin_p;
+    A.ks = L.kind == K_CONV3 ? 3 : 1;
+    A.gather = swof::GATHER_SAME;
+    A.w = WB(u, l);
+    A.Kp = L.Kp;
+    A.bias = L.kind == K_CONVT ? rep_bias(u, l) : Bv(u, l);
+    A.ntot = L.ncols;
+    A.y = out.p;
+    A.ypre = pre;
+    A.yf = outf;
+    A.cy = outf ? outf_c : out.c;
+    A.yc0 = outf ? 0 : out.c0;
+    A.act = L.act;
+    A.store = L.kind == K_CONVT ? swof::SCATTER_UP2 : swof::STORE_NHWC;
+    A.cout_up = L.cout;
+    A.err = u->err;
+    return swof::conv(A, s);
+}
+
+// backward of one layer: dy (FP32, channels [dyc0, dyc0 + cout) of stride
+// dyc, at the layer's output grid oh x ow) -> weight/bias gradients and,
+// when dx is given, the input gradient (FP32, channels [dxc0, ...) of dxc).
+int bwd_layer(swof_unet *u, int l, int B, int ih, int iw, Act in, const float *dy, int dyc, int dyc0,
+              const bf16 *pre, float *dx, int dxc, int dxc0, cudaStream_t s)
+{
+    const Layer &L = u->layers[l];
+    const bool up = L.kind == K_CONVT;
+    const int oh = up ? 2 * ih : ih, ow = up ? 2 * iw : iw;
+    const long long Po = (long long)B * oh * ow, Pi = (long long)B * ih * iw;
+    // dz = dy * act'(pre), compact bf16 [Po][cout]
+    swof::k_act_bwd<<<swof::grid_for(Po * L.cout), 256, 0, s>>>(dy, dyc, dyc0, pre, L.act, u->dz, Po, L.cout);
+    // bias gradient
+    {
+        int per = 256 / L.cout > 0 ? 256 / L.cout : 1;
+        int threads = per * L.cout;
+        if (threads > 1024) threads = L.cout;
+        long long blocks = (Po + per - 1) / per;
+        if (blocks > 1024) blocks = 1024;
+        swof::k_colsum<<<(unsigned)blocks, threads, 0, s>>>(u->dz, Po, L.cout, L.cout, GB(u, l));
+    }
+    // weight gradient
+    swof::WgradArgs G{};
+    G.g = u->dz;
+    G.gc = L.cout;
+    G.gmode = up ? swof::GATHER_UP2 : swof::GATHER_SAME;
+    G.cout_up = L.cout;
+    G.x = in.p;
+    G.cx = in.c;
+    G.xc0 = in.c0;
+    G.cin = L.cin_p;
+    G.ks = L.kind == K_CONV3 ? 3 : 1;
+    G.B = B;
+    G.H = ih;
+    G.W = iw;
+    G.nrows = L.ncols;
+    G.Kp = L.Kp;
+    G.dw = GW(u, l);
+    G.err = u->err;
+    int st = swof::wgrad(G, L.Kp, s);
+    if (st || !dx) return st;
+    // data gradient
+    swof::ConvArgs A{};
+    A.x = u->dz;
+    A.B = B;
+    A.H = ih;
+    A.W = iw;
+    A.cx = L.cout;
+    A.xc0 = 0;
+    A.cin = L.cout;
+    A.ks = L.kind == K_CONV3 ? 3 : 1;
+    A.gather = up ? swof::GATHER_UP2 : swof::GATHER_SAME;
+    A.w = u->wd + u->wd_off[l];
+    A.Kp = L.Kpd;
+    A.bias = nullptr;
+    A.ntot = L.cin_p;
+    A.yf = dx;
+    A.cy = dxc;
+    A.yc0 = dxc0;
+    A.act = swof::ACT_NONE;
+    A.store = swof::STORE_NHWC;
+    A.err = u->err;
+    (void)Pi;
+    return swof::conv(A, s);
+}
+
+int forward(swof_unet *u, int B, cudaStream_t s)
+{
+    int st = SWOF_OK;
+    const int C = u->C;
+    Act in{u->x0, 16, 0};
+    for (int l = 0; l < 4 && !st; ++l) {
+        int h = u->H >> l, w = u->W >> l, c = C << l;
+        if (l > 0) {
+            int hp = u->H >> (l - 1), wp = u->W >> (l - 1), cp = C << (l - 1);
+            long long n = (long long)B * h * w * cp;
+            swof::k_pool_fwd<<<swof::grid_for(n), 256, 0, s>>>(u->cat[l - 1], 2 * cp, 0, B, hp, wp, cp, u->pool[l]);
+            in = Act{u->pool[l], cp, 0};
+        }
+        st = fwd_layer(u, 2 * l, B, h, w, in, Act{u->ea[l], c, 0}, u->ea_pre[l], nullptr, 0, s);
+        Act o = l < 3 ? Act{u->cat[l], 2 * c, 0} : Act{u->bott, c, 0};
+        if (!st) st = fwd_layer(u, 2 * l + 1, B, h, w, Act{u->ea[l], c, 0}, o, l < 3 ? u->eb_pre[l] : u->bott_pre,
+                                nullptr, 0, s);
+    }
+    Act below{u->bott, C << 3, 0};
+    for (int l = 2; l >= 0 && !st; --l) {
+        int h = u->H >> l, w = u->W >> l, c = C << l;
+        int base = 8 + 3 * (2 - l);
+        // transposed conv from the level below (its grid) into the second half of cat[l]
+        st = fwd_layer(u, base, B, h / 2, w / 2, below, Act{u->cat[l], 2 * c, c}, nullptr, nullptr, 0, s);
+        if (!st) st = fwd_layer(u, base + 1, B, h, w, Act{u->cat[l], 2 * c, 0}, Act{u->da[l], c, 0}, u->da_pre[l],
+                                nullptr, 0, s);
+        if (!st) st = fwd_layer(u, base + 2, B, h, w, Act{u->da[l], c, 0}, Act{u->db[l], c, 0}, u->db_pre[l],
+                                nullptr, 0, s);
+        below = Act{u->db[l], c, 0};
+    }
+    if (!st) st = fwd_layer(u, 17, B, u->H, u->W, below, Act{nullptr, 16, 0}, nullptr, u->out, 16, s);
+    return st;
+}
+
+int backward(swof_unet *u, int B, cudaStream_t s)
+{
+    const int C = u->C;
+    int st = SWOF_OK;
+    // output layer: dy = d(loss)/d(pred) in gpred
+    st = bwd_layer(u, 17, B, u->H, u->W, Act{u->db[0], C, 0}, u->gpred, 16, 0, nullptr, u->g_db[0], C, 0, s);
+    for (int l = 0; l <= 2 && !st; ++l) {
+        // process levels top-down in the decoder order: level 0 first (closest to the output)
+        int h = u->H >> l, w = u->W >> l, c = C << l;
+        int base = 8 + 3 * (2 - l);
+        st = bwd_layer(u, base + 2, B, h, w, Act{u->da[l], c, 0}, u->g_db[l], c, 0, u->db_pre[l], u->g_da[l], c, 0, s);
+        if (!st) st = bwd_layer(u, base + 1, B, h, w, Act{u->cat[l], 2 * c, 0}, u->g_da[l], c, 0, u->da_pre[l],
+                                u->g_cat[l], 2 * c, 0, s);
+        // transposed conv: its output gradient is the second half of g_cat[l]
+        Act below = l < 2 ? Act{u->db[l + 1], 2 * c, 0} : Act{u->bott, 8 * C, 0};
+        float *gbelow = l < 2 ? u->g_db[l + 1] : u->g_bott;
+        if (!st) st = bwd_layer(u, base, B, h / 2, w / 2, below, u->g_cat[l], 2 * c, c, nullptr, gbelow, 2 * c, 0, s);
+    }
+    // bottom and encoder, deepest first
+    for (int l = 3; l >= 0 && !st; --l) {
+        int h = u->H >> l, w = u->W >> l, c = C << l;
+        Act in_b{u->ea[l], c, 0};
+        const float *dyb = l < 3 ? u->g_cat[l] : u->g_bott;
+        int dybc = l < 3 ? 2 * c : c;
+        st = bwd_layer(u, 2 * l + 1, B, h, w, in_b, dyb, dybc, 0, l < 3 ? u->eb_pre[l] : u->bott_pre, u->g_ea[l], c, 0, s);
+        Act in_a = l == 0 ? Act{u->x0, 16, 0} : Act{u->pool[l], C << (l - 1), 0};
+        float *gin = l == 0 ? nullptr : u->g_pool[l];
+        if (!st) st = bwd_layer(u, 2 * l, B, h, w, in_a, u->g_ea[l], c, 0, u->ea_pre[l], gin, C << (l > 0 ? l - 1 : 0), 0, s);
+        if (!st && l > 0) {
+            int hp = u->H >> (l - 1), wp = u->W >> (l - 1), cp = C << (l - 1);
+            long long n = (long long)B * h * w * cp;
+            swof::k_pool_bwd_add<<<swof::grid_for(n), 256, 0, s>>>(u->g_pool[l], B, hp, wp, cp, u->g_cat[l - 1], 2 * cp, 0);
+        }
+    }
+    return st ? st : (cudaGetLastError() == cudaSuccess ? SWOF_OK : SWOF_ECUDA);
+}
+
+}  // namespace
+
+// Loss and gradients for the packed input in x0 and the target in tgt
+// ([P][out_ch] FP32); gradients replace the previous ones.
+int loss_and_grads(swof_unet *u, int B, cudaStream_t s)
+{
+    long long P = (long long)B * u->H * u->W;
+    cudaMemsetAsync(u->g, 0, u->nparam * sizeof(float), s);
+    cudaMemsetAsync(u->loss, 0, sizeof(double), s);
+    int st = forward(u, B, s);
+    if (st) return st;
+    swof::k_mse<<<swof::grid_for(P * 16), 256, 0, s>>>(u->out, u->tgt, P, u->out_ch, u->gpred, u->loss);
+    return backward(u, B, s);
+}
+
+int adamw(swof_unet *u, float lr, float b1, float b2, float eps, float wd, cudaStream_t s)
+{
+    u->step++;
+    float bc1 = 1.0f - std::pow(b1, (float)u->step), bc2 = 1.0f - std::pow(b2, (float)u->step);
+    swof::k_adamw<<<swof::grid_for((long long)u->nparam), 256, 0, s>>>(u->w, u->g, u->m, u->v, (long long)u->nparam,
+                                                                         lr, b1, b2, eps, wd, bc1, bc2);
+    return refresh_weights(u, s);
+}
+
+int read_status(swof_unet *u, cudaStream_t s, double *loss_host)
+{
+    int err = 0;
+    double l = 0.0;
+    if (cudaMemcpyAsync(&err, u->err, sizeof err, cudaMemcpyDeviceToHost, s) != cudaSuccess) return SWOF_ECUDA;
+    if (cudaMemcpyAsync(&l, u->loss, sizeof l, cudaMemcpyDeviceToHost, s) != cudaSuccess) return SWOF_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SWOF_ECUDA;
+    if (loss_host) *loss_host = l;
+    return err ? SWOF_ETIMEOUT : SWOF_OK;
+}
+
+extern "C" {
+
+int swof_unet_create(int base, int in_ch, int out_ch, int H, int W, int max_batch, unsigned long long seed,
+                     swof_unet **out)
+{
+    if (!out) return SWOF_EINVAL;
+    *out = nullptr;
+    if (base < 16 || base % 16 || base > 64 || in_ch < 1 || in_ch > 16 || out_ch < 1 || out_ch > 16 ||
+        H < 16 || W < 16 || H % 8 || W % 8 || max_batch < 1)
+        return SWOF_EINVAL;
+    swof_unet *u = new (std::nothrow) swof_unet();
+    if (!u) return SWOF_ENOMEM;
+    u->C = base;
+    u->in_ch = in_ch;
+    u->out_ch = out_ch;
+    u->H = H;
+    u->W = W;
+    u->maxB = max_batch;
+    const int C = base;
+    auto add = [&](int kind, int cin, int cout, int act) { u->layers.push_back(make_layer(kind, cin, cout, act)); };
+    add(K_CONV3, in_ch, C, 1);
+    add(K_CONV3, C, C, 1);
+    for (int l = 1; l < 4; ++l) {
+        add(K_CONV3, C << (l - 1), C << l, 1);
+        add(K_CONV3, C << l, C << l, 1);
+    }
+    for (int l = 2; l >= 0; --l) {
+        add(K_CONVT, C << (l + 1), C << l, 0);
+        add(K_CONV3, 2 * (C << l), C << l, 1);
+        add(K_CONV3, C << l, C << l, 1);
+    }
+    add(K_CONV1, C, 16, 0);
+    size_t off = 0;
+    for (Layer &L : u->layers) {
+        L.woff = off;
+        off += L.nw;
+    }
+    for (Layer &L : u->layers) {
+        L.boff = off;
+        off += L.nb;
+    }
+    u->nparam = off;
+    size_t nwd = 0;
+    for (Layer &L : u->layers) {
+        u->wd_off.push_back(nwd);
+        nwd += (size_t)L.cin_p * L.Kpd;
+    }
+    u->nwd = nwd;
+    int st = SWOF_OK;
+    u->w = dmalloc<float>(u, off, &st);
+    u->g = dmalloc<float>(u, off, &st);
+    u->m = dmalloc<float>(u, off, &st);
+    u->v = dmalloc<float>(u, off, &st);
+    u->wbf = dmalloc<bf16>(u, off, &st);
+    u->wd = dmalloc<bf16>(u, nwd, &st);
+    int nrep = 0;
+    for (Layer &L : u->layers)
+        if (L.kind == K_CONVT) nrep += 4 * L.cout;
+    u->bias_rep = dmalloc<float>(u, (size_t)nrep, &st);
+    u->err = dmalloc<int>(u, 1, &st);
+    u->loss = dmalloc<double>(u, 1, &st);
+    u->norm = dmalloc<float>(u, 48, &st);
+    const long long B = max_batch;
+    long long P0 = B * H * W;
+    u->x0 = dmalloc<bf16>(u, (size_t)(P0 * 16), &st);
+    u->out = dmalloc<float>(u, (size_t)(P0 * 16), &st);
+    u->tgt = dmalloc<float>(u, (size_t)(P0 * 16), &st);
+    u->gpred = dmalloc<float>(u, (size_t)(P0 * 16), &st);
+    size_t maxdz = 0;
+    for (int l = 0; l < 4; ++l) {
+        long long P = B * (H >> l) * (W >> l);
+        int c = C << l;
+        u->ea.push_back(dmalloc<bf16>(u, (size_t)(P * c), &st));
+        u->ea_pre.push_back(dmalloc<bf16>(u, (size_t)(P * c), &st));
+        u->g_ea.push_back(dmalloc<float>(u, (size_t)(P * c), &st));
+        u->eb_pre.push_back(l < 3 ? dmalloc<bf16>(u, (size_t)(P * c), &st) : nullptr);
+        u->cat.push_back(l < 3 ? dmalloc<bf16>(u, (size_t)(P * 2 * c), &st) : nullptr);
+        u->g_cat.push_back(l < 3 ? dmalloc<float>(u, (size_t)(P * 2 * c), &st) : nullptr);
+        u->pool.push_back(l > 0 ? dmalloc<bf16>(u, (size_t)(P * (c / 2)), &st) : nullptr);
+        u->g_pool.push_back(l > 0 ? dmalloc<float>(u, (size_t)(P * (c / 2)), &st) : nullptr);
+        u->da.push_back(l < 3 ? dmalloc<bf16>(u, (size_t)(P * c), &st) : nullptr);
+        u->da_pre.push_back(l < 3 ? dmalloc<bf16>(u, (size_t)(P * c), &st) : nullptr);
+        u->db.push_back(l < 3 ? dmalloc<bf16>(u, (size_t)(P * c), &st) : nullptr);
+        u->db_pre.push_back(l < 3 ? dmalloc<bf16>(u, (size_t)(P * c), &st) : nullptr);
+        u->g_da.push_back(l < 3 ? dmalloc<float>(u, (size_t)(P * c), &st) : nullptr);
+        u->g_db.push_back(l < 3 ? dmalloc<float>(u, (size_t)(P * c), &st) : nullptr);
+        maxdz = maxdz > (size_t)(P * 2 * c) ? maxdz : (size_t)(P * 2 * c);
+    }
+    {
+        long long P3 = B * (H >> 3) * (W >> 3);
+        u->bott = dmalloc<bf16>(u, (size_t)(P3 * (C << 3)), &st);
+        u->bott_pre = dmalloc<bf16>(u, (size_t)(P3 * (C << 3)), &st);
+        u->g_bott = dmalloc<float>(u, (size_t)(P3 * (C << 3)), &st);
+    }
+    maxdz = maxdz > (size_t)(P0 * 16) ? maxdz : (size_t)(P0 * 16);
+    u->dz = dmalloc<bf16>(u, maxdz, &st);
+    if (!st) {
+        // Kaiming-normal weights (std sqrt(2 / fan_in)), zero biases, in the
+        // logical entries of each padded row
+        std::vector<float> hw(off, 0.0f);
+        Rng rng{seed * 0x9E3779B97F4A7C15ull + 12345u};
+        for (const Layer &L : u->layers) {
+            int taps = L.kind == K_CONV3 ? 9 : 1;
+            int fan = (L.kind == K_CONVT ? 1 : taps) * L.cin;
+            double sd = std::sqrt(2.0 / fan);
+            if (L.kind == K_CONV1) sd *= 0.1;   // small initial increments
+            for (int n = 0; n < L.ncols; ++n)
+                for (int t = 0; t < taps; ++t)
+                    for (int c = 0; c < L.cin; ++c) hw[L.woff + (size_t)n * L.Kp + t * L.cin_p + c] = (float)(sd * rng.normal());
+        }
+        st = cudaMemcpy(u->w, hw.data(), off * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess ? SWOF_OK : SWOF_ECUDA;
+        std::vector<float> nrm(48, 0.0f);
+        for (int c = 0; c < 16; ++c) {
+            nrm[16 + c] = 1.0f;
+            nrm[32 + c] = 1.0f;
+        }
+        if (!st) st = cudaMemcpy(u->norm, nrm.data(), 48 * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess ? SWOF_OK : SWOF_ECUDA;
+        if (!st) st = refresh_weights(u, nullptr);
+        if (!st) st = cudaDeviceSynchronize() == cudaSuccess ? SWOF_OK : SWOF_ECUDA;
+    }
+    if (st) {
+        swof_unet_destroy(u);
+        return st;
+    }
+    *out = u;
+    return SWOF_OK;
+}
+
+void swof_unet_destroy(swof_unet *u)
+{
+    if (!u) return;
+    cudaDeviceSynchronize();
+    for (void *p : u->allocs) cudaFree(p);
+    delete u;
+}
+
+long long swof_unet_param_count(const swof_unet *u) { return u ? (long long)u->nparam : 0; }
+
+int swof_unet_layout(const swof_unet *u, int layer, int *info)
+{
+    if (!u || !info || layer < 0 || layer >= (int)u->layers.size()) return SWOF_EINVAL;
+    const Layer &L = u->layers[(size_t)layer];
+    info[0] = L.kind;
+    info[1] = L.cin;
+    info[2] = L.cin_p;
+    info[3] = L.cout;
+    info[4] = L.ncols;
+    info[5] = L.Kp;
+    info[6] = (int)L.woff;
+    info[7] = (int)L.boff;
+    info[8] = L.act;
+    return (int)u->layers.size();
+}
+
+int swof_unet_get_params(swof_unet *u, float *host)
+{
+    if (!u || !host) return SWOF_EINVAL;
+    return cudaMemcpy(host, u->w, u->nparam * sizeof(float), cudaMemcpyDeviceToHost) == cudaSuccess ? SWOF_OK : SWOF_ECUDA;
+}
+
+int swof_unet_set_params(swof_unet *u, const float *host)
+{
+    if (!u || !host) return SWOF_EINVAL;
+    if (cudaMemcpy(u->w, host, u->nparam * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) return SWOF_ECUDA;
+    int st = refresh_weights(u, nullptr);
+    return st ? st : (cudaDeviceSynchronize() == cudaSuccess ? SWOF_OK : SWOF_ECUDA);
+}
+
+int swof_unet_get_grads(swof_unet *u, float *host)
+{
+    if (!u || !host) return SWOF_EINVAL;
+    return cudaMemcpy(host, u->g, u->nparam * sizeof(float), cudaMemcpyDeviceToHost) == cudaSuccess ? SWOF_OK : SWOF_ECUDA;
+}
+
+int swof_unet_set_norm(swof_unet *u, const float *mean, const float *scale_in, const float *scale_out)
+{
+    if (!u || !mean || !scale_in || !scale_out) return SWOF_EINVAL;
+    std::vector<float> nrm(48, 0.0f);
+    for (int c = 0; c < 16; ++c) {
+        nrm[16 + c] = 1.0f;
+        nrm[32 + c] = 1.0f;
+    }
+    for (int c = 0; c < u->in_ch; ++c) {
+        if (!(scale_in[c] > 0.0f)) return SWOF_EINVAL;
+        nrm[c] = mean[c];
+        nrm[16 + c] = 1.0f / scale_in[c];
+    }
+    for (int c = 0; c < u->out_ch; ++c) {
+        if (!(scale_out[c] > 0.0f)) return SWOF_EINVAL;
+        nrm[32 + c] = scale_out[c];
+    }
+    return cudaMemcpy(u->norm, nrm.data(), 48 * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess ? SWOF_OK : SWOF_ECUDA;
+}
+
+// Forward on raw network inputs: x bf16 [B*H*W][16] (device) -> out fp32 [B*H*W][16] (device).
+int swof_unet_forward_raw(swof_unet *u, const void *x, int B, float *y, void *stream)
+{
+    if (!u || !x || !y || B < 1 || B > u->maxB) return SWOF_EINVAL;
+    cudaStream_t s = S(stream);
+    long long P = (long long)B * u->H * u->W;
+    if (cudaMemcpyAsync(u->x0, x, (size_t)P * 16 * sizeof(bf16), cudaMemcpyDeviceToDevice, s) != cudaSuccess) return SWOF_ECUDA;
+    int st = forward(u, B, s);
+    if (st) return st;
+    return cudaMemcpyAsync(y, u->out, (size_t)P * 16 * sizeof(float), cudaMemcpyDeviceToDevice, s) == cudaSuccess ? SWOF_OK : SWOF_ECUDA;
+}
+
+// Loss and gradients (no update) on raw inputs and targets: x bf16
+// [P][16] and tgt fp32 [P][out_ch] (device).  Synchronises; *loss_host
+// gets the sum of squared errors (nullable).
+int swof_unet_grads_raw(swof_unet *u, const void *x, const float *tgt, int B, double *loss_host, void *stream)
+{
+    if (!u || !x || !tgt || B < 1 || B > u->maxB) return SWOF_EINVAL;
+    cudaStream_t s = S(stream);
+    long long P = (long long)B * u->H * u->W;
+    cudaMemsetAsync(u->err, 0, sizeof(int), s);
+    if (cudaMemcpyAsync(u->x0, x, (size_t)P * 16 * sizeof(bf16), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(u->tgt, tgt, (size_t)P * u->out_ch * sizeof(float), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return SWOF_ECUDA;
+    int st = loss_and_grads(u, B, s);
+    return st ? st : read_status(u, s, loss_host);
+}
+
+// Diagnostics: copy an internal activation of the last forward (bf16 or
+// fp32) to host as fp32.  which: 0 input x0, 1 ea, 2 ea_pre, 3 cat, 4 pool,
+// 5 da, 6 db, 7 bottom, 8 output; level l; n values.
+int swof_unet_activation(swof_unet *u, int which, int l, float *host, long long n)
+{
+    if (!u || !host || n < 0 || l < 0 || l > 3) return SWOF_EINVAL;
+    const void *src = nullptr;
+    bool isbf = true;
+    switch (which) {
+    case 0: src = u->x0; break;
+    case 1: src = u->ea[l]; break;
+    case 2: src = u->ea_pre[l]; break;
+    case 3: src = u->cat[l]; break;
+    case 4: src = u->pool[l]; break;
+    case 5: src = u->da[l]; break;
+    case 6: src = u->db[l]; break;
+    case 7: src = u->bott; break;
+    case 8: src = u->out; isbf = false; break;
+    default: return SWOF_EINVAL;
+    }
+    if (!src) return SWOF_EINVAL;
+    if (cudaDeviceSynchronize() != cudaSuccess) return SWOF_ECUDA;
+    if (!isbf) return cudaMemcpy(host, src, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost) == cudaSuccess ? SWOF_OK : SWOF_ECUDA;
+    std::vector<uint16_t> tmp((size_t)n);
+    if (cudaMemcpy(tmp.data(), src, (size_t)n * 2, cudaMemcpyDeviceToHost) != cudaSuccess) return SWOF_ECUDA;
+    for (long long i = 0; i < n; ++i) {
+        uint32_t b = (uint32_t)tmp[(size_t)i] << 16;
+        std::memcpy(&host[i], &b, 4);
+    }
+    return SWOF_OK;
+}
+
+// One AdamW update of the FP32 master weights from the current gradients.
+int swof_unet_adamw(swof_unet *u, float lr, float beta1, float beta2, float eps, float weight_decay, void *stream)
+{
+    if (!u || !(lr >= 0.0f)) return SWOF_EINVAL;
+    return adamw(u, lr, beta1, beta2, eps, weight_decay, S(stream));
+}
+
+// Training step on states: in [B][in_ch][H][W] (h, hu, hv, z), next
+// [B][out_ch][H][W] (h, hu, hv a span later), FP32 device.  The network
+// learns (next - in) / scale_out from (in - mean) / scale_in.
+int swof_surrogate_train_step(swof_unet *u, const float *in, const float *next, int B, float lr, float weight_decay,
+                              double *loss_host, void *stream)
+{
+    if (!u || !in || !next || B < 1 || B > u->maxB) return SWOF_EINVAL;
+    cudaStream_t s = S(stream);
+    long long P = (long long)B * u->H * u->W;
+    cudaMemsetAsync(u->err, 0, sizeof(int), s);
+    swof::k_pack_input<<<swof::grid_for(P * 16), 256, 0, s>>>(in, u->in_ch, B, u->H, u->W, u->norm, u->norm + 16, u->x0);
+    swof::k_target<<<swof::grid_for(P * u->out_ch), 256, 0, s>>>(in, u->in_ch, next, u->out_ch, B, u->H, u->W,
+                                                                   u->norm + 32, u->tgt);
+    int st = loss_and_grads(u, B, s);
+    if (!st) st = adamw(u, lr, 0.9f, 0.999f, 1e-8f, weight_decay, s);
+    return st ? st : read_status(u, s, loss_host);
+}
+
+// Prediction: out[b] = in[b][0:out_ch] + scale_out * net((in - mean) / scale_in), FP32 device.
+int swof_surrogate_predict(swof_unet *u, const float *in, int B, float *out, void *stream)
+{
+    if (!u || !in || !out || B < 1 || B > u->maxB) return SWOF_EINVAL;
+    cudaStream_t s = S(stream);
+    long long P = (long long)B * u->H * u->W;
+    swof::k_pack_input<<<swof::grid_for(P * 16), 256, 0, s>>>(in, u->in_ch, B, u->H, u->W, u->norm, u->norm + 16, u->x0);
+    int st = forward(u, B, s);
+    if (st) return st;
+    swof::k_residual<<<swof::grid_for((long long)B * u->out_ch * u->H * u->W), 256, 0, s>>>(
+        in, u->in_ch, u->out, u->out_ch, B, u->H, u->W, u->norm + 32, out);
+    return cudaGetLastError() == cudaSuccess ? SWOF_OK : SWOF_ECUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+"""Surrogate U-Net on the tcgen05 tensor cores vs the numpy reference
+(needs a GPU).  The reference rounds to bf16 where the GPU stores bf16, so
+the two differ only by FP32 vs FP64 accumulation (and an occasional bf16
+rounding flip): forward and gradients agree to ~1e-2 relative L2."""
+import numpy as np
+import pytest
+
+import paper_1307_4839_gb300 as sw
+from oracle.unet_ref import UNetRef
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import torch
+    assert torch.cuda.is_available()
+    sw.build()
+    sw.load()
+    C, H, B = 16, 32, 2
+    net = sw.UNet(base=C, in_ch=4, out_ch=3, H=H, W=H, max_batch=B, seed=3)
+    rng = np.random.default_rng(1)
+    # give the biases and the output layer some weight so every path matters
+    p = net.params()
+    lay = net.layout()
+    for d in lay:
+        p[d["boff"]: d["boff"] + d["cout"]] = 0.1 * rng.standard_normal(d["cout"]).astype(np.float32)
+    d = lay[-1]
+    p[d["woff"]: d["woff"] + d["ncols"] * d["Kp"]] *= 10.0
+    net.set_params(p)
+    x = np.zeros((B, H, H, 16), dtype=np.float32)
+    x[..., :4] = rng.standard_normal((B, H, H, 4))
+    tgt = rng.standard_normal((B, H, H, 3)).astype(np.float32)
+    return net, p, x, tgt, C, H, B
+
+
+def test_layout_matches_reference(setup):
+    net, p, x, tgt, C, H, B = setup
+    from oracle.unet_ref import layers_spec
+    spec, n = layers_spec(C, 4, 3)
+    assert n == net.nparam
+    for a, b in zip(net.layout(), spec):
+        for k in ("kind", "cin", "cin_p", "cout", "ncols", "Kp", "woff", "boff", "act"):
+            assert a[k] == b[k], k
+
+
+def test_forward_matches_reference(setup):
+    import torch
+    net, p, x, tgt, C, H, B = setup
+    dx = torch.tensor(x.reshape(-1, 16), device="cuda").to(torch.bfloat16).contiguous()
+    y = torch.zeros((B * H * H, 16), device="cuda")
+    net.forward_raw(dx, y)
+    torch.cuda.synchronize()
+    ref, _ = UNetRef(C, 4, 3, p.astype(np.float64), use_bf16=True).forward(x.astype(np.float64))
+    got = y.cpu().numpy().reshape(B, H, H, 16)
+    assert np.all(np.isfinite(got))
+    assert rel_l2(got, ref) < 2e-2, rel_l2(got, ref)
+
+
+def test_gradients_match_reference(setup):
+    import torch
+    net, p, x, tgt, C, H, B = setup
+    dx = torch.tensor(x.reshape(-1, 16), device="cuda").to(torch.bfloat16).contiguous()
+    dt = torch.tensor(tgt.reshape(-1, 3), device="cuda").contiguous()
+    loss = net.grads_raw(dx, dt)
+    g = net.grads()
+    rloss, rg = UNetRef(C, 4, 3, p.astype(np.float64), use_bf16=True).loss_and_grads(x.astype(np.float64),
+                                                                                    tgt.astype(np.float64))
+    assert abs(loss - rloss) <= 2e-2 * rloss
+    for k, d in enumerate(net.layout()):
+        w = slice(d["woff"], d["woff"] + d["ncols"] * d["Kp"])
+        b = slice(d["boff"], d["boff"] + d["cout"])
+        assert rel_l2(g[w], rg[w]) < 5e-2, (k, rel_l2(g[w], rg[w]))
+        assert rel_l2(g[b], rg[b]) < 5e-2, (k, rel_l2(g[b], rg[b]))
+
+
+def test_training_reduces_loss():
+    import torch
+    sw.build()
+    C, H, B = 16, 32, 4
+    net = sw.UNet(base=C, in_ch=4, out_ch=3, H=H, W=H, max_batch=B, seed=5)
+    rng = np.random.default_rng(2)
+    yy, xx = np.meshgrid(np.arange(H), np.arange(H), indexing="ij")
+    state = np.zeros((B, 4, H, H), dtype=np.float32)
+    for b in range(B):
+        state[b, 0] = 1.0 + 0.3 * np.sin(2 * np.pi * (xx + 3 * b) / H)
+        state[b, 3] = 0.1 * np.cos(2 * np.pi * yy / H)
+    nxt = state[:, :3].copy()
+    nxt[:, 0] += 0.05 * np.roll(state[:, 0], 1, axis=-1) - 0.05
+    dsi = torch.tensor(state, device="cuda")
+    dsn = torch.tensor(nxt, device="cuda")
+    net.set_norm(mean=[1.0, 0.0, 0.0, 0.0], scale_in=[0.3, 1.0, 1.0, 0.1], scale_out=[0.05, 0.05, 0.05])
+    losses = [net.train_step(dsi, dsn, lr=2e-3) for _ in range(60)]
+    assert losses[-1] < 0.2 * losses[0], (losses[0], losses[-1])
+    out = torch.zeros_like(dsn)
+    net.predict(dsi, out)
+    torch.cuda.synchronize()
+    err = np.abs(out.cpu().numpy() - nxt).mean() / np.abs(nxt - state[:, :3]).mean()
+    assert err < 0.5, err
