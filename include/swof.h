@@ -325,6 +325,69 @@ SWOF_API int swof_surrogate_train_step(swof_unet *u, const float *in, const floa
                                        float weight_decay, double *loss_host, void *stream);
 SWOF_API int swof_surrogate_predict(swof_unet *u, const float *in, int B, float *out, void *stream);
 
+/* Coarsen a context's state: block means of h, hu, hv and the infiltrated
+ * depth V_inf over f x f cells (FP64 sums) into out, a device fp32 array
+ * [4][ny/f][nx/f] (nx, ny multiples of f), enqueued on the context's
+ * stream.  The surrogate's training data and its judge (the fine solver,
+ * coarsened).  Errors: SWOF_EINVAL. */
+SWOF_API int swof_coarsen(swof_ctx *ctx, int f, float *out);
+
+/* Per-member FP64 statistics of a batch of states [B][C][H][W] (device
+ * fp32; channels h, hu, hv, then V_inf when C >= 4) into the device array
+ * out[5B]: out[5b..5b+4] = {sum h, sum min(h, 0), discharge leaving through
+ * the edges in outmask [m^3/s], sum V_inf (0 when C < 4), min h}.  outmask
+ * bits: 1 W, 2 E, 4 S, 8 N (the edge order of swof_params.bc); discharge is
+ * the normal q of the edge cells times the edge length (dx or dy).
+ * Fixed-order sums (deterministic).  Enqueued on stream. */
+SWOF_API int swof_batch_stats(const float *states, int B, int C, int H, int W, int outmask, double dx,
+                              double dy, double *out, void *stream);
+
+/* Rollout: advance B coarse members `calls` times by one span each with
+ * the network, checking every prediction and falling back to the plain
+ * solver where the check fails.
+ *   states      device fp32 [B][in_ch][H][W]: channels 0..out_ch-1 are the
+ *               state (h, hu, hv[, V_inf]), the rest the network's other
+ *               inputs; updated in place (the rain channel gets the rain
+ *               rate of each member's next span, averaged over its steps).
+ *   t           host [B]: each member's time, advanced by span per call.
+ *   rain        host [B][3]: rain rate [m/s], t_on, t_off per member.
+ *   fallback    host array of contexts on the same H x W grid (W = nx),
+ *               FP64 or FP32, created with dt_fixed = span / fallback_steps
+ *               and the member's z, friction, rain, infiltration and edges;
+ *               fallback_of[b] indexes it (members may share a context: it is
+ *               reset from the member's state, V_inf and time before use).
+ *   accepted    host [calls][B] (nullable): 1 where the prediction passed.
+ *   checks      host [calls][B][2] (nullable): mass and positivity errors.
+ * Check (after the prediction, before any clamp), relative to the water
+ * present plus the span's rain, with area A = dx dy per cell:
+ *   mass       |dV - (rain in - (V_inf increase) A - discharge out)| <= tol,
+ *              the discharge the trapezoid of the edge discharge before and
+ *              after, the rain that of the fallback_steps steps of the span
+ *              (rain falls in a step that starts in [t_on, t_off));
+ *   positivity -sum min(h, 0) A <= tol.
+ * Passing members take the prediction with h < 0 set to 0, q = 0 where
+ * h <= h_dry and V_inf never decreasing; the others take the solver's
+ * state after fallback_steps steps.  Synchronises once per call.  Errors:
+ * SWOF_EINVAL; SWOF_ESTATE if a failing member has no fallback (it stays
+ * at its pre-call state and time; the rollout stops after that call); a
+ * fallback context's own error.  inject_* is a test hook: add inject_dh to
+ * member inject_member's predicted depth at call inject_call (-1: off). */
+typedef struct swof_rollout_opts {
+    int calls;
+    int fallback_steps;
+    double span;
+    double dx, dy;
+    double tol;
+    double h_dry;
+    int rain_channel;          /* input channel of the rain rate, or -1 */
+    int outflow_mask;          /* edges where water leaves (bits as above) */
+    int inject_member, inject_call;
+    double inject_dh;
+} swof_rollout_opts;
+SWOF_API int swof_surrogate_rollout(swof_unet *u, float *states, int B, double *t, const double *rain,
+                                    swof_ctx *const *fallback, const int *fallback_of,
+                                    const swof_rollout_opts *opts, int *accepted, double *checks, void *stream);
+
 /* Human-readable text for a status code (static storage). */
 SWOF_API const char *swof_strerror(int code);
 

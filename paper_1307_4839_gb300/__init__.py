@@ -132,6 +132,10 @@ _SIGS = {
                                                  ctypes.c_void_p]),
     "swof_surrogate_predict": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                               ctypes.c_void_p]),
+    "swof_coarsen": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "swof_batch_stats": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 5 + [ctypes.c_double] * 2
+                         + [ctypes.c_void_p, ctypes.c_void_p]),
+    "swof_surrogate_rollout": (ctypes.c_int, [ctypes.c_void_p] * 2 + [ctypes.c_int] + [ctypes.c_void_p] * 8),
     "swof_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "swof_version": (ctypes.c_char_p, []),
 }
@@ -323,6 +327,11 @@ class Solver:
         _check(load().swof_get_timing(self._ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
                                       ctypes.byref(n)), "swof_get_timing")
         return {"lambda_ms": a.value, "stage1_ms": b.value, "stage2_ms": c.value, "launches": n.value}
+
+    def coarsen(self, f: int, out):
+        """Block means of (h, hu, hv, V_inf) over f x f cells into the torch
+        tensor out [4][ny/f][nx/f] (float32, CUDA), on the context's stream."""
+        _check(load().swof_coarsen(self._ctx, int(f), ctypes.c_void_p(out.data_ptr())), "swof_coarsen")
 
     def use_graph(self, on=True):
         _check(load().swof_use_graph(self._ctx, int(bool(on))), "swof_use_graph")
@@ -577,3 +586,47 @@ class UNet:
         _check(load().swof_surrogate_predict(self._u, ctypes.c_void_p(state_in.data_ptr()), int(state_in.shape[0]),
                                              ctypes.c_void_p(out.data_ptr()), self._s(stream)),
                "swof_surrogate_predict")
+
+
+def batch_stats(states, out, outmask=0, dx=1.0, dy=1.0, stream=None):
+    """Per-member {sum h, sum min(h, 0), discharge out [m^3/s], sum V_inf,
+    min h} of states [B][C][H][W] (float32 CUDA) into out [B][5] (float64
+    CUDA); outmask bits 1 W, 2 E, 4 S, 8 N."""
+    B, C, H, W = states.shape
+    _check(load().swof_batch_stats(ctypes.c_void_p(states.data_ptr()), int(B), int(C), int(H), int(W), int(outmask),
+                                   float(dx), float(dy), ctypes.c_void_p(out.data_ptr()),
+                                   None if stream is None else ctypes.c_void_p(stream)),
+           "swof_batch_stats")
+
+
+class RolloutOpts(ctypes.Structure):
+    _fields_ = [("calls", ctypes.c_int), ("fallback_steps", ctypes.c_int), ("span", ctypes.c_double),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("tol", ctypes.c_double),
+                ("h_dry", ctypes.c_double), ("rain_channel", ctypes.c_int), ("outflow_mask", ctypes.c_int),
+                ("inject_member", ctypes.c_int), ("inject_call", ctypes.c_int), ("inject_dh", ctypes.c_double)]
+
+
+def rollout(net, states, t, rain, fallback, fallback_of, *, calls, span, fallback_steps, dx, dy, tol=1e-3,
+            h_dry=1e-6, rain_channel=-1, outflow_mask=0, inject=None, stream=None):
+    """swof_surrogate_rollout: advance the members in `states` (float32 CUDA
+    [B][in_ch][H][W], updated in place) by `calls` network calls with the
+    positivity / mass check and per-member fallback to the solvers in
+    `fallback` (Solver list; fallback_of[b] indexes it).  t (float64 [B]) is
+    advanced in place; rain is [B][3] (rate, t_on, t_off).  Returns
+    (accepted [calls][B] int, checks [calls][B][2] float64)."""
+    B = states.shape[0]
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    rain = np.ascontiguousarray(rain, dtype=np.float64).reshape(B, 3)
+    fb = (ctypes.c_void_p * max(len(fallback), 1))(*[f._ctx.value for f in fallback])
+    fo = np.ascontiguousarray(fallback_of, dtype=np.int32)
+    o = RolloutOpts(int(calls), int(fallback_steps), float(span), float(dx), float(dy), float(tol), float(h_dry),
+                    int(rain_channel), int(outflow_mask), -1, -1, 0.0)
+    if inject is not None:
+        o.inject_member, o.inject_call, o.inject_dh = int(inject[0]), int(inject[1]), float(inject[2])
+    acc = np.zeros((max(calls, 1), B), dtype=np.int32)
+    chk = np.zeros((max(calls, 1), B, 2))
+    st = load().swof_surrogate_rollout(net._u, ctypes.c_void_p(states.data_ptr()), int(B), t.ctypes.data,
+                                       rain.ctypes.data, fb, fo.ctypes.data, ctypes.byref(o), acc.ctypes.data,
+                                       chk.ctypes.data, None if stream is None else ctypes.c_void_p(stream))
+    _check(st, "swof_surrogate_rollout")
+    return acc[:calls], chk[:calls], t

@@ -623,6 +623,11 @@ int read_status(swof_unet *u, cudaStream_t s, double *loss_host)
     return err ? SWOF_ETIMEOUT : SWOF_OK;
 }
 
+void swof_unet_dims(const swof_unet *u, int *d)
+{
+    d[0] = u->in_ch, d[1] = u->out_ch, d[2] = u->H, d[3] = u->W, d[4] = u->maxB;
+}
+
 extern "C" {
 
 int swof_unet_create(int base, int in_ch, int out_ch, int H, int W, int max_batch, unsigned long long seed,
