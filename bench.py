@@ -67,6 +67,11 @@ def parse():
     ap.add_argument("--no-wet", action="store_true")
     ap.add_argument("--ens-members", type=int, default=256)
     ap.add_argument("--ens-steps", type=int, default=1000)
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--sur-train-traj", type=int, default=27, help="training trajectories (750 pairs each)")
+    ap.add_argument("--sur-steps", type=int, default=2000, help="training steps (batch 16)")
+    ap.add_argument("--sur-calls", type=int, default=50)
+    ap.add_argument("--sur-members", type=int, default=512)
     return ap.parse_args()
 
 
@@ -77,6 +82,13 @@ def peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return FALLBACK_HBM_GBS, "fallback"
+
+
+def bf16_peak() -> float:
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except Exception:
+        return 1900.0
 
 
 def recorded_traffic(kernel: str, precision: str):
@@ -329,6 +341,132 @@ def measure_ensemble(sw, torch, args, ws):
             "accuracy": "per-member relative L1 vs the FP64 oracle in tests/test_gpu_ensemble.py"}
 
 
+def unet_flops(layout, H: int) -> float:
+    """Multiply-adds x 2 of one forward sample over the real (unpadded)
+    channels: the algorithmic FLOPs of the network."""
+    level = [0, 0, 1, 1, 2, 2, 3, 3, 3, 2, 2, 2, 1, 1, 1, 0, 0, 0]
+    fl = 0.0
+    for l, d in enumerate(layout):
+        taps = 9 if d["kind"] == 0 else 1
+        fl += 2.0 * d["ncols"] * taps * d["cin"] * (H >> level[l]) ** 2
+    return fl
+
+
+def measure_surrogate(sw, torch, args, peak_tf):
+    """The learned surrogate on coarsened rainfall-runoff hillslopes.
+
+    Fine scenarios: 1024^2 hillslopes (dx 1 m, slope 0.05, furrows, noise,
+    lognormal K_s, Green-Ampt, Manning 0.05, outflow downslope) with rain
+    U(30, 80) mm/h for 600 s, stepped 1200 s at a fixed dt of 0.1 s (CFL
+    checked each step) by the FP32 solver; every 16 steps (1.6 s) the state
+    is coarsened 4 x 4 to 256^2.  27 training trajectories give 20,250
+    pairs; 4 more are held out.  The base-32 U-Net is trained on the GPU,
+    then 512 held-out members (4 trajectories x 128 start times) are rolled
+    50 calls (800 fine steps each) with the checks and the fallback.  The
+    accuracy judge is the fine solver coarsened (FP32 for all members, FP64
+    for the members of one trajectory)."""
+    import numpy as np
+    from paper_1307_4839_gb300 import surrogate as S
+    n, f, dt, span_steps, n_spans = 1024, 4, 0.1, 16, 750
+    n_tr, n_te = args.sur_train_traj, 4
+    rng = np.random.default_rng(11)
+    rain = rng.uniform(30.0, 80.0, n_tr + n_te)
+    works = S.hillslope_works(n, seeds=range(n_tr + n_te), rain_mm_h=rain, rain_s=600.05)
+    t0 = time.perf_counter()
+    ds = S.generate(works, f, dt, span_steps, n_spans)
+    gen_s = time.perf_counter() - t0
+    pairs = ds.pairs(range(n_tr))
+    net = S.make_net(ds, pairs, base=32, max_batch=32, seed=0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    t0 = time.perf_counter()
+    losses = S.train(net, ds, pairs, steps=args.sur_steps, batch=16, lr=2e-3, seed=0, stream=stream.cuda_stream)
+    train_s = time.perf_counter() - t0
+    per = max(1, args.sur_members // n_te)
+    span_max = n_spans - args.sur_calls
+    starts = [int(round(k * span_max / per)) for k in range(per)]
+    members = [(n_tr + i, k) for i in range(n_te) for k in starts][: args.sur_members]
+    ro = S.Rollout(ds, net, members)
+    start = ro.states[:, :S.OUT_CH].clone()
+    # untimed first call on a copy (graph capture of the fallback solvers)
+    warm = S.Rollout(ds, net, members[:32])
+    warm.run(1, stream=stream.cuda_stream)
+    warm.close()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    acc, chk = ro.run(args.sur_calls, stream=stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    judge = ro.judge()
+    e_sur = S.rel_l1(ro.states, judge)
+    e_per = S.rel_l1(start, judge)
+    e_crs = S.rel_l1(S.coarse_baseline(ds, members, args.sur_calls), judge)
+    # FP64 judge for the members of the first held-out trajectory
+    k_need = max(k for a, k in members if a == n_tr) + args.sur_calls
+    ds64 = S.generate([works[n_tr]], f, dt, span_steps, k_need, precision=sw.FP64)
+    sel = [b for b, (a, _) in enumerate(members) if a == n_tr]
+    idx = torch.tensor([k + args.sur_calls for a, k in members if a == n_tr], device="cuda")
+    j64 = ds64.data[0].index_select(0, idx)[:, :S.OUT_CH]
+    e_sur64 = S.rel_l1(ro.states[sel], j64)
+    e_judge = S.rel_l1(judge[sel], j64)
+    ro.close()
+    # forward throughput of the network alone (tensor cores)
+    B = 32
+    x = ro.states[:B].contiguous()
+    y = torch.empty((B, S.OUT_CH) + tuple(x.shape[-2:]), device="cuda")
+    for _ in range(2):
+        net.predict(x, y, stream=stream.cuda_stream)
+    e0.record(stream)
+    for _ in range(5):
+        net.predict(x, y, stream=stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / 5
+    fl = unet_flops(net.layout(), x.shape[-1])
+    # the plain fine solvers on one of these scenarios
+    plain = {}
+    for name, prec, k in (("fp64", sw.FP64, 48), ("fp32", sw.FP32, 480)):
+        s_ = sw.Solver.from_workload(works[n_tr], prec, dt_fixed=dt, t_end=1e30, stream=stream.cuda_stream)
+        s_.step(16)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s_.step(k, sync=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plain[name] = n * n * k / (e0.elapsed_time(e1) * 1e-3) * 1e-9
+        s_.close()
+    spans = len(members) * args.sur_calls
+    eff = spans * span_steps * n * n / (ms * 1e-3) * 1e-9
+    ch = ["h", "hu", "hv", "V_inf"]
+    out = {"value": eff, "unit": UNIT + " (fine-grid equivalent)",
+           "what": "512 members x 50 calls of the BF16 tcgen05 U-Net on 4x-coarsened 1024^2 hillslopes, "
+                   "positivity/mass check each call, per-member fallback to the coarse solver",
+           "member_spans_per_s": spans / (ms * 1e-3), "ms_total": ms, "members": len(members),
+           "calls": args.sur_calls, "fine_steps_per_call": span_steps,
+           "accepted_fraction": float(acc.mean()), "worst_check": float(chk.max()),
+           "over_plain_fp64": eff / plain["fp64"], "over_plain_fp32": eff / plain["fp32"],
+           "plain_fp64_fine": plain["fp64"], "plain_fp32_fine": plain["fp32"],
+           "rel_l1_vs_fine_fp32": dict(zip(ch, map(float, e_sur))),
+           "rel_l1_vs_fine_fp64_one_traj": dict(zip(ch, map(float, e_sur64))),
+           "fp32_judge_vs_fp64": dict(zip(ch, map(float, e_judge))),
+           "persistence_rel_l1": dict(zip(ch, map(float, e_per))),
+           "coarse_solver_rel_l1": dict(zip(ch, map(float, e_crs))),
+           "training": {"pairs": int(len(pairs)), "steps": args.sur_steps, "batch": 16, "s": train_s,
+                        "loss_first": float(losses[:20].mean()), "loss_last": float(losses[-20:].mean()),
+                        "params": net.nparam},
+           "data_generation_s": gen_s,
+           "unet_forward": {"batch": B, "ms": fwd_ms, "tflops": fl * B / (fwd_ms * 1e-3) * 1e-12,
+                            "frac_of_bf16_peak": fl * B / (fwd_ms * 1e-3) * 1e-12 / peak_tf,
+                            "gflop_per_sample": fl * 1e-9}}
+    net.close()
+    del ds, ds64
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
@@ -402,6 +540,9 @@ def main():
 
     if not args.no_ensemble and P == "fp32":
         variants["ensemble"] = measure_ensemble(sw, torch, args, ws)
+
+    if not args.no_surrogate and P == "fp32":
+        variants["surrogate"] = measure_surrogate(sw, torch, args, bf16_peak())
 
 
     e2e = None

@@ -144,7 +144,13 @@ SWOF_API int swof_get_state_device(swof_ctx *ctx, void *h, void *hu, void *hv, i
 SWOF_API int swof_get_infiltrated(swof_ctx *ctx, double *vinf);
 SWOF_API int swof_set_infiltrated(swof_ctx *ctx, const double *vinf);
 
-/* Simulated time (FP64); resets nothing else. */
+/* V_inf from / to a dense device array [ny][nx] of dtype (SWOF_FP64 or
+ * SWOF_FP32), enqueued on the context stream; no validation of values. */
+SWOF_API int swof_set_infiltrated_device(swof_ctx *ctx, const void *vinf, int dtype);
+SWOF_API int swof_get_infiltrated_device(swof_ctx *ctx, void *vinf, int dtype);
+
+/* Simulated time (FP64), enqueued on the context stream (ordered before
+ * later steps); resets nothing else. */
 SWOF_API int swof_set_time(swof_ctx *ctx, double t);
 
 /* Advance n full Heun steps (Algorithm 1), each with one dt from Eq. (cfl)

@@ -132,6 +132,8 @@ _SIGS = {
                                                  ctypes.c_void_p]),
     "swof_surrogate_predict": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                               ctypes.c_void_p]),
+    "swof_set_infiltrated_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "swof_get_infiltrated_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "swof_coarsen": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "swof_batch_stats": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 5 + [ctypes.c_double] * 2
                          + [ctypes.c_void_p, ctypes.c_void_p]),
@@ -288,6 +290,17 @@ class Solver:
     def set_infiltrated(self, v):
         v = _f64(v)
         _check(load().swof_set_infiltrated(self._ctx, _ptr(v)), "swof_set_infiltrated")
+
+    def set_infiltrated_device(self, v):
+        """torch CUDA tensor (float64 or float32), contiguous [ny][nx]."""
+        dt = FP64 if str(v.dtype) == "torch.float64" else FP32
+        _check(load().swof_set_infiltrated_device(self._ctx, ctypes.c_void_p(v.data_ptr()), dt),
+               "swof_set_infiltrated_device")
+
+    def get_infiltrated_device(self, v):
+        dt = FP64 if str(v.dtype) == "torch.float64" else FP32
+        _check(load().swof_get_infiltrated_device(self._ctx, ctypes.c_void_p(v.data_ptr()), dt),
+               "swof_get_infiltrated_device")
 
     def set_time(self, t):
         _check(load().swof_set_time(self._ctx, float(t)), "swof_set_time")

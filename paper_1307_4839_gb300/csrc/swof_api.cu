@@ -398,9 +398,10 @@ void swof_destroy(swof_ctx *c)
 
 static int clear_status(swof_ctx *c)
 {
-    int zero = 0;
-    return cuda_err(cudaMemcpyAsync(&c->ctl->status, &zero, sizeof zero, cudaMemcpyHostToDevice, c->stream));
+    return cuda_err(cudaMemsetAsync(&c->ctl->status, 0, sizeof c->ctl->status, c->stream));
 }
+
+__global__ void k_set_time(DevCtl *ctl, double t) { ctl->t = t; }
 
 int swof_set_state(swof_ctx *c, const double *h, const double *hu, const double *hv)
 {
@@ -481,9 +482,8 @@ int swof_set_infiltrated(swof_ctx *c, const double *v)
 int swof_set_time(swof_ctx *c, double t)
 {
     if (!c || !std::isfinite(t)) return SWOF_EINVAL;
-    cudaError_t e = cudaMemcpyAsync(&c->ctl->t, &t, sizeof t, cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    return cuda_err(e);
+    k_set_time<<<1, 1, 0, c->stream>>>(c->ctl, t);
+    return cuda_err(cudaGetLastError());
 }
 
 int swof_step(swof_ctx *c, int n, swof_step_info *info)

@@ -123,6 +123,39 @@ __global__ void k_commit(float *st, int C, const float *pred, int Co, long long 
     }
 }
 
+// V_inf interior <-> dense [ny][nx] array of type S
+template <typename T, typename S, bool TO_FIELD>
+__global__ void k_vinf_copy(Params P, T *vinf, S *d)
+{
+    const long long n = (long long)P.nx * P.ny;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(i / P.nx), x = (int)(i - (long long)j * P.nx);
+        T &f = vinf[(size_t)(j + 2) * P.pitch + (size_t)(x + P.lpad)];
+        if (TO_FIELD)
+            f = (T)d[i];
+        else
+            d[i] = (S)f;
+    }
+}
+
+template <bool TO_FIELD>
+int vinf_copy(swof_ctx *c, void *d, int dtype)
+{
+    const int g = grid_for((long long)c->P.nx * c->P.ny);
+    if (c->prec == SWOF_FP64) {
+        if (dtype == SWOF_FP64)
+            k_vinf_copy<double, double, TO_FIELD><<<g, 256, 0, c->stream>>>(c->P, c->f64.vinf, (double *)d);
+        else
+            k_vinf_copy<double, float, TO_FIELD><<<g, 256, 0, c->stream>>>(c->P, c->f64.vinf, (float *)d);
+    } else {
+        if (dtype == SWOF_FP64)
+            k_vinf_copy<float, double, TO_FIELD><<<g, 256, 0, c->stream>>>(c->P, c->f32.vinf, (double *)d);
+        else
+            k_vinf_copy<float, float, TO_FIELD><<<g, 256, 0, c->stream>>>(c->P, c->f32.vinf, (float *)d);
+    }
+    return cuerr(cudaGetLastError());
+}
+
 __global__ void k_add(float *a, long long n, float v)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -141,6 +174,27 @@ double span_rain(const double *r, double t0, double span, int n)
     return r[0] * c / n;
 }
 
+// Events owned by one rollout call: one on the rollout stream, one per
+// fallback context used.
+struct Events {
+    cudaEvent_t main = nullptr;
+    std::vector<std::pair<swof_ctx *, cudaEvent_t>> ctx;
+    ~Events()
+    {
+        if (main) cudaEventDestroy(main);
+        for (auto &p : ctx) cudaEventDestroy(p.second);
+    }
+    cudaEvent_t of(swof_ctx *c)
+    {
+        for (auto &p : ctx)
+            if (p.first == c) return p.second;
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+        ctx.emplace_back(c, e);
+        return e;
+    }
+};
+
 struct Scratch {
     std::vector<void *> p;
     ~Scratch()
@@ -157,30 +211,18 @@ struct Scratch {
     }
 };
 
-// Replace member b's slot of states by the plain solver's result over the
-// span: its fallback context takes the pre-call state, V_inf and time.
-int fallback_member(swof_ctx *c, float *sb, int C, long long HW, int out_ch, double t, int steps,
-                    std::vector<double> &hv, std::vector<float> &hf)
+// Enqueue, on the fallback context's stream, the plain solver's advance of
+// member slot sb over the span: the context takes the member's pre-call
+// state, V_inf and time, takes `steps` steps and writes its state back.
+int enqueue_fallback(swof_ctx *c, float *sb, int C, long long HW, int out_ch, double t, int steps)
 {
     int st = swof_set_state_device(c, sb, sb + HW, sb + 2 * HW, SWOF_FP32);
-    if (st) return st;
-    if (out_ch >= 4 && C >= 4) {
-        if (cudaMemcpy(hf.data(), sb + 3 * HW, HW * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
-            return SWOF_ECUDA;
-        for (long long i = 0; i < HW; ++i) hv[i] = hf[i];
-        if ((st = swof_set_infiltrated(c, hv.data()))) return st;
-    }
-    if ((st = swof_set_time(c, t))) return st;
-    swof_step_info info;
-    if ((st = swof_step(c, steps, &info))) return st;
-    if ((st = swof_get_state_device(c, sb, sb + HW, sb + 2 * HW, SWOF_FP32))) return st;
-    if (out_ch >= 4 && C >= 4) {
-        if ((st = swof_get_infiltrated(c, hv.data()))) return st;
-        for (long long i = 0; i < HW; ++i) hf[i] = (float)hv[i];
-        if (cudaMemcpy(sb + 3 * HW, hf.data(), HW * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
-            return SWOF_ECUDA;
-    }
-    return cuerr(cudaStreamSynchronize(c->stream));
+    if (!st && out_ch >= 4 && C >= 4) st = vinf_copy<true>(c, sb + 3 * HW, SWOF_FP32);
+    if (!st) st = swof_set_time(c, t);
+    if (!st) st = swof_step(c, steps, nullptr);
+    if (!st) st = swof_get_state_device(c, sb, sb + HW, sb + 2 * HW, SWOF_FP32);
+    if (!st && out_ch >= 4 && C >= 4) st = vinf_copy<false>(c, sb + 3 * HW, SWOF_FP32);
+    return st;
 }
 
 }  // namespace
@@ -196,6 +238,18 @@ int swof_coarsen(swof_ctx *c, int f, float *out)
     else
         k_coarsen<float><<<grid_for(n), 256, 0, c->stream>>>(c->P, c->f32, f, out);
     return cuerr(cudaGetLastError());
+}
+
+int swof_set_infiltrated_device(swof_ctx *c, const void *v, int dtype)
+{
+    if (!c || !v || (dtype != SWOF_FP64 && dtype != SWOF_FP32)) return SWOF_EINVAL;
+    return vinf_copy<true>(c, const_cast<void *>(v), dtype);
+}
+
+int swof_get_infiltrated_device(swof_ctx *c, void *v, int dtype)
+{
+    if (!c || !v || (dtype != SWOF_FP64 && dtype != SWOF_FP32)) return SWOF_EINVAL;
+    return vinf_copy<false>(c, v, dtype);
 }
 
 int swof_batch_stats(const float *states, int B, int C, int H, int W, int outmask, double dx, double dy,
@@ -226,11 +280,15 @@ int swof_surrogate_rollout(swof_unet *u, float *states, int B, double *t, const 
     int *acc_d = m.get<int>(B);
     float *rain_d = m.get<float>(B);
     if (!pred || !stats || !acc_d || !rain_d) return SWOF_ENOMEM;
-    std::vector<double> sh((size_t)10 * B), hv(HW);
-    std::vector<float> hf(HW), rain_next(B);
+    std::vector<double> sh((size_t)10 * B);
+    std::vector<float> rain_next(B);
     std::vector<int> acc(B);
+    std::vector<swof_ctx *> used;
     const double A = o->dx * o->dy, area = A * (double)HW;
     int status = SWOF_OK;
+    Events evs;
+    if (cudaEventCreateWithFlags(&evs.main, cudaEventDisableTiming) != cudaSuccess) return SWOF_ECUDA;
+    cudaEvent_t ev = evs.main;
     for (int k = 0; k < o->calls && status == SWOF_OK; ++k) {
         int st = swof_batch_stats(states, B, C, H, W, o->outflow_mask, o->dx, o->dy, stats, s);
         for (int b0 = 0; b0 < B && !st; b0 += maxB) {
@@ -269,7 +327,10 @@ int swof_surrogate_rollout(swof_unet *u, float *states, int B, double *t, const 
             return SWOF_ECUDA;
         k_commit<<<grid_for((long long)B * HW), 256, 0, s>>>(states, C, pred, Co, HW, B, acc_d, rain_d,
                                                               o->rain_channel, (float)o->h_dry);
-        if (cudaStreamSynchronize(s) != cudaSuccess) return SWOF_ECUDA;
+        if (cudaEventRecord(ev, s) != cudaSuccess) return SWOF_ECUDA;
+        // failing members: the plain solver on each fallback context's own
+        // stream (after the commit), the rollout stream waiting for all
+        used.clear();
         for (int b = 0; b < B; ++b) {
             if (!acc[b]) {
                 const int fi = fallback && fallback_of ? fallback_of[b] : -1;
@@ -278,13 +339,26 @@ int swof_surrogate_rollout(swof_unet *u, float *states, int B, double *t, const 
                     status = SWOF_ESTATE;   // no solver to fall back on: this member stops here
                     continue;
                 }
-                if ((st = fallback_member(fc, states + (size_t)b * C * HW, C, HW, Co, t[b], o->fallback_steps, hv,
-                                          hf)))
+                if (cudaStreamWaitEvent(fc->stream, ev, 0) != cudaSuccess) return SWOF_ECUDA;
+                if ((st = enqueue_fallback(fc, states + (size_t)b * C * HW, C, HW, Co, t[b], o->fallback_steps)))
                     return st;
+                used.push_back(fc);
             }
             t[b] += o->span;
         }
+        for (swof_ctx *fc : used) {
+            cudaEvent_t e = evs.of(fc);
+            if (!e || cudaEventRecord(e, fc->stream) != cudaSuccess || cudaStreamWaitEvent(s, e, 0) != cudaSuccess)
+                return SWOF_ECUDA;
+        }
     }
+    // latched errors of the fallback solvers used (synchronises them)
+    for (auto &p : evs.ctx) {
+        swof_step_info info;
+        int st = swof_step(p.first, 0, &info);
+        if (st) return st;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SWOF_ECUDA;
     return status;
 }
 

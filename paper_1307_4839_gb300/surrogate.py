@@ -190,10 +190,13 @@ def coarse_solver(traj: Trajectory, steps: int, precision=FP32, stream=None) -> 
 
 class Rollout:
     """Members (trajectory, start snapshot) of a Dataset rolled forward by
-    the network with the checked fallback; states [B][IN_CH][Hc][Wc]."""
+    the network with the checked fallback; states [B][IN_CH][Hc][Wc].
+    Each trajectory gets a pool of up to `pool` coarse solvers (own CUDA
+    streams, CUDA graphs) that its failing members share round-robin, so
+    fallbacks of different members run concurrently."""
 
     def __init__(self, ds: Dataset, net: UNet, members, fallback_steps: int | None = None,
-                 fallback_precision=FP32, tol: float = 1e-3):
+                 fallback_precision=FP32, tol: float = 1e-3, pool: int = 8):
         import torch
         self.ds, self.net, self.tol = ds, net, tol
         self.members = [(int(a), int(b)) for a, b in members]
@@ -203,9 +206,18 @@ class Rollout:
         self.states = ds.flat.index_select(0, idx).contiguous()
         self.t = np.array([ds.trajs[a].times[b] for a, b in self.members], dtype=np.float64)
         self.rain = np.array([ds.trajs[a].rain for a, _ in self.members], dtype=np.float64)
-        used = sorted({a for a, _ in self.members})
-        self.fallback = [coarse_solver(ds.trajs[a], self.fallback_steps, fallback_precision) for a in used]
-        self.fallback_of = np.array([used.index(a) for a, _ in self.members], dtype=np.int32)
+        self.fallback, self.fallback_of = [], np.zeros(len(self.members), dtype=np.int32)
+        first, size, count = {}, {}, {}
+        for b, (a, _) in enumerate(self.members):
+            if a not in first:
+                size[a] = min(pool, sum(1 for x, _ in self.members if x == a))
+                first[a], count[a] = len(self.fallback), 0
+                for _ in range(size[a]):
+                    s = coarse_solver(ds.trajs[a], self.fallback_steps, fallback_precision)
+                    s.use_graph(True)
+                    self.fallback.append(s)
+            self.fallback_of[b] = first[a] + count[a] % size[a]
+            count[a] += 1
         self.calls = 0
 
     def run(self, calls: int, inject=None, stream=None):
@@ -250,12 +262,14 @@ def coarse_baseline(ds: Dataset, members, calls: int, steps: int | None = None, 
             cache[a] = coarse_solver(tr, n, precision)
         s = cache[a]
         x = ds.data[a, b, :OUT_CH].clone()
+        torch.cuda.synchronize()
         s.set_state_device(x[0], x[1], x[2])
-        s.set_infiltrated(x[3].double().cpu().numpy())
+        s.set_infiltrated_device(x[3])
         s.set_time(tr.times[b])
         s.step(calls * n)
         s.get_state_device(x[0], x[1], x[2])
-        x[3] = torch.from_numpy(s.infiltrated()).float().to("cuda")
+        s.get_infiltrated_device(x[3])
+        s.step(0)                 # synchronises the solver's stream
         out.append(x)
     for s in cache.values():
         s.close()
