@@ -63,6 +63,7 @@ def parse():
                     help="precision of the headline measurement (fp64: no variants)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tile", type=int, default=-1, help="fixed tile shape (skips the autotuner)")
+    ap.add_argument("--tile2", type=int, default=-1, help="fixed stage-2 tile shape (with --tile)")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-wet", action="store_true")
     ap.add_argument("--ens-members", type=int, default=256)
@@ -91,12 +92,14 @@ def bf16_peak() -> float:
         return 1900.0
 
 
-def recorded_traffic(kernel: str, precision: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
-    src = os.path.join(ROOT, "paper_1307_4839_gb300", "csrc", "swof_kernels.cuh")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    f = os.path.join(ROOT, "profiles", f"{kernel}_{precision}_valley4096.txt")
+def recorded_traffic(kernel: str, precision: str, tile):
+    """DRAM bytes per launch from the committed ncu summary of this kernel,
+    if it was taken on the current kernel source and tile shape (else
+    None)."""
+    csrc = os.path.join(ROOT, "paper_1307_4839_gb300", "csrc")
+    src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("swof_kernels.cuh", "swof_sweep.cuh"))
+    sha = hashlib.sha256(src).hexdigest()[:16]
+    f = os.path.join(ROOT, "profiles", f"k_sweep_{kernel}_{precision}_valley4096.txt")
     if not os.path.exists(f):
         return None
     vals = {}
@@ -105,6 +108,8 @@ def recorded_traffic(kernel: str, precision: str):
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
     if vals.get("kernel_source_sha256_16") != sha:
+        return None
+    if tile is not None and f", {tile[0]}, {tile[1]}>" not in vals.get("kernel", ""):
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
@@ -248,7 +253,7 @@ def run_reference(args, ws, rank):
 
 
 def measure(sw, torch, w, precision: str, steps: int, warmup: int, ws: int, clocks: Clocks | None,
-            autotune: bool = True, tile: int = -1):
+            autotune: bool = True, tile: int = -1, tile2: int = -1):
     prec = sw.FP32 if precision == "fp32" else sw.FP64
     # a dedicated (non-null) stream: the kernels and the timing events share it
     stream = torch.cuda.Stream()
@@ -257,9 +262,10 @@ def measure(sw, torch, w, precision: str, steps: int, warmup: int, ws: int, cloc
     s.step(warmup)
     if tile >= 0 or not autotune:
         shape = max(tile, 0)
-        s.set_tile_shape(shape)
-        tune = {"shape": [shape, shape], "stage1": list(sw.tile_shapes()[shape]),
-                "stage2": list(sw.tile_shapes()[shape])}
+        shape2 = tile2 if tile2 >= 0 else shape
+        s.set_tile_shape(shape, shape2)
+        tune = {"shape": [shape, shape2], "stage1": list(sw.tile_shapes()[shape]),
+                "stage2": list(sw.tile_shapes()[shape2])}
     else:
         tune = s.autotune(reps=3, cache=os.path.join(ROOT, "paper_1307_4839_gb300", "_build", "autotune.json"))
     torch.cuda.synchronize()
@@ -486,7 +492,7 @@ def main():
     clocks = Clocks(local)
     P = args.precision
     ms, t, clk, diag, solver = measure(sw, torch, w, P, args.steps, args.warmup, ws, clocks,
-                                       not args.no_autotune, args.tile)
+                                       not args.no_autotune, args.tile, args.tile2)
     ms_max = max_over_ranks(ms, ws)
     ms_step = ms_max / args.steps
     value = ws * cells / (ms_step * 1e-3) * 1e-9
@@ -499,7 +505,7 @@ def main():
     roofline = {"bound": "hbm", "kernel": f"k_sweep<{tname},{dom[-1]}>" if dom != "lambda" else f"k_lambda<{tname}>",
                 "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "peak_kind": f"{peak_kind} copy bandwidth (burst)",
-                "traffic": recorded_traffic(dom, P),
+                "traffic": recorded_traffic(dom, P, diag["tile"].get(dom)) if dom != "lambda" else None,
                 "algorithmic_bytes_per_cell": BYTES[P][dom],
                 "kernel_ms": {kk: round(v, 5) for kk, v in avg.items()},
                 "step_frac_of_hbm": STEP_BYTES[P] * cells / (ms_step * 1e-3) * 1e-9 / hbm}
