@@ -37,6 +37,27 @@ __device__ __forceinline__ Cell<T> make_cell(T h, T qx, T qy, T zy, T hdry)
     return c;
 }
 
+// CTA-wide barrier / AND-vote; a one-warp CTA needs only the warp's own
+// (memory-ordering) synchronisation.
+template <int NTX>
+__device__ __forceinline__ void cta_sync()
+{
+    if constexpr (NTX == 32)
+        __syncwarp();
+    else
+        __syncthreads();
+}
+template <int NTX>
+__device__ __forceinline__ int cta_and(int p)
+{
+    if constexpr (NTX == 32) {
+        __syncwarp();
+        return __all_sync(0xffffffffu, p);
+    } else {
+        return __syncthreads_and(p);
+    }
+}
+
 template <typename T, int NTX>
 struct SweepSmem {
     using K = decltype(speed_key(T(0)));
@@ -147,7 +168,10 @@ __device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, 
         if (r >= j0 && r < j0 + H && r < P.ny) {     // uniform over the CTA
             s_st[t] = {rc.h, rc.u, rc.v, rc.rh};
             s_zx[t] = zx;
-            __syncthreads();
+            // A row with h = 0 in every column of the CTA has zero x fluxes
+            // and a zero Fc (h_- + h_+ = 0): its x differences are +0, the
+            // value a1..a3 already hold, so the CTA skips the x part.
+            if (!cta_and<NTX>(rc.h == T(0))) {
             Rec<T> q{};
             const bool rec = t >= 1 && t <= NTX - 2;
             if (rec) {
@@ -160,7 +184,7 @@ __device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, 
                                  L.y, rc.u, R.y, L.z, rc.v, R.z, rc.rh, C.hdry);
                 s_m[t] = {q.hm, q.zm, q.unm, q.utm};
             }
-            __syncthreads();
+            cta_sync<NTX>();
             V4<T> fe{};
             if (t >= 1 && t <= NTX - 3) {
                 V4<T> R = s_m[t + 1];
@@ -168,7 +192,7 @@ __device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, 
                              fe.x, fe.y, fe.z, fe.w);
                 s_f[t] = fe;
             }
-            __syncthreads();
+            cta_sync<NTX>();
             if (out_col) {
                 if (STAGE == 2 && P.check_cfl)
                     k2x = kmax(k2x, speed_key(mx(ab(q.unm) + sq(C.g * q.hm), ab(q.unp) + sq(C.g * q.hp))));
@@ -179,6 +203,7 @@ __device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, 
                 a3 = fe.w - fw.w;
                 if (gi == 0 && P.bc[0] == SWOF_BC_OUTFLOW) outacc -= fw.x * (T)P.dy;
                 if (gi == P.nx - 1 && P.bc[1] == SWOF_BC_OUTFLOW) outacc += fe.x * (T)P.dy;
+            }
             }
         }
 
@@ -264,8 +289,8 @@ __device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, 
             if (STAGE == 2 && P.fuse_lambda && k >= 4) {       // uniform over the CTA
                 V4<T> *buf = S.nw[k & 1];
                 buf[t] = {fh, fu, fv, frh};
-                __syncthreads();
-                if (out_col && ro < P.ny) {
+                // all three rows of U^{n+1} dry across the CTA: every speed is 0
+                if (!cta_and<NTX>(fh == T(0) && y1h == T(0) && y2h == T(0)) && out_col && ro < P.ny) {
                     if (xlam) {
                         V4<T> L = buf[t - 1], R = buf[t + 1];
                         lx = kmax(lx, speed_key(cell_speed(L.x, fh, R.x, L.y, fu, R.y, frh, C.hdry, C.g)));
