@@ -226,19 +226,38 @@ inline int grid_for(long long n) { long long g = (n + 255) / 256; return (int)(g
 template <int NT>
 int conv_launch(const ConvArgs &A, cudaStream_t s)
 {
-    size_t smem = sizeof(ConvSmem) + 1024;
-    if (cudaFuncSetAttribute(k_conv<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return SWOF_ECUDA;
+    size_t smem = ConvCfg<NT>::SMEM;
+    static int per_sm = 0;         // resident CTAs per SM (persistent grid)
+    if (!per_sm) {
+        if (cudaFuncSetAttribute(k_conv<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return SWOF_ECUDA;
+        int n = 0, dev = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_conv<NT>, ConvCfg<NT>::THREADS, smem) != cudaSuccess ||
+            n < 1)
+            n = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        per_sm = n * (sms > 0 ? sms : 152);
+    }
     long long M = (long long)A.B * A.H * A.W;
-    dim3 grid((unsigned)((M + 127) / 128), (unsigned)(A.ntot / NT));
-    k_conv<NT><<<grid, 128, smem, s>>>(A);
+    long long tiles = (M + 127) / 128;
+    long long gy = A.ntot / NT;
+    long long gx = (4LL * per_sm + gy - 1) / gy;
+    if (gx > tiles) gx = tiles;
+    if (gx < 1) gx = 1;
+    dim3 grid((unsigned)gx, (unsigned)gy);
+    k_conv<NT><<<grid, ConvCfg<NT>::THREADS, smem, s>>>(A);
     return cudaGetLastError() == cudaSuccess ? SWOF_OK : SWOF_ECUDA;
 }
 
-int conv(const ConvArgs &A, cudaStream_t s)
+int conv(ConvArgs A, cudaStream_t s)
 {
     int nt = A.ntot >= 256 ? 256 : A.ntot;
     if (A.ntot % nt) return SWOF_EINVAL;
+    if (A.cin < 8 || (A.cin & (A.cin - 1)) || (long long)A.B * A.H * A.W >= (1LL << 31) / 4)
+        return SWOF_EINVAL;
+    A.cin_shift = 0;
+    while ((1 << A.cin_shift) < A.cin) ++A.cin_shift;
     switch (nt) {
     case 16: return conv_launch<16>(A, s);
     case 32: return conv_launch<32>(A, s);
@@ -445,6 +464,7 @@ int fwd_layer(swof_unet *u, int l, int B, int h, int w, Act in, Act out, bf16 *p
     A.cy = outf ? outf_c : out.c;
     A.yc0 = outf ? 0 : out.c0;
     A.act = L.act;
+    A.pre_round = 1;
     A.store = L.kind == K_CONVT ? swof::SCATTER_UP2 : swof::STORE_NHWC;
     A.cout_up = L.cout;
     A.err = u->err;
@@ -517,9 +537,12 @@ int bwd_layer(swof_unet *u, int l, int B, int ih, int iw, Act in, const float *d
     return swof::conv(A, s);
 }
 
-int forward(swof_unet *u, int B, cudaStream_t s)
+// keep_pre = false (inference): the pre-activations are not stored (the
+// activations still use their bf16-rounded values, as in training).
+int forward(swof_unet *u, int B, cudaStream_t s, bool keep_pre = true)
 {
     int st = SWOF_OK;
+    auto pre = [&](bf16 *p) { return keep_pre ? p : nullptr; };
     const int C = u->C;
     Act in{u->x0, 16, 0};
     for (int l = 0; l < 4 && !st; ++l) {
@@ -530,10 +553,11 @@ int forward(swof_unet *u, int B, cudaStream_t s)
             swof::k_pool_fwd<<<swof::grid_for(n), 256, 0, s>>>(u->cat[l - 1], 2 * cp, 0, B, hp, wp, cp, u->pool[l]);
             in = Act{u->pool[l], cp, 0};
         }
-        st = fwd_layer(u, 2 * l, B, h, w, in, Act{u->ea[l], c, 0}, u->ea_pre[l], nullptr, 0, s);
+        st = fwd_layer(u, 2 * l, B, h, w, in, Act{u->ea[l], c, 0}, pre(u->ea_pre[l]), nullptr, 0, s);
         Act o = l < 3 ? Act{u->cat[l], 2 * c, 0} : Act{u->bott, c, 0};
-        if (!st) st = fwd_layer(u, 2 * l + 1, B, h, w, Act{u->ea[l], c, 0}, o, l < 3 ? u->eb_pre[l] : u->bott_pre,
-                                nullptr, 0, s);
+        if (!st)
+            st = fwd_layer(u, 2 * l + 1, B, h, w, Act{u->ea[l], c, 0}, o, pre(l < 3 ? u->eb_pre[l] : u->bott_pre),
+                           nullptr, 0, s);
     }
     Act below{u->bott, C << 3, 0};
     for (int l = 2; l >= 0 && !st; --l) {
@@ -541,10 +565,10 @@ int forward(swof_unet *u, int B, cudaStream_t s)
         int base = 8 + 3 * (2 - l);
         // transposed conv from the level below (its grid) into the second half of cat[l]
         st = fwd_layer(u, base, B, h / 2, w / 2, below, Act{u->cat[l], 2 * c, c}, nullptr, nullptr, 0, s);
-        if (!st) st = fwd_layer(u, base + 1, B, h, w, Act{u->cat[l], 2 * c, 0}, Act{u->da[l], c, 0}, u->da_pre[l],
-                                nullptr, 0, s);
-        if (!st) st = fwd_layer(u, base + 2, B, h, w, Act{u->da[l], c, 0}, Act{u->db[l], c, 0}, u->db_pre[l],
-                                nullptr, 0, s);
+        if (!st) st = fwd_layer(u, base + 1, B, h, w, Act{u->cat[l], 2 * c, 0}, Act{u->da[l], c, 0},
+                                pre(u->da_pre[l]), nullptr, 0, s);
+        if (!st) st = fwd_layer(u, base + 2, B, h, w, Act{u->da[l], c, 0}, Act{u->db[l], c, 0},
+                                pre(u->db_pre[l]), nullptr, 0, s);
         below = Act{u->db[l], c, 0};
     }
     if (!st) st = fwd_layer(u, 17, B, u->H, u->W, below, Act{nullptr, 16, 0}, nullptr, u->out, 16, s);
@@ -914,7 +938,7 @@ int swof_surrogate_predict(swof_unet *u, const float *in, int B, float *out, voi
     cudaStream_t s = S(stream);
     long long P = (long long)B * u->H * u->W;
     swof::k_pack_input<<<swof::grid_for(P * 16), 256, 0, s>>>(in, u->in_ch, B, u->H, u->W, u->norm, u->norm + 16, u->x0);
-    int st = forward(u, B, s);
+    int st = forward(u, B, s, false);
     if (st) return st;
     swof::k_residual<<<swof::grid_for((long long)B * u->out_ch * u->H * u->W), 256, 0, s>>>(
         in, u->in_ch, u->out, u->out_ch, B, u->H, u->W, u->norm + 32, out);
