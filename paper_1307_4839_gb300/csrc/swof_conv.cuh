@@ -17,6 +17,7 @@
 // The forward K loop is a multi-stage cp.async pipeline (the weight-gradient
 // kernel double-buffers); every wait is bounded.
 #pragma once
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -52,7 +53,29 @@ struct ConvArgs {
 
 constexpr long long CONV_WAIT_LIMIT = 1LL << 22;
 
-__device__ __forceinline__ float gelu_f(float v) { return 0.5f * v * (1.0f + erff(v * 0.70710678118654752f)); }
+// erf(x) by Abramowitz & Stegun, Handbook of Mathematical Functions, formula
+// 7.1.28: 1 - (1 + a1 x + ... + a6 x^6)^-16 for x >= 0 (|error| <= 3e-7),
+// odd extension; one reciprocal, no exponential.  The surrogate rounds its
+// activations to bf16 (relative 4e-3), far above this error.
+__device__ __forceinline__ float erf_as(float x)
+{
+    const float a = fabsf(x);
+    float p = 0.0000430638f;
+    p = fmaf(p, a, 0.0002765672f);
+    p = fmaf(p, a, 0.0001520143f);
+    p = fmaf(p, a, 0.0092705272f);
+    p = fmaf(p, a, 0.0422820123f);
+    p = fmaf(p, a, 0.0705230784f);
+    p = fmaf(p, a, 1.0f);
+    p = p * p;
+    p = p * p;
+    p = p * p;
+    p = p * p;                         // (...)^16; +inf for large x -> erf = 1
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(p));
+    return copysignf(1.0f - r, x);
+}
+__device__ __forceinline__ float gelu_f(float v) { return 0.5f * v * (1.0f + erf_as(v * 0.70710678118654752f)); }
 
 struct __align__(1024) ConvSmem {
     uint8_t a[2][128 * 64 * 2];
@@ -61,110 +84,139 @@ struct __align__(1024) ConvSmem {
     uint32_t tmem;
 };
 
-// ---- cp.async (16-byte copies global -> shared, zero-filled when the
+// ---- cp.async (16-byte copies global -> shared through L1, which keeps
+// the 3x3 taps' re-reads of a pixel on chip; zero-filled when the
 // source size is 0) ----
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes)
 {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 // Pipeline depth and shared-memory footprint of k_conv<NT>.
 template <int NT>
 struct ConvCfg {
-    static constexpr int STAGES = NT >= 256 ? 3 : 4;
+    static constexpr int STAGES = NT >= 256 ? 3 : (NT >= 128 ? 4 : 6);
     static constexpr int A_BYTES = 128 * 64 * 2;
     static constexpr int B_BYTES = NT * 64 * 2;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-    static constexpr int TMEM_COLS = NT < 32 ? 32 : NT;
-    static constexpr int THREADS = 256;
-    static constexpr int ROWS_PER_THREAD = 128 * 8 / THREADS;
-    static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 64 + 1024;
+    static constexpr int TC = NT < 32 ? 32 : NT;           // columns of one accumulator
+    static constexpr int TMEM_COLS = 2 * TC;               // two accumulators
+    static constexpr int THREADS = 288;                    // 4 producer, 1 MMA, 4 epilogue warps
+    static constexpr int BIAS_BYTES = 256 * 4;
+    static constexpr int BAR_BYTES = (2 * STAGES + 4) * 8 + 16;
+    static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + BIAS_BYTES + BAR_BYTES + 1024;
 };
 
-// Epilogue of one 128-pixel tile: TMEM -> + bias -> (pre-activation,
-// activation) -> stores.  Each thread owns one pixel row.
-template <int NT>
-__device__ __forceinline__ void conv_epilogue(const ConvArgs &A, uint32_t tmem, long long m0, int n0, long long M)
+// Bounded mbarrier wait that also gives up when another role has aborted;
+// a wait that runs out raises the abort flag.
+__device__ __forceinline__ bool conv_wait(uint32_t bar, uint32_t parity, volatile int *abort)
 {
-    // warp w reads TMEM lanes 32 (w % 4) ..; the warps w / 4 = 0, 1 take
-    // alternate 16-column groups
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int lw = warp & 3, half = warp >> 2;
-    const long long p = m0 + lw * 32 + lane;
+    for (long long i = 0; i < CONV_WAIT_LIMIT; ++i) {
+        if (tc05::mbar_try_wait(bar, parity)) return true;
+        if ((i & 63) == 63 && *abort) return false;
+    }
+    *abort = 1;
+    return false;
+}
+
+// Epilogue of one 128-pixel tile for the 32 pixel rows of TMEM lane quarter
+// `quarter` (this warp): accumulator columns at TMEM address tb + c, bias
+// from shared memory, optional pre-activation, activation, stores.
+template <int NT>
+__device__ __forceinline__ void conv_tile_epilogue(const ConvArgs &A, uint32_t tmem, int acc_col, int quarter,
+                                                   long long m0, int n0, long long M, const float *sbias)
+{
+    const int lane = threadIdx.x & 31;
     const int hw = A.H * A.W;
+    const long long p = m0 + quarter * 32 + lane;
+    const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)acc_col;
 #pragma unroll 1
-    for (int c0 = 16 * half; c0 < NT; c0 += 32) {
+    for (int c0 = 0; c0 < NT; c0 += 16) {
         float v[16];
-        tc05::tmem_ld16(tmem + ((uint32_t)(lw * 32) << 16) + (uint32_t)c0, v);
+        tc05::tmem_ld16(tb + (uint32_t)c0, v);
         if (p >= M) continue;
         const int col0 = n0 + c0;
-        if (A.bias) {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] += A.bias[col0 + i];
-        }
+        for (int i = 0; i < 16; ++i) v[i] += sbias[c0 + i];
         long long dst;           // pixel index in the output tensor
         int ch;                  // first channel written
         if (A.store == STORE_NHWC) {
             dst = p;
             ch = A.yc0 + col0;
         } else {                 // 16 columns share one sub-position (cout_up multiple of 16)
-            int sub = col0 / A.cout_up, o = col0 - sub * A.cout_up;
-            int b = (int)(p / hw), rem = (int)(p - (long long)b * hw);
-            int yy = rem / A.W, xx = rem - yy * A.W;
+            const int sub = col0 / A.cout_up, o = col0 - sub * A.cout_up;
+            const int b = (int)(p / hw), rem = (int)(p - (long long)b * hw);
+            const int yy = rem / A.W, xx = rem - yy * A.W;
             dst = ((long long)b * 2 * A.H + 2 * yy + (sub >> 1)) * (2 * A.W) + 2 * xx + (sub & 1);
             ch = A.yc0 + o;
         }
         if (A.yf) {
-            float4 *d = reinterpret_cast<float4 *>(A.yf + dst * A.cy + ch);
+            float4 *dp = reinterpret_cast<float4 *>(A.yf + dst * A.cy + ch);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) d[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            for (int i = 0; i < 4; ++i) dp[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
         }
         if (A.ypre) {   // compact, indexed by the GEMM row and column
             __align__(16) __nv_bfloat16 t[16];
 #pragma unroll
             for (int i = 0; i < 16; ++i) t[i] = __float2bfloat16_rn(v[i]);
-            uint4 *d = reinterpret_cast<uint4 *>(A.ypre + p * A.ntot + col0);
-            d[0] = reinterpret_cast<uint4 *>(t)[0];
-            d[1] = reinterpret_cast<uint4 *>(t)[1];
+            uint4 *dp = reinterpret_cast<uint4 *>(A.ypre + p * A.ntot + col0);
+            dp[0] = reinterpret_cast<uint4 *>(t)[0];
+            dp[1] = reinterpret_cast<uint4 *>(t)[1];
         }
         if (A.y) {
             __align__(16) __nv_bfloat16 t[16];
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
                 // the activation acts on the bf16-rounded pre-activation
-                float z = A.pre_round ? __bfloat162float(__float2bfloat16_rn(v[i])) : v[i];
+                const float z = A.pre_round ? __bfloat162float(__float2bfloat16_rn(v[i])) : v[i];
                 t[i] = __float2bfloat16_rn(A.act == ACT_GELU ? gelu_f(z) : z);
             }
-            uint4 *d = reinterpret_cast<uint4 *>(A.y + dst * A.cy + ch);
-            d[0] = reinterpret_cast<uint4 *>(t)[0];
-            d[1] = reinterpret_cast<uint4 *>(t)[1];
+            uint4 *dp = reinterpret_cast<uint4 *>(A.y + dst * A.cy + ch);
+            dp[0] = reinterpret_cast<uint4 *>(t)[0];
+            dp[1] = reinterpret_cast<uint4 *>(t)[1];
         }
     }
 }
 
-// A persistent CTA: 128-pixel tiles m = blockIdx.x, blockIdx.x + gridDim.x,
-// ... of column tile blockIdx.y (NT columns).  The K chunks of all its
-// tiles form one stream fed by a STAGES-deep cp.async pipeline: while the
-// tensor core works on chunk g, the copies of chunks g+1 .. g+STAGES-1 are
-// in flight -- across tile boundaries, so the next tile's operands load
-// during a tile's epilogue.  Each thread gathers the same 8 A rows (pixels)
-// and 16-byte column j of every chunk; their coordinates are decoded once
-// per tile.
+// One persistent CTA handles the 128-pixel tiles m = blockIdx.x,
+// blockIdx.x + gridDim.x, ... of column tile blockIdx.y (NT columns), with
+// warp roles:
+//   warps 0-3  producers: gather the implicit A rows (8 pixel rows and one
+//              16-byte column per thread, coordinates decoded once per tile)
+//              and the weight rows with cp.async into a STAGES-deep ring;
+//              after a chunk's copies land, fence them to the async proxy
+//              and arrive on its `full` barrier;
+//   warp 4     one thread issues the tcgen05 MMAs of each chunk into one of
+//              two TMEM accumulators and commits to the chunk's `empty`
+//              barrier (slot reusable) and, per tile, to `acc_full`;
+//   warps 5-8  epilogue: drain the finished accumulator (each warp its
+//              32 TMEM lanes), bias, activation, stores; arrive on
+//              `acc_empty`, so the next-but-one tile may reuse it.
+// Loads, MMAs and epilogues of different chunks and tiles overlap; no
+// CTA-wide barrier inside the loop.  Every wait is bounded.
 template <int NT>
 __global__ void __launch_bounds__(ConvCfg<NT>::THREADS) k_conv(ConvArgs A)
 {
     using Cfg = ConvCfg<NT>;
-    constexpr int RPT = Cfg::ROWS_PER_THREAD;
-    constexpr int RSTEP = 128 / RPT;       // row step between a thread's rows
     constexpr int S = Cfg::STAGES;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *base = smem_raw + ((1024 - (reinterpret_cast<uintptr_t>(smem_raw) & 1023)) & 1023);
-    unsigned long long *bar = reinterpret_cast<unsigned long long *>(base + S * Cfg::STAGE_BYTES);
-    uint32_t *tmem_word = reinterpret_cast<uint32_t *>(bar + S);
-    const int tid = threadIdx.x, warp = tid >> 5;
+    float *sbias = reinterpret_cast<float *>(base + S * Cfg::STAGE_BYTES);
+    unsigned long long *full = reinterpret_cast<unsigned long long *>(base + S * Cfg::STAGE_BYTES + Cfg::BIAS_BYTES);
+    unsigned long long *empty = full + S;
+    unsigned long long *accf = empty + S;
+    unsigned long long *acce = accf + 2;
+    uint32_t *tmem_word = reinterpret_cast<uint32_t *>(acce + 2);
+    volatile int *abort = reinterpret_cast<volatile int *>(tmem_word + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long M = (long long)A.B * A.H * A.W;
     const int tiles = (int)((M + 127) / 128);
     const int n0 = blockIdx.y * NT;
@@ -172,142 +224,320 @@ __global__ void __launch_bounds__(ConvCfg<NT>::THREADS) k_conv(ConvArgs A)
     const int my_tiles = (int)blockIdx.x < tiles ? (tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const int G = my_tiles * nk;
     if (G == 0) return;             // uniform: nothing allocated yet
-    if (warp == 0) {
+    if (warp == 4) {
         tc05::tmem_alloc(tc05::smem_u32(tmem_word), Cfg::TMEM_COLS);
         tc05::tmem_relinquish();
     }
-    if (tid == 0)
-        for (int q = 0; q < S; ++q) tc05::mbar_init(tc05::smem_u32(&bar[q]), 1);
+    if (tid == 0) {
+        for (int q = 0; q < S; ++q) {
+            tc05::mbar_init(tc05::smem_u32(&full[q]), 128);
+            tc05::mbar_init(tc05::smem_u32(&empty[q]), 1);
+        }
+        for (int q = 0; q < 2; ++q) {
+            tc05::mbar_init(tc05::smem_u32(&accf[q]), 1);
+            tc05::mbar_init(tc05::smem_u32(&acce[q]), 128);
+        }
+        *abort = 0;
+    }
+    for (int i = tid; i < NT; i += Cfg::THREADS) sbias[i] = A.bias ? A.bias[n0 + i] : 0.0f;
     tc05::fence_before();
     __syncthreads();
     tc05::fence_after();
     const uint32_t tmem = *tmem_word;
-    const uint32_t idesc = tc05::idesc_bf16(128, NT);
     const uint32_t sbase = tc05::smem_u32(base);
-
-    const int j = tid & 7;
-    const int taps = (A.gather == GATHER_SAME) ? A.ks * A.ks : 4;
-    const int half = A.ks >> 1;
     const int hw = A.H * A.W;
-    int ry[RPT], rx[RPT];
-    int rbase[RPT];                  // pixel index of the tap origin (-1: row beyond M)
-    int dec_tile = -1;
-    // rows r_i = r0 + RSTEP i of a tile are RSTEP pixels apart: decode r0 once,
-    // then step
-    auto decode = [&](int ti) {
-        const int m0 = ((int)blockIdx.x + ti * (int)gridDim.x) * 128;
-        int p = m0 + (tid >> 3);
-        int b = p / hw, rem = p - b * hw;
-        int y = rem / A.W, x = rem - y * A.W;
+
+    if (warp < 4) {
+        // ---------------- producers ----------------
+        const int j = tid & 7;
+        const int taps = (A.gather == GATHER_SAME) ? A.ks * A.ks : 4;
+        const int half = A.ks >> 1;
+        int ry[8], rx[8], rbase[8];
+        int dec_tile = -1;
+        auto decode = [&](int ti) {           // rows r_i = r0 + 16 i, 16 pixels apart
+            const int m0 = ((int)blockIdx.x + ti * (int)gridDim.x) * 128;
+            int p = m0 + (tid >> 3);
+            int b = p / hw, rem = p - b * hw;
+            int y = rem / A.W, x = rem - y * A.W;
 #pragma unroll
-        for (int i = 0; i < RPT; ++i) {
-            if (p < (int)M) {
-                ry[i] = y;
-                rx[i] = x;
-                rbase[i] = (A.gather == GATHER_SAME) ? p : (b * 2 * A.H + 2 * y) * (2 * A.W) + 2 * x;
-            } else {
-                ry[i] = rx[i] = 0;
-                rbase[i] = -1;
-            }
-            p += RSTEP;
-            x += RSTEP;
-            while (x >= A.W) {
-                x -= A.W;
-                if (++y == A.H) {
-                    y = 0;
-                    ++b;
+            for (int i = 0; i < 8; ++i) {
+                if (p < (int)M) {
+                    ry[i] = y;
+                    rx[i] = x;
+                    rbase[i] = (A.gather == GATHER_SAME) ? p : (b * 2 * A.H + 2 * y) * (2 * A.W) + 2 * x;
+                } else {
+                    ry[i] = rx[i] = 0;
+                    rbase[i] = -1;
+                }
+                p += 16;
+                x += 16;
+                while (x >= A.W) {
+                    x -= A.W;
+                    if (++y == A.H) {
+                        y = 0;
+                        ++b;
+                    }
                 }
             }
-        }
-        dec_tile = ti;
-    };
-    auto issue = [&](int g) {
-        const int ti = g / nk, kc = g - ti * nk;
-        if (ti != dec_tile) decode(ti);
-        const uint32_t sa = sbase + (g % S) * Cfg::STAGE_BYTES, sb = sa + Cfg::A_BYTES;
-        const int k = kc * 64 + 8 * j;
-        const int tap = k >> A.cin_shift, c = k & (A.cin - 1);
-        int dy = 0, dx = 0, toff;
-        if (A.gather == GATHER_SAME) {
-            const int ty = A.ks == 3 ? (tap * 11) >> 5 : 0;      // tap / 3 for tap < 9
-            dy = ty - half;
-            dx = tap - ty * A.ks - half;
-            toff = dy * A.W + dx;
-        } else {
-            toff = (tap >> 1) * (2 * A.W) + (tap & 1);
-        }
-#pragma unroll
-        for (int i = 0; i < RPT; ++i) {
-            const int r = (tid >> 3) + RSTEP * i;
-            bool ok = rbase[i] >= 0 && tap < taps;
+            dec_tile = ti;
+        };
+        int g = 0;
+#pragma unroll 1
+        for (; g < G; ++g) {
+            const int slot = g % S;
+            if (!conv_wait(tc05::smem_u32(&empty[slot]), (uint32_t)(((g / S) & 1) ^ 1), abort)) break;
+            const int ti = g / nk, kc = g - ti * nk;
+            if (ti != dec_tile) decode(ti);
+            const uint32_t sa = sbase + slot * Cfg::STAGE_BYTES, sb = sa + Cfg::A_BYTES;
+            const int k = kc * 64 + 8 * j;
+            const int tap = k >> A.cin_shift, c = k & (A.cin - 1);
+            int dy = 0, dx = 0, toff;
             if (A.gather == GATHER_SAME) {
-                const int sy = ry[i] + dy, sx = rx[i] + dx;
-                ok = ok && sy >= 0 && sy < A.H && sx >= 0 && sx < A.W;
+                const int ty = A.ks == 3 ? (tap * 11) >> 5 : 0;      // tap / 3 for tap < 9
+                dy = ty - half;
+                dx = tap - ty * A.ks - half;
+                toff = dy * A.W + dx;
+            } else {
+                toff = (tap >> 1) * (2 * A.W) + (tap & 1);
             }
-            const __nv_bfloat16 *src = ok ? A.x + (long long)(rbase[i] + toff) * A.cx + A.xc0 + c : A.x;
-            cp_async16(sa + tc05::canon_off(r, 8 * j), src, ok ? 16u : 0u);
-        }
-        for (int v = tid; v < NT * 8; v += Cfg::THREADS) {
-            const int r = v >> 3, jj = v & 7;
-            cp_async16(sb + tc05::canon_off(r, 8 * jj), A.w + (long long)(n0 + r) * A.Kp + kc * 64 + 8 * jj, 16u);
-        }
-    };
-    // parity of the completion of chunk g on its slot's barrier (the
-    // (g / S)-th completion of slot g % S); every completion is consumed
-    // in order, at most once, before its slot is refilled
-    auto wait_mma = [&](int g) -> bool {
-        return tc05::mbar_wait(tc05::smem_u32(&bar[g % S]), (uint32_t)((g / S) & 1), CONV_WAIT_LIMIT);
-    };
-
-    int bad = 0;
-    int waited = -1;               // chunks whose MMA completion has been consumed: 0 .. waited
-#pragma unroll 1
-    for (int q = 0; q < S - 1; ++q) {
-        if (q < G) issue(q);
-        cp_async_commit();
-    }
-#pragma unroll 1
-    for (int g = 0; g < G; ++g) {
-        const int slot = g % S, ti = g / nk, kc = g - ti * nk;
-        cp_async_wait<S - 2>();          // this thread's copies of chunk g have landed
-        tc05::fence_async_smem();
-        if (__syncthreads_or(bad)) break;
-        if (tid == 0) {
-            tc05::fence_after();
-            const uint32_t a0 = sbase + slot * Cfg::STAGE_BYTES, b0 = a0 + Cfg::A_BYTES;
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                tc05::mma_bf16(tmem, tc05::sdesc(a0 + q * 256, tc05::CANON_LBO, tc05::CANON_SBO),
-                               tc05::sdesc(b0 + q * 256, tc05::CANON_LBO, tc05::CANON_SBO), idesc,
-                               (kc > 0 || q > 0) ? 1u : 0u);
-            tc05::mma_commit(tc05::smem_u32(&bar[slot]));
-        }
-        // refill the slot of chunk g-1 with chunk g+S-1 once its MMAs are done
-        const int nxt = g + S - 1;
-        if (nxt < G) {
-            if (g >= 1 && waited < g - 1) {
-                if (!wait_mma(g - 1)) bad = 1;
-                waited = g - 1;
+            for (int i = 0; i < 8; ++i) {
+                const int r = (tid >> 3) + 16 * i;
+                bool ok = rbase[i] >= 0 && tap < taps;
+                if (A.gather == GATHER_SAME) {
+                    const int sy = ry[i] + dy, sx = rx[i] + dx;
+                    ok = ok && sy >= 0 && sy < A.H && sx >= 0 && sx < A.W;
+                }
+                const __nv_bfloat16 *src = ok ? A.x + (long long)(rbase[i] + toff) * A.cx + A.xc0 + c : A.x;
+                cp_async16(sa + tc05::canon_off(r, 8 * j), src, ok ? 16u : 0u);
             }
-            if (!bad) issue(nxt);
-        }
-        cp_async_commit();
-        if (kc == nk - 1) {              // tile ti complete: its last commit covers all its MMAs
-            if (!bad && waited < g) {
-                if (!wait_mma(g)) bad = 1;
-                waited = g;
+            for (int v = tid; v < NT * 8; v += 128) {
+                const int r = v >> 3, jj = v & 7;
+                cp_async16(sb + tc05::canon_off(r, 8 * jj), A.w + (long long)(n0 + r) * A.Kp + kc * 64 + 8 * jj, 16u);
             }
+            cp_async_commit();
+            if (g >= S - 2) {                 // chunk g - (S - 2) has landed
+                cp_async_wait<S - 2>();
+                tc05::fence_async_smem();
+                mbar_arrive(tc05::smem_u32(&full[(g - (S - 2)) % S]));
+            }
+        }
+        cp_async_wait<0>();
+        tc05::fence_async_smem();
+        if (g == G)
+            for (int q = (G > S - 2 ? G - (S - 2) : 0); q < G; ++q) mbar_arrive(tc05::smem_u32(&full[q % S]));
+    } else if (warp == 4) {
+        // ---------------- MMA issue ----------------
+        if (lane == 0) {
+            const uint32_t idesc = tc05::idesc_bf16(128, NT);
+            bool ok = true;
+#pragma unroll 1
+            for (int lt = 0; lt < my_tiles && ok; ++lt) {
+                const int acc = lt & 1;
+                if (!conv_wait(tc05::smem_u32(&acce[acc]), (uint32_t)(((lt >> 1) & 1) ^ 1), abort)) break;
+                tc05::fence_after();
+                const uint32_t d = tmem + (uint32_t)(acc * Cfg::TC);
+#pragma unroll 1
+                for (int kc = 0; kc < nk; ++kc) {
+                    const int g = lt * nk + kc, slot = g % S;
+                    if (!conv_wait(tc05::smem_u32(&full[slot]), (uint32_t)((g / S) & 1), abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc05::fence_after();
+                    const uint32_t a0 = sbase + slot * Cfg::STAGE_BYTES, b0 = a0 + Cfg::A_BYTES;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        tc05::mma_bf16(d, tc05::sdesc(a0 + q * 256, tc05::CANON_LBO, tc05::CANON_SBO),
+                                       tc05::sdesc(b0 + q * 256, tc05::CANON_LBO, tc05::CANON_SBO), idesc,
+                                       (kc > 0 || q > 0) ? 1u : 0u);
+                    tc05::mma_commit(tc05::smem_u32(&empty[slot]));
+                }
+                if (ok) tc05::mma_commit(tc05::smem_u32(&accf[acc]));
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue ----------------
+        const int quarter = warp & 3;       // TMEM lanes 32 * quarter ..
+#pragma unroll 1
+        for (int lt = 0; lt < my_tiles; ++lt) {
+            const int acc = lt & 1;
+            if (!conv_wait(tc05::smem_u32(&accf[acc]), (uint32_t)((lt >> 1) & 1), abort)) break;
             tc05::fence_after();
-            if (__syncthreads_or(bad)) break;
-            conv_epilogue<NT>(A, tmem, ((long long)blockIdx.x + (long long)ti * gridDim.x) * 128, n0, M);
+            const long long m0 = ((long long)blockIdx.x + (long long)lt * gridDim.x) * 128;
+            conv_tile_epilogue<NT>(A, tmem, acc * Cfg::TC, quarter, m0, n0, M, sbias);
             tc05::fence_before();
+            mbar_arrive(tc05::smem_u32(&acce[acc]));
         }
     }
-    cp_async_wait<0>();
-    if (bad && tid == 0 && A.err) atomicExch(A.err, 1);
     tc05::fence_before();
     __syncthreads();
-    if (warp == 0) tc05::tmem_dealloc(tmem, Cfg::TMEM_COLS);
+    if (*abort && tid == 0 && A.err) atomicExch(A.err, 1);
+    if (warp == 4) tc05::tmem_dealloc(tmem, Cfg::TMEM_COLS);
+}
+
+
+// ---------------------------------------------------------------------------
+// 3x3 convolution over image rows of W >= 128 pixels (W a multiple of 128)
+// without a gather.  A tile is 128 consecutive pixels (h, w0 .. w0+127) of
+// one image row.  For each block of CB input channels the producer loads the
+// tile's halo -- rows h-1 .. h+1, pixels w0-1 .. w0+128 -- with one TMA box
+// per 8-channel plane, laid out plane by plane with the pixels at a 16-byte
+// stride; the box's out-of-image part is zero-filled by the TMA unit.  In
+// that layout the A operand of tap (dy, dx) is the same 128 x CB tile
+// shifted by ((1 + dy) * 130 + 1 + dx) pixels: a K-major no-swizzle
+// descriptor with 8-row groups 128 B apart (SBO) and k-groups one plane
+// apart (LBO).  The whole weight tile [NT][Kp] stays in shared memory.
+// Warp roles: 0 TMA producer, 1 MMA issue, 2-5 epilogue (two TMEM
+// accumulators, as in k_conv).
+constexpr int HALO_PX = 130, HALO_ROWS = 3;
+constexpr int HALO_PLANE = ((HALO_PX * HALO_ROWS * 16 + 127) / 128) * 128;   // 6272 B, 128-B aligned
+
+template <int NT, int CB>
+struct HaloCfg {
+    static constexpr int STAGES = CB >= 64 ? 2 : 3;
+    static constexpr int STAGE_BYTES = (CB / 8) * HALO_PLANE;
+    static constexpr int WMAX = 96 * 1024;                 // resident weight tile limit
+    static constexpr int TC = NT < 32 ? 32 : NT;
+    static constexpr int TMEM_COLS = 2 * TC;
+    static constexpr int THREADS = 192;
+    static size_t smem(int Kp) { return (size_t)STAGES * STAGE_BYTES + (size_t)NT * Kp * 2 + 256 * 4 + (2 * STAGES + 4) * 8 + 16 + 1024; }
+};
+
+template <int NT, int CB>
+__global__ void __launch_bounds__(HaloCfg<NT, CB>::THREADS) k_conv_halo(ConvArgs A, const __grid_constant__ CUtensorMap tmap)
+{
+    using Cfg = HaloCfg<NT, CB>;
+    constexpr int S = Cfg::STAGES;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *base = smem_raw + ((1024 - (reinterpret_cast<uintptr_t>(smem_raw) & 1023)) & 1023);
+    uint8_t *wsm = base + S * Cfg::STAGE_BYTES;                        // weights, canonical per 64-chunk
+    float *sbias = reinterpret_cast<float *>(wsm + (size_t)NT * A.Kp * 2);
+    unsigned long long *full = reinterpret_cast<unsigned long long *>(sbias + 256);
+    unsigned long long *empty = full + S;
+    unsigned long long *accf = empty + S;
+    unsigned long long *acce = accf + 2;
+    uint32_t *tmem_word = reinterpret_cast<uint32_t *>(acce + 2);
+    volatile int *abort = reinterpret_cast<volatile int *>(tmem_word + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long M = (long long)A.B * A.H * A.W;
+    const int tiles = (int)(M / 128);
+    const int per_row = A.W / 128;
+    const int n0 = blockIdx.y * NT;
+    const int nb = A.cin / CB;                     // channel blocks
+    const int my_tiles = (int)blockIdx.x < tiles ? (tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int G = my_tiles * nb;
+    if (G == 0) return;
+    if (warp == 1) {
+        tc05::tmem_alloc(tc05::smem_u32(tmem_word), Cfg::TMEM_COLS);
+        tc05::tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int q = 0; q < S; ++q) {
+            tc05::mbar_init(tc05::smem_u32(&full[q]), 1);
+            tc05::mbar_init(tc05::smem_u32(&empty[q]), 1);
+        }
+        for (int q = 0; q < 2; ++q) {
+            tc05::mbar_init(tc05::smem_u32(&accf[q]), 1);
+            tc05::mbar_init(tc05::smem_u32(&acce[q]), 128);
+        }
+        *abort = 0;
+    }
+    // resident weights and biases
+    const uint32_t wbase = tc05::smem_u32(wsm);
+    for (int v = tid; v < NT * (A.Kp / 8); v += Cfg::THREADS) {
+        const int r = v % NT, kg = v / NT, k = kg * 8;
+        cp_async16(wbase + (k >> 6) * (NT * 128) + tc05::canon_off(r, k & 63), A.w + (long long)(n0 + r) * A.Kp + k, 16u);
+    }
+    cp_async_commit();
+    for (int i = tid; i < NT; i += Cfg::THREADS) sbias[i] = A.bias ? A.bias[n0 + i] : 0.0f;
+    cp_async_wait<0>();
+    tc05::fence_async_smem();
+    tc05::fence_before();
+    __syncthreads();
+    tc05::fence_after();
+    const uint32_t tmem = *tmem_word;
+    const uint32_t sbase = tc05::smem_u32(base);
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+#pragma unroll 1
+            for (int g = 0; g < G; ++g) {
+                const int slot = g % S;
+                if (!conv_wait(tc05::smem_u32(&empty[slot]), (uint32_t)(((g / S) & 1) ^ 1), abort)) break;
+                const int lt = g / nb, cb = g - lt * nb;
+                const int t = (int)blockIdx.x + lt * (int)gridDim.x;
+                const int rowi = t / per_row, w0 = (t - rowi * per_row) * 128;
+                const int b = rowi / A.H, h = rowi - b * A.H;
+                const uint32_t bar = tc05::smem_u32(&full[slot]);
+                tc05::mbar_arrive_expect_tx(bar, (uint32_t)((CB / 8) * HALO_PX * HALO_ROWS * 16));
+#pragma unroll
+                for (int q = 0; q < CB / 8; ++q)
+                    tc05::tma_load_4d(sbase + slot * Cfg::STAGE_BYTES + q * HALO_PLANE, &tmap, cb * CB + 8 * q, w0 - 1,
+                                      h - 1, b, bar);
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---------------- MMA issue ----------------
+        if (lane == 0) {
+            const uint32_t idesc = tc05::idesc_bf16(128, NT);
+            bool ok = true;
+#pragma unroll 1
+            for (int lt = 0; lt < my_tiles && ok; ++lt) {
+                const int acc = lt & 1;
+                if (!conv_wait(tc05::smem_u32(&acce[acc]), (uint32_t)(((lt >> 1) & 1) ^ 1), abort)) break;
+                tc05::fence_after();
+                const uint32_t d = tmem + (uint32_t)(acc * Cfg::TC);
+#pragma unroll 1
+                for (int cb = 0; cb < nb; ++cb) {
+                    const int g = lt * nb + cb, slot = g % S;
+                    if (!conv_wait(tc05::smem_u32(&full[slot]), (uint32_t)((g / S) & 1), abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc05::fence_after();
+                    const uint32_t hb = sbase + slot * Cfg::STAGE_BYTES;
+#pragma unroll 1
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const int ty = (tap * 11) >> 5, tx = tap - 3 * ty;        // tap / 3, tap % 3
+                        const uint32_t a_tap = hb + (uint32_t)((ty * HALO_PX + tx) * 16);
+                        const int kb = tap * A.cin + cb * CB;                     // weight column of this slice
+#pragma unroll
+                        for (int q = 0; q < CB / 16; ++q) {
+                            const int k = kb + 16 * q;
+                            const uint32_t b_k = wbase + (uint32_t)((k >> 6) * (NT * 128) + ((k & 63) >> 3) * 128);
+                            tc05::mma_bf16(d, tc05::sdesc(a_tap + (uint32_t)(2 * q * HALO_PLANE), HALO_PLANE, 128),
+                                           tc05::sdesc(b_k, tc05::CANON_LBO, tc05::CANON_SBO), idesc,
+                                           (cb > 0 || tap > 0 || q > 0) ? 1u : 0u);
+                        }
+                    }
+                    tc05::mma_commit(tc05::smem_u32(&empty[slot]));
+                }
+                if (ok) tc05::mma_commit(tc05::smem_u32(&accf[acc]));
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue ----------------
+        const int quarter = warp & 3;
+#pragma unroll 1
+        for (int lt = 0; lt < my_tiles; ++lt) {
+            const int acc = lt & 1;
+            if (!conv_wait(tc05::smem_u32(&accf[acc]), (uint32_t)((lt >> 1) & 1), abort)) break;
+            tc05::fence_after();
+            const long long m0 = ((long long)blockIdx.x + (long long)lt * gridDim.x) * 128;
+            conv_tile_epilogue<NT>(A, tmem, acc * Cfg::TC, quarter, m0, n0, M, sbias);
+            tc05::fence_before();
+            mbar_arrive(tc05::smem_u32(&acce[acc]));
+        }
+    }
+    tc05::fence_before();
+    __syncthreads();
+    if (*abort && tid == 0 && A.err) atomicExch(A.err, 1);
+    if (warp == 1) tc05::tmem_dealloc(tmem, Cfg::TMEM_COLS);
 }
 
 }  // namespace swof

@@ -36,7 +36,7 @@ typedef __nv_bfloat16 bf16;
 __device__ __forceinline__ float gelu_grad(float z)
 {
     const float phi = 0.39894228040143268f * __expf(-0.5f * z * z);
-    const float Phi = 0.5f * (1.0f + erff(z * 0.70710678118654752f));
+    const float Phi = 0.5f * (1.0f + erf_as(z * 0.70710678118654752f));
     return Phi + z * phi;
 }
 
@@ -250,6 +250,89 @@ int conv_launch(const ConvArgs &A, cudaStream_t s)
     return cudaGetLastError() == cudaSuccess ? SWOF_OK : SWOF_ECUDA;
 }
 
+// ---- TMA tensor maps (the encoder comes from the driver at run time) ----
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled()
+{
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+template <int NT, int CB>
+int conv_halo_launch(const ConvArgs &A, cudaStream_t s)
+{
+    using Cfg = HaloCfg<NT, CB>;
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return SWOF_ECUDA;
+    CUtensorMap tmap;
+    cuuint64_t dims[4] = {(cuuint64_t)A.cin, (cuuint64_t)A.W, (cuuint64_t)A.H, (cuuint64_t)A.B};
+    cuuint64_t strides[3] = {(cuuint64_t)A.cx * 2, (cuuint64_t)A.W * A.cx * 2, (cuuint64_t)A.H * A.W * A.cx * 2};
+    cuuint32_t box[4] = {8, (cuuint32_t)HALO_PX, (cuuint32_t)HALO_ROWS, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    if (enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)(A.x + A.xc0), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return SWOF_ECUDA;
+    const size_t smem = Cfg::smem(A.Kp);
+    static int per_sm = 0;
+    static size_t smem_set = 0;
+    if (smem > smem_set) {
+        if (cudaFuncSetAttribute(k_conv_halo<NT, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return SWOF_ECUDA;
+        smem_set = smem;
+        per_sm = 0;
+    }
+    if (!per_sm) {
+        int n = 0, dev = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_conv_halo<NT, CB>, Cfg::THREADS, smem) != cudaSuccess ||
+            n < 1)
+            n = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        per_sm = n * (sms > 0 ? sms : 152);
+    }
+    const long long tiles = (long long)A.B * A.H * A.W / 128;
+    const long long gy = A.ntot / NT;
+    long long gx = (per_sm + gy - 1) / gy;
+    if (gx > tiles) gx = tiles;
+    if (gx < 1) gx = 1;
+    k_conv_halo<NT, CB><<<dim3((unsigned)gx, (unsigned)gy), Cfg::THREADS, smem, s>>>(A, tmap);
+    return cudaGetLastError() == cudaSuccess ? SWOF_OK : SWOF_ECUDA;
+}
+
+template <int NT>
+int conv_halo(const ConvArgs &A, cudaStream_t s)
+{
+    switch (A.cin >= 64 ? 64 : A.cin) {
+    case 16: return conv_halo_launch<NT, 16>(A, s);
+    case 32: return conv_halo_launch<NT, 32>(A, s);
+    default: return conv_halo_launch<NT, 64>(A, s);
+    }
+}
+
+// 3x3 layers over rows of >= 128 pixels whose weight tile fits in shared
+// memory take the TMA halo kernel; the rest the gather kernel.
+bool halo_ok(const ConvArgs &A, int nt)
+{
+    return A.gather == GATHER_SAME && A.ks == 3 && A.store == STORE_NHWC && A.W % 128 == 0 && A.cin >= 16 &&
+           (A.cin >= 64 ? A.cin % 64 == 0 : true) && (size_t)nt * A.Kp * 2 <= (size_t)HaloCfg<32, 64>::WMAX &&
+           ((A.xc0 * 2) % 16 == 0) && ((A.cx * 2) % 16 == 0) && A.H <= 65535;
+}
+
 int conv(ConvArgs A, cudaStream_t s)
 {
     int nt = A.ntot >= 256 ? 256 : A.ntot;
@@ -258,6 +341,15 @@ int conv(ConvArgs A, cudaStream_t s)
         return SWOF_EINVAL;
     A.cin_shift = 0;
     while ((1 << A.cin_shift) < A.cin) ++A.cin_shift;
+    if (halo_ok(A, nt)) {
+        switch (nt) {
+        case 16: return conv_halo<16>(A, s);
+        case 32: return conv_halo<32>(A, s);
+        case 64: return conv_halo<64>(A, s);
+        case 128: return conv_halo<128>(A, s);
+        default: break;
+        }
+    }
     switch (nt) {
     case 16: return conv_launch<16>(A, s);
     case 32: return conv_launch<32>(A, s);

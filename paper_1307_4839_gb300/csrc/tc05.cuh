@@ -39,6 +39,27 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long lo
     return false;
 }
 
+// Arrive on the mbarrier and add `bytes` to the transaction count the
+// current phase waits for (the TMA copies complete them).
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// ---- TMA ----
+// Tiled 4-D tensor copy global -> shared described by a tensor map (in
+// kernel-parameter memory); completion is signalled on the mbarrier as
+// transaction bytes.  Out-of-range box elements are filled with zeros.
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const void *tmap, int c0, int c1, int c2, int c3,
+                                            uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+
 // ---- tensor memory ----
 // Allocate ncols (power of two, >= 32) TMEM columns; the address is written
 // to the shared-memory word dst.  Executed by one whole warp.

@@ -101,3 +101,38 @@ def test_training_reduces_loss():
     torch.cuda.synchronize()
     err = np.abs(out.cpu().numpy() - nxt).mean() / np.abs(nxt - state[:, :3]).mean()
     assert err < 0.5, err
+
+
+def test_wide_rows_take_the_tma_halo_path():
+    """At 128 x 128 the level-0 3x3 convolutions (rows of 128 pixels) run on
+    the TMA halo kernel in the forward pass and in the data gradients; the
+    network must still match the reference there."""
+    import torch
+    sw.build()
+    C, H, B = 16, 128, 1
+    net = sw.UNet(base=C, in_ch=4, out_ch=3, H=H, W=H, max_batch=B, seed=7)
+    rng = np.random.default_rng(4)
+    p = net.params()
+    for d in net.layout():
+        p[d["boff"]: d["boff"] + d["cout"]] = 0.1 * rng.standard_normal(d["cout"]).astype(np.float32)
+    d = net.layout()[-1]
+    p[d["woff"]: d["woff"] + d["ncols"] * d["Kp"]] *= 10.0
+    net.set_params(p)
+    x = np.zeros((B, H, H, 16), dtype=np.float32)
+    x[..., :4] = rng.standard_normal((B, H, H, 4))
+    tgt = rng.standard_normal((B, H, H, 3)).astype(np.float32)
+    dx = torch.tensor(x.reshape(-1, 16), device="cuda").to(torch.bfloat16).contiguous()
+    y = torch.zeros((B * H * H, 16), device="cuda")
+    net.forward_raw(dx, y)
+    torch.cuda.synchronize()
+    ref_net = UNetRef(C, 4, 3, p.astype(np.float64), use_bf16=True)
+    ref, _ = ref_net.forward(x.astype(np.float64))
+    got = y.cpu().numpy().reshape(B, H, H, 16)
+    assert rel_l2(got, ref) < 2e-2, rel_l2(got, ref)
+    loss = net.grads_raw(dx, torch.tensor(tgt.reshape(-1, 3), device="cuda").contiguous())
+    g = net.grads()
+    rloss, rg = ref_net.loss_and_grads(x.astype(np.float64), tgt.astype(np.float64))
+    assert abs(loss - rloss) <= 2e-2 * rloss
+    for k, dd in enumerate(net.layout()):
+        w = slice(dd["woff"], dd["woff"] + dd["ncols"] * dd["Kp"])
+        assert rel_l2(g[w], rg[w]) < 5e-2, (k, rel_l2(g[w], rg[w]))
