@@ -556,7 +556,8 @@ struct WgradArgs {
     const __nv_bfloat16 *g;    // output gradient
     int gc, gmode, cout_up;    // its channel stride; GATHER_SAME or GATHER_UP2 (transposed conv)
     const __nv_bfloat16 *x;    // layer input
-    int cx, xc0, cin, ks;      // input channel stride / offset / count, stencil (3 or 1)
+    int cx, xc0, cin, ks;      // input channel stride / offset / count (a power of two), stencil (3 or 1)
+    int cin_shift;             // log2(cin)
     int B, H, W;               // pixel grid of the reduction
     int nrows;                 // M' (number of valid rows n)
     int Kp;                    // row length of dW (padded K)
@@ -576,29 +577,78 @@ __device__ __forceinline__ void transpose8(const uint4 (&in)[8], uint4 (&out)[8]
         for (int i = 0; i < 8; ++i) d[j * 8 + i] = s[i * 8 + j];
 }
 
-__device__ __forceinline__ uint4 load_g(const WgradArgs &A, long long p, int n, long long P)
+// Eight consecutive pixels p0 .. p0+7 of the output-gradient rows n .. n+7
+// (16 bytes per pixel) into in[0..7]; zero beyond P or nrows.  The pixel
+// coordinates are decoded once and stepped.
+__device__ __forceinline__ void load_g8(const WgradArgs &A, int p0, int n, int P, uint4 (&in)[8])
 {
-    if (p >= P || n >= A.nrows) return make_uint4(0, 0, 0, 0);
-    if (A.gmode == GATHER_SAME) return *reinterpret_cast<const uint4 *>(A.g + p * A.gc + n);
+    if (n >= A.nrows) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) in[i] = make_uint4(0, 0, 0, 0);
+        return;
+    }
+    if (A.gmode == GATHER_SAME) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            in[i] = (p0 + i < P) ? *reinterpret_cast<const uint4 *>(A.g + (long long)(p0 + i) * A.gc + n)
+                                 : make_uint4(0, 0, 0, 0);
+        return;
+    }
     const int hw = A.H * A.W;
-    int sub = n / A.cout_up, o = n - sub * A.cout_up;
-    int b = (int)(p / hw), rem = (int)(p - (long long)b * hw);
-    int yy = rem / A.W, xx = rem - yy * A.W;
-    long long q = ((long long)b * 2 * A.H + 2 * yy + (sub >> 1)) * (2 * A.W) + 2 * xx + (sub & 1);
-    return *reinterpret_cast<const uint4 *>(A.g + q * A.gc + o);
+    const int sub = n / A.cout_up, o = n - sub * A.cout_up;
+    int b = p0 / hw, rem = p0 - b * hw;
+    int y = rem / A.W, x = rem - y * A.W;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        if (p0 + i < P) {
+            const long long q = ((long long)b * 2 * A.H + 2 * y + (sub >> 1)) * (2 * A.W) + 2 * x + (sub & 1);
+            in[i] = *reinterpret_cast<const uint4 *>(A.g + q * A.gc + o);
+        } else {
+            in[i] = make_uint4(0, 0, 0, 0);
+        }
+        if (++x == A.W) {
+            x = 0;
+            if (++y == A.H) {
+                y = 0;
+                ++b;
+            }
+        }
+    }
 }
 
-__device__ __forceinline__ uint4 load_x(const WgradArgs &A, long long p, int k, long long P)
+// Eight consecutive pixels p0 .. p0+7 of the gathered layer input at column
+// k (tap k / cin, channels k % cin .. +7), zero outside the image or beyond
+// the taps; decoded once and stepped.
+__device__ __forceinline__ void load_x8(const WgradArgs &A, int p0, int k, int P, uint4 (&in)[8])
 {
     const int taps = A.ks * A.ks;
-    int tap = k / A.cin, c = k - tap * A.cin;
-    if (p >= P || tap >= taps) return make_uint4(0, 0, 0, 0);
-    const int hw = A.H * A.W, half = A.ks >> 1;
-    int b = (int)(p / hw), rem = (int)(p - (long long)b * hw);
-    int yy = rem / A.W, xx = rem - yy * A.W;
-    int sy = yy + tap / A.ks - half, sx = xx + tap % A.ks - half;
-    if (sy < 0 || sy >= A.H || sx < 0 || sx >= A.W) return make_uint4(0, 0, 0, 0);
-    return *reinterpret_cast<const uint4 *>(A.x + (((long long)b * A.H + sy) * A.W + sx) * A.cx + A.xc0 + c);
+    const int tap = k >> A.cin_shift, c = k & (A.cin - 1);
+    if (tap >= taps) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) in[i] = make_uint4(0, 0, 0, 0);
+        return;
+    }
+    const int half = A.ks >> 1;
+    const int ty = A.ks == 3 ? (tap * 11) >> 5 : 0;      // tap / 3 for tap < 9
+    const int dy = ty - half, dx = tap - ty * A.ks - half;
+    const int hw = A.H * A.W;
+    int b = p0 / hw, rem = p0 - b * hw;
+    int y = rem / A.W, x = rem - y * A.W;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int sy = y + dy, sx = x + dx;
+        if (p0 + i < P && sy >= 0 && sy < A.H && sx >= 0 && sx < A.W)
+            in[i] = *reinterpret_cast<const uint4 *>(A.x + (long long)((b * A.H + sy) * A.W + sx) * A.cx + A.xc0 + c);
+        else
+            in[i] = make_uint4(0, 0, 0, 0);
+        if (++x == A.W) {
+            x = 0;
+            if (++y == A.H) {
+                y = 0;
+                ++b;
+            }
+        }
+    }
 }
 
 template <int NT>
@@ -643,8 +693,7 @@ __global__ void __launch_bounds__(128) k_wgrad(WgradArgs A)
         {
             int nb = tid & 15, pb = tid >> 4;
             uint4 in[8], out[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) in[i] = load_g(A, p0 + pb * 8 + i, nb0 + nb * 8, P);
+            load_g8(A, (int)p0 + pb * 8, nb0 + nb * 8, (int)P, in);
             transpose8(in, out);
 #pragma unroll
             for (int r = 0; r < 8; ++r)
@@ -654,8 +703,7 @@ __global__ void __launch_bounds__(128) k_wgrad(WgradArgs A)
         for (int blk = tid; blk < (NT / 8) * 8; blk += 128) {
             int kbk = blk % (NT / 8), pb = blk / (NT / 8);
             uint4 in[8], out[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) in[i] = load_x(A, p0 + pb * 8 + i, kb0 + kbk * 8, P);
+            load_x8(A, (int)p0 + pb * 8, kb0 + kbk * 8, (int)P, in);
             transpose8(in, out);
 #pragma unroll
             for (int r = 0; r < 8; ++r)

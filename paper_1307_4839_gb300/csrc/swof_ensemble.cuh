@@ -164,9 +164,9 @@ __global__ void __launch_bounds__(NTX) k_ensemble(EnsDesc<T> D)
         } else {
             int bx = (int)(local % I.gdx), by = (int)(local / I.gdx);
             if (s_phase == 1)
-                sweep_tile<T, 1, NTX, H>(I.P, I.F, bx, by, I.gdx, I.gdy, S);
+                sweep_tile<T, 1, NTX, H, false>(I.P, I.F, bx, by, I.gdx, I.gdy, S);
             else
-                sweep_tile<T, 2, NTX, H>(I.P, I.F, bx, by, I.gdx, I.gdy, S);
+                sweep_tile<T, 2, NTX, H, false>(I.P, I.F, bx, by, I.gdx, I.gdy, S);
         }
         __threadfence();
         __syncthreads();

@@ -72,7 +72,11 @@ struct SweepSmem {
 
 // One stage over the tile (bx, by) of a (gdx x gdy) tiling; the kernel
 // below maps it to its block index, the ensemble kernel to a queue item.
-template <typename T, int STAGE, int NTX, int H>
+// DRY_SKIP: let a CTA skip the x part of a row (and the wave speeds of three
+// rows) that is dry across its columns -- exact, and a large saving on
+// mostly dry grids; grids that are wet everywhere (the ensemble's rain
+// scenarios) run without the vote.
+template <typename T, int STAGE, int NTX, int H, bool DRY_SKIP = true>
 __device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, int bx, int by, int gdx, int gdy,
                                            SweepSmem<T, NTX> &S)
 {
@@ -171,7 +175,7 @@ __device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, 
             // A row with h = 0 in every column of the CTA has zero x fluxes
             // and a zero Fc (h_- + h_+ = 0): its x differences are +0, the
             // value a1..a3 already hold, so the CTA skips the x part.
-            if (!cta_and<NTX>(rc.h == T(0))) {
+            if (!(DRY_SKIP ? cta_and<NTX>(rc.h == T(0)) : (cta_sync<NTX>(), 0))) {
             Rec<T> q{};
             const bool rec = t >= 1 && t <= NTX - 2;
             if (rec) {
@@ -290,7 +294,8 @@ __device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, 
                 V4<T> *buf = S.nw[k & 1];
                 buf[t] = {fh, fu, fv, frh};
                 // all three rows of U^{n+1} dry across the CTA: every speed is 0
-                if (!cta_and<NTX>(fh == T(0) && y1h == T(0) && y2h == T(0)) && out_col && ro < P.ny) {
+                if (!(DRY_SKIP ? cta_and<NTX>(fh == T(0) && y1h == T(0) && y2h == T(0)) : (cta_sync<NTX>(), 0)) && out_col &&
+                    ro < P.ny) {
                     if (xlam) {
                         V4<T> L = buf[t - 1], R = buf[t + 1];
                         lx = kmax(lx, speed_key(cell_speed(L.x, fh, R.x, L.y, fu, R.y, frh, C.hdry, C.g)));

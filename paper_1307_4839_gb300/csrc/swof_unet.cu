@@ -379,8 +379,11 @@ int wgrad_launch(WgradArgs A, int ncols, cudaStream_t s)
     return cudaGetLastError() == cudaSuccess ? SWOF_OK : SWOF_ECUDA;
 }
 
-int wgrad(const WgradArgs &A, int ncols, cudaStream_t s)
+int wgrad(WgradArgs A, int ncols, cudaStream_t s)
 {
+    if (A.cin < 8 || (A.cin & (A.cin - 1)) || (long long)A.B * A.H * A.W >= (1LL << 31) / 4) return SWOF_EINVAL;
+    A.cin_shift = 0;
+    while ((1 << A.cin_shift) < A.cin) ++A.cin_shift;
     if (ncols % 256 == 0) return wgrad_launch<256>(A, ncols, s);
     if (ncols % 128 == 0) return wgrad_launch<128>(A, ncols, s);
     return wgrad_launch<64>(A, ncols, s);
