@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--ens-members", type=int, default=256)
     ap.add_argument("--ens-steps", type=int, default=1000)
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--unet-only", type=int, default=0, metavar="B",
+                    help="only time the surrogate network's forward at batch B (randomly initialised, 256^2)")
     ap.add_argument("--sur-train-traj", type=int, default=27, help="training trajectories (750 pairs each)")
     ap.add_argument("--sur-steps", type=int, default=2000, help="training steps (batch 16)")
     ap.add_argument("--sur-calls", type=int, default=50)
@@ -99,7 +101,9 @@ def recorded_traffic(kernel: str, precision: str, tile):
     csrc = os.path.join(ROOT, "paper_1307_4839_gb300", "csrc")
     src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("swof_kernels.cuh", "swof_sweep.cuh"))
     sha = hashlib.sha256(src).hexdigest()[:16]
-    f = os.path.join(ROOT, "profiles", f"k_sweep_{kernel}_{precision}_valley4096.txt")
+    if tile is None:
+        return None
+    f = os.path.join(ROOT, "profiles", f"k_sweep_{kernel}_{precision}_valley4096_{tile[0]}x{tile[1]}.txt")
     if not os.path.exists(f):
         return None
     vals = {}
@@ -109,7 +113,7 @@ def recorded_traffic(kernel: str, precision: str, tile):
             vals[k.strip()] = v.strip()
     if vals.get("kernel_source_sha256_16") != sha:
         return None
-    if tile is not None and f", {tile[0]}, {tile[1]}>" not in vals.get("kernel", ""):
+    if f", {tile[0]}, {tile[1]}>" not in vals.get("kernel", ""):
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
@@ -473,6 +477,33 @@ def measure_surrogate(sw, torch, args, peak_tf):
     return out
 
 
+def unet_forward_only(sw, torch, B: int, steps: int, warmup: int):
+    """The surrogate network's forward alone: base 32, 8 input and 4 output
+    channels, 256^2, batch B, random weights and inputs."""
+    import numpy as np
+    H = 256
+    net = sw.UNet(base=32, in_ch=8, out_ch=4, H=H, W=H, max_batch=B, seed=0)
+    net.set_norm(np.zeros(8), np.ones(8), np.ones(4))
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    x = torch.randn(B, 8, H, H, device="cuda")
+    y = torch.zeros(B, 4, H, H, device="cuda")
+    for _ in range(warmup):
+        net.predict(x, y, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        net.predict(x, y, stream=stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    fl = unet_flops(net.layout(), H) * B
+    print(json.dumps({"what": "surrogate U-Net forward", "batch": B, "ms": ms, "tflops": fl / (ms * 1e-3) * 1e-12,
+                      "frac_of_bf16_peak": fl / (ms * 1e-3) * 1e-12 / bf16_peak()}), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
@@ -485,6 +516,9 @@ def main():
     sw.build()
     sw.load()
     torch.cuda.set_device(local)
+    if args.unet_only:
+        unet_forward_only(sw, torch, args.unet_only, args.steps, args.warmup)
+        return
     w = workload(args.n)
     cells = w.nx * w.ny
     hbm, peak_kind = peaks()
