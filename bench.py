@@ -69,10 +69,13 @@ def parse():
     ap.add_argument("--ens-members", type=int, default=256)
     ap.add_argument("--ens-steps", type=int, default=1000)
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--unet-only", type=int, default=0, metavar="B",
                     help="only time the surrogate network's forward at batch B (randomly initialised, 256^2)")
     ap.add_argument("--sur-train-traj", type=int, default=27, help="training trajectories (750 pairs each)")
-    ap.add_argument("--sur-steps", type=int, default=2000, help="training steps (batch 16)")
+    ap.add_argument("--sur-steps", type=int, default=2000, help="training steps")
+    ap.add_argument("--sur-batch", type=int, default=16)
+    ap.add_argument("--sur-lr", type=float, default=2e-3)
     ap.add_argument("--sur-calls", type=int, default=50)
     ap.add_argument("--sur-members", type=int, default=512)
     return ap.parse_args()
@@ -351,6 +354,56 @@ def measure_ensemble(sw, torch, args, ws):
             "accuracy": "per-member relative L1 vs the FP64 oracle in tests/test_gpu_ensemble.py"}
 
 
+def measure_fp32_accuracy(sw):
+    """Relative L1 of the FP32 path against the FP64 path (which equals the
+    CPU oracle bit for bit, tests/test_gpu_parity.py) per workload: the dam
+    break to t = 1 s (each with its own CFL dt), the 4096^2 valley and the
+    2048^2 rainfall hillslope on the FP64 dt sequence, lake-at-rest drift."""
+    import numpy as np
+    import swof_inputs as si
+
+    def rel(a, b):
+        return float(np.abs(a - b).sum() / max(np.abs(b).sum(), 1e-300))
+
+    out = {}
+    w = si.dam_break(200)
+    st = {}
+    for name, prec in (("fp64", sw.FP64), ("fp32", sw.FP32)):
+        s = sw.Solver.from_workload(w, prec)
+        for _ in range(5000):
+            if s.step(1).t >= w.t_end:
+                break
+        st[name] = s.state()
+        s.close()
+    out["dam_break_200_t1s"] = {"h": rel(st["fp32"][0], st["fp64"][0]), "hu": rel(st["fp32"][1], st["fp64"][1])}
+    for key, w, n in (("valley_4096_200_steps", si.valley(4096), 200),
+                      ("hillslope_2048_600_steps_rain_ga", si.hillslope(2048), 600)):
+        s64 = sw.Solver.from_workload(w, sw.FP64)
+        s64.step(n)
+        dts = s64.dt_history(n)
+        a = s64.state() + (s64.infiltrated(),)
+        t64 = s64.diagnostics()["t"]
+        s64.close()
+        s32 = sw.Solver.from_workload(w, sw.FP32)
+        s32.set_dt_sequence(dts)
+        s32.step(n)
+        b = s32.state() + (s32.infiltrated(),)
+        s32.close()
+        r = {f: rel(y, x) for f, x, y in zip(("h", "hu", "hv", "V_inf"), a, b) if np.abs(x).sum() > 0}
+        r["t_s"] = t64
+        out[key] = r
+    w = si.lake_at_rest(n=64, level=1.0)
+    s = sw.Solver.from_workload(w, sw.FP32)
+    s.step(1000)
+    h, qx, qy = s.state()
+    wet = w.h > 0
+    out["lake_at_rest_64_1000_steps"] = {"max_surface_drift_m": float(np.max(np.abs((h + w.z)[wet] - 1.0))),
+                                         "max_abs_q": float(max(np.abs(qx).max(), np.abs(qy).max()))}
+    s.close()
+    out["target"] = "relative L1 <= 1e-5 (FP32 vs FP64)"
+    return out
+
+
 def unet_flops(layout, H: int) -> float:
     """Multiply-adds x 2 of one forward sample over the real (unpadded)
     channels: the algorithmic FLOPs of the network."""
@@ -390,7 +443,8 @@ def measure_surrogate(sw, torch, args, peak_tf):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     t0 = time.perf_counter()
-    losses = S.train(net, ds, pairs, steps=args.sur_steps, batch=16, lr=2e-3, seed=0, stream=stream.cuda_stream)
+    losses = S.train(net, ds, pairs, steps=args.sur_steps, batch=args.sur_batch, lr=args.sur_lr, seed=0,
+                     stream=stream.cuda_stream)
     train_s = time.perf_counter() - t0
     per = max(1, args.sur_members // n_te)
     span_max = n_spans - args.sur_calls
@@ -464,7 +518,8 @@ def measure_surrogate(sw, torch, args, peak_tf):
            "fp32_judge_vs_fp64": dict(zip(ch, map(float, e_judge))),
            "persistence_rel_l1": dict(zip(ch, map(float, e_per))),
            "coarse_solver_rel_l1": dict(zip(ch, map(float, e_crs))),
-           "training": {"pairs": int(len(pairs)), "steps": args.sur_steps, "batch": 16, "s": train_s,
+           "training": {"pairs": int(len(pairs)), "steps": args.sur_steps, "batch": args.sur_batch,
+                        "lr": args.sur_lr, "s": train_s,
                         "loss_first": float(losses[:20].mean()), "loss_last": float(losses[-20:].mean()),
                         "params": net.nparam},
            "data_generation_s": gen_s,
@@ -584,6 +639,8 @@ def main():
     if not args.no_surrogate and P == "fp32":
         variants["surrogate"] = measure_surrogate(sw, torch, args, bf16_peak())
 
+    accuracy = measure_fp32_accuracy(sw) if (P == "fp32" and not args.no_accuracy) else None
+
 
     e2e = None
     if not args.no_e2e:
@@ -629,6 +686,7 @@ def main():
         "gpu_launches": launches,
         "clocks": clk,
         "variants": variants,
+        "fp32_accuracy": accuracy,
         "final_state": {"t": diag["t"], "volume": diag["volume"], "min_h": diag["min_h"]},
     }
     if rank == 0:
