@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--side", type=int, default=4096, help="valley grid side (cells)")
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -239,7 +239,7 @@ def run_reference(args, ws, rank):
         return
     import oracle
     oracle.build()
-    w = workload(args.n)
+    w = workload(args.side)
     cells = w.nx * w.ny
     import oracle as orc
     o = orc.Oracle.from_workload(w)
@@ -574,7 +574,7 @@ def main():
     if args.unet_only:
         unet_forward_only(sw, torch, args.unet_only, args.steps, args.warmup)
         return
-    w = workload(args.n)
+    w = workload(args.side)
     cells = w.nx * w.ny
     hbm, peak_kind = peaks()
 

@@ -390,26 +390,38 @@ __global__ void __launch_bounds__(ConvCfg<NT>::THREADS) k_conv(ConvArgs A)
 // descriptor with 8-row groups 128 B apart (SBO) and k-groups one plane
 // apart (LBO).  The whole weight tile [NT][Kp] stays in shared memory.
 // Warp roles: 0 TMA producer, 1 MMA issue, 2-5 epilogue (two TMEM
-// accumulators, as in k_conv).
+// accumulators, as in k_conv).  The halo ring has S stages, as many as
+// fit beside the weights (2 .. 6).
 constexpr int HALO_PX = 130, HALO_ROWS = 3;
 constexpr int HALO_PLANE = ((HALO_PX * HALO_ROWS * 16 + 127) / 128) * 128;   // 6272 B, 128-B aligned
 
 template <int NT, int CB>
 struct HaloCfg {
-    static constexpr int STAGES = CB >= 64 ? 2 : 3;
+    static constexpr int MAX_STAGES = 6;
     static constexpr int STAGE_BYTES = (CB / 8) * HALO_PLANE;
-    static constexpr int WMAX = 96 * 1024;                 // resident weight tile limit
+    static constexpr int WMAX = 160 * 1024;                // resident weight tile limit
+    static constexpr int SMEM_MAX = 227 * 1024;
     static constexpr int TC = NT < 32 ? 32 : NT;
     static constexpr int TMEM_COLS = 2 * TC;
     static constexpr int THREADS = 192;
-    static size_t smem(int Kp) { return (size_t)STAGES * STAGE_BYTES + (size_t)NT * Kp * 2 + 256 * 4 + (2 * STAGES + 4) * 8 + 16 + 1024; }
+    static size_t smem(int Kp, int stages)
+    {
+        return (size_t)stages * STAGE_BYTES + (size_t)NT * Kp * 2 + 256 * 4 + (2 * MAX_STAGES + 4) * 8 + 16 + 1024;
+    }
+    // the deepest ring (2 .. MAX_STAGES) that fits beside the weights; 0 if none
+    static int stages(int Kp)
+    {
+        for (int sgs = MAX_STAGES; sgs >= 2; --sgs)
+            if (smem(Kp, sgs) <= (size_t)SMEM_MAX) return sgs;
+        return 0;
+    }
 };
 
 template <int NT, int CB>
-__global__ void __launch_bounds__(HaloCfg<NT, CB>::THREADS) k_conv_halo(ConvArgs A, const __grid_constant__ CUtensorMap tmap)
+__global__ void __launch_bounds__(HaloCfg<NT, CB>::THREADS)
+    k_conv_halo(ConvArgs A, const __grid_constant__ CUtensorMap tmap, int S)
 {
     using Cfg = HaloCfg<NT, CB>;
-    constexpr int S = Cfg::STAGES;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *base = smem_raw + ((1024 - (reinterpret_cast<uintptr_t>(smem_raw) & 1023)) & 1023);
     uint8_t *wsm = base + S * Cfg::STAGE_BYTES;                        // weights, canonical per 64-chunk

@@ -286,7 +286,9 @@ int conv_halo_launch(const ConvArgs &A, cudaStream_t s)
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return SWOF_ECUDA;
-    const size_t smem = Cfg::smem(A.Kp);
+    const int stages = Cfg::stages(A.Kp);
+    if (stages < 2) return SWOF_EINVAL;
+    const size_t smem = Cfg::smem(A.Kp, stages);
     static int per_sm = 0;
     static size_t smem_set = 0;
     if (smem > smem_set) {
@@ -310,27 +312,49 @@ int conv_halo_launch(const ConvArgs &A, cudaStream_t s)
     long long gx = (per_sm + gy - 1) / gy;
     if (gx > tiles) gx = tiles;
     if (gx < 1) gx = 1;
-    k_conv_halo<NT, CB><<<dim3((unsigned)gx, (unsigned)gy), Cfg::THREADS, smem, s>>>(A, tmap);
+    k_conv_halo<NT, CB><<<dim3((unsigned)gx, (unsigned)gy), Cfg::THREADS, smem, s>>>(A, tmap, stages);
     return cudaGetLastError() == cudaSuccess ? SWOF_OK : SWOF_ECUDA;
+}
+
+// Channel block of the halo kernel: the widest of 64, 32, 16 (dividing cin)
+// whose halo stages fit in shared memory beside the resident weight tile;
+// 0 if none does.
+template <int NT>
+int halo_cb(const ConvArgs &A)
+{
+    if (A.cin % 64 == 0 && HaloCfg<NT, 64>::stages(A.Kp) >= 2) return 64;
+    if (A.cin % 32 == 0 && HaloCfg<NT, 32>::stages(A.Kp) >= 3) return 32;
+    if (A.cin % 16 == 0 && HaloCfg<NT, 16>::stages(A.Kp) >= 3) return 16;
+    return 0;
 }
 
 template <int NT>
 int conv_halo(const ConvArgs &A, cudaStream_t s)
 {
-    switch (A.cin >= 64 ? 64 : A.cin) {
+    switch (halo_cb<NT>(A)) {
     case 16: return conv_halo_launch<NT, 16>(A, s);
     case 32: return conv_halo_launch<NT, 32>(A, s);
-    default: return conv_halo_launch<NT, 64>(A, s);
+    case 64: return conv_halo_launch<NT, 64>(A, s);
+    default: return SWOF_EINVAL;
     }
 }
 
 // 3x3 layers over rows of >= 128 pixels whose weight tile fits in shared
-// memory take the TMA halo kernel; the rest the gather kernel.
+// memory (beside the halo stages) take the TMA halo kernel; the rest the
+// gather kernel.
 bool halo_ok(const ConvArgs &A, int nt)
 {
-    return A.gather == GATHER_SAME && A.ks == 3 && A.store == STORE_NHWC && A.W % 128 == 0 && A.cin >= 16 &&
-           (A.cin >= 64 ? A.cin % 64 == 0 : true) && (size_t)nt * A.Kp * 2 <= (size_t)HaloCfg<32, 64>::WMAX &&
-           ((A.xc0 * 2) % 16 == 0) && ((A.cx * 2) % 16 == 0) && A.H <= 65535;
+    if (!(A.gather == GATHER_SAME && A.ks == 3 && A.store == STORE_NHWC && A.W % 128 == 0 && A.cin >= 16 &&
+          ((A.xc0 * 2) % 16 == 0) && ((A.cx * 2) % 16 == 0) && A.H <= 65535 &&
+          (size_t)nt * A.Kp * 2 <= (size_t)HaloCfg<32, 64>::WMAX))
+        return false;
+    switch (nt) {
+    case 16: return halo_cb<16>(A) != 0;
+    case 32: return halo_cb<32>(A) != 0;
+    case 64: return halo_cb<64>(A) != 0;
+    case 128: return halo_cb<128>(A) != 0;
+    default: return false;
+    }
 }
 
 int conv(ConvArgs A, cudaStream_t s)

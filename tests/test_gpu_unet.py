@@ -136,3 +136,29 @@ def test_wide_rows_take_the_tma_halo_path():
     for k, dd in enumerate(net.layout()):
         w = slice(dd["woff"], dd["woff"] + dd["ncols"] * dd["Kp"])
         assert rel_l2(g[w], rg[w]) < 5e-2, (k, rel_l2(g[w], rg[w]))
+
+
+def test_base32_at_256_forward_matches_reference():
+    """The surrogate's own size: base 32 at 256 x 256, where the level-1
+    decoder convolution (128 input channels, a 147 KB weight tile) runs on
+    the halo kernel with 32-channel blocks."""
+    import torch
+    sw.build()
+    C, H, B = 32, 256, 1
+    net = sw.UNet(base=C, in_ch=4, out_ch=3, H=H, W=H, max_batch=B, seed=9)
+    rng = np.random.default_rng(6)
+    p = net.params()
+    for d in net.layout():
+        p[d["boff"]: d["boff"] + d["cout"]] = 0.1 * rng.standard_normal(d["cout"]).astype(np.float32)
+    d = net.layout()[-1]
+    p[d["woff"]: d["woff"] + d["ncols"] * d["Kp"]] *= 10.0
+    net.set_params(p)
+    x = np.zeros((B, H, H, 16), dtype=np.float32)
+    x[..., :4] = rng.standard_normal((B, H, H, 4))
+    dx = torch.tensor(x.reshape(-1, 16), device="cuda").to(torch.bfloat16).contiguous()
+    y = torch.zeros((B * H * H, 16), device="cuda")
+    net.forward_raw(dx, y)
+    torch.cuda.synchronize()
+    ref, _ = UNetRef(C, 4, 3, p.astype(np.float64), use_bf16=True).forward(x.astype(np.float64))
+    got = y.cpu().numpy().reshape(B, H, H, 16)
+    assert rel_l2(got, ref) < 2e-2, rel_l2(got, ref)
