@@ -126,11 +126,15 @@ SWOF_API void swof_destroy(swof_ctx *ctx);
 
 /* Set the conservative state (h, hu, hv), host [ny][nx] float64, copied and
  * converted to the context precision; ghosts are refilled.  Rejects NaN/Inf
- * (SWOF_ENONFINITE) and h < 0 (SWOF_ENEGATIVE) before touching the state. */
+ * (SWOF_ENONFINITE) and h < 0 (SWOF_ENEGATIVE) before touching the state.
+ * The arrays are copied to a device staging buffer (3 nx ny doubles,
+ * allocated on the first host exchange and kept) and checked there; pinned
+ * host memory makes the copy a direct DMA.  Synchronises. */
 SWOF_API int swof_set_state(swof_ctx *ctx, const double *h, const double *hu, const double *hv);
 
-/* Copy the state to host arrays [ny][nx] float64 (FP32 values widened).
- * Synchronises; returns a latched device status if one is set. */
+/* Copy the state to host arrays [ny][nx] float64 (FP32 values widened,
+ * through the same device staging buffer).  Synchronises; returns a latched
+ * device status if one is set. */
 SWOF_API int swof_get_state(swof_ctx *ctx, double *h, double *hu, double *hv);
 
 /* Same with device pointers of dense [ny][nx] arrays of the given dtype

@@ -264,10 +264,18 @@ class Solver:
         h, qx, qy = _f64(h), _f64(qx), _f64(qy)
         _check(load().swof_set_state(self._ctx, _ptr(h), _ptr(qx), _ptr(qy)), "swof_set_state")
 
-    def state(self):
-        h = np.empty((self.ny, self.nx))
-        qx = np.empty_like(h)
-        qy = np.empty_like(h)
+    def state(self, out=None):
+        """(h, hu, hv) as float64 [ny][nx] host arrays; `out` = three
+        caller arrays (e.g. views of pinned memory) to fill instead."""
+        if out is None:
+            h = np.empty((self.ny, self.nx))
+            qx = np.empty_like(h)
+            qy = np.empty_like(h)
+        else:
+            h, qx, qy = out
+            for a in out:
+                if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != self.nx * self.ny:
+                    raise ValueError("out arrays must be contiguous float64 [ny][nx]")
         _check(load().swof_get_state(self._ctx, _ptr(h), _ptr(qx), _ptr(qy)), "swof_get_state")
         return h, qx, qy
 

@@ -391,6 +391,8 @@ void swof_destroy(swof_ctx *c)
     for (void *p : c->allocs) cudaFree(p);
     if (c->dt_seq) cudaFree(c->dt_seq);
     if (c->dt_hist) cudaFree(c->dt_hist);
+    if (c->staging) cudaFree(c->staging);
+    if (c->d_flag) cudaFree(c->d_flag);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     cudaSetDevice(dev);
     delete c;
@@ -403,23 +405,60 @@ static int clear_status(swof_ctx *c)
 
 __global__ void k_set_time(DevCtl *ctl, double t) { ctl->t = t; }
 
+// Check a host state copied to the device: bit 1 of *flag for NaN/Inf,
+// bit 2 for h < 0.
+__global__ void k_check_state(const double *s, long long n, int *flag)
+{
+    int f = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 3 * n; i += (long long)gridDim.x * blockDim.x) {
+        const double v = s[i];
+        if (!isfinite(v)) f |= 1;
+        else if (i < n && v < 0.0) f |= 2;
+    }
+    f = __reduce_or_sync(0xffffffffu, f);
+    if (f && (threadIdx.x & 31) == 0) atomicOr(flag, f);
+}
+
+// The staging buffer [3][ny][nx] of doubles and the flag word (allocated on
+// first use, kept until destroy).
+static int ensure_staging(swof_ctx *c)
+{
+    if (c->staging) return SWOF_OK;
+    const size_t n = (size_t)c->P.nx * c->P.ny;
+    if (cudaMalloc(&c->staging, 3 * n * sizeof(double)) != cudaSuccess) {
+        c->staging = nullptr;
+        return SWOF_ENOMEM;
+    }
+    if (cudaMalloc(&c->d_flag, sizeof(int)) != cudaSuccess) return SWOF_ENOMEM;
+    return SWOF_OK;
+}
+
+// Host arrays are copied to a device staging buffer (from pinned memory
+// this is a plain DMA), checked there, and only then converted into the
+// state: a rejected state leaves the old one untouched.
 int swof_set_state(swof_ctx *c, const double *h, const double *hu, const double *hv)
 {
     if (!c || !h || !hu || !hv) return SWOF_EINVAL;
-    size_t n = (size_t)c->P.nx * c->P.ny;
-    if (!all_finite(h, n) || !all_finite(hu, n) || !all_finite(hv, n)) return SWOF_ENONFINITE;
-    for (size_t k = 0; k < n; ++k)
-        if (h[k] < 0.0) return SWOF_ENEGATIVE;
-    int st;
-    if (c->prec == SWOF_FP64) {
-        st = upload_interior<double>(c, c->f64.h, h);
-        if (!st) st = upload_interior<double>(c, c->f64.qx, hu);
-        if (!st) st = upload_interior<double>(c, c->f64.qy, hv);
-    } else {
-        st = upload_interior<float>(c, c->f32.h, h);
-        if (!st) st = upload_interior<float>(c, c->f32.qx, hu);
-        if (!st) st = upload_interior<float>(c, c->f32.qy, hv);
-    }
+    int st = ensure_staging(c);
+    if (st) return st;
+    const size_t n = (size_t)c->P.nx * c->P.ny;
+    double *s0 = c->staging, *s1 = s0 + n, *s2 = s1 + n;
+    cudaError_t e = cudaMemcpyAsync(s0, h, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s1, hu, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s2, hv, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream);
+    if (e != cudaSuccess) return SWOF_ECUDA;
+    long long blocks = ((long long)(3 * n) + 255) / 256;
+    k_check_state<<<(unsigned)(blocks < 152 * 16 ? (blocks > 0 ? blocks : 1) : 152 * 16), 256, 0, c->stream>>>(
+        s0, (long long)n, c->d_flag);
+    int flag = 0;
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return SWOF_ECUDA;
+    if (flag & 1) return SWOF_ENONFINITE;
+    if (flag & 2) return SWOF_ENEGATIVE;
+    st = cuda_err((cudaError_t)c->L->unpack(c->P, c->fields(), s0, s1, s2, SWOF_FP64, c->stream));
     if (!st) st = cuda_err((cudaError_t)c->L->ghosts(c->P, c->fields(), c->stream));
     if (!st) st = clear_status(c);
     if (!st) st = invalidate_lambda(c);
@@ -429,20 +468,21 @@ int swof_set_state(swof_ctx *c, const double *h, const double *hu, const double 
 int swof_get_state(swof_ctx *c, double *h, double *hu, double *hv)
 {
     if (!c || !h || !hu || !hv) return SWOF_EINVAL;
-    int st;
-    if (c->prec == SWOF_FP64) {
-        st = download_interior<double>(c, c->f64.h, h);
-        if (!st) st = download_interior<double>(c, c->f64.qx, hu);
-        if (!st) st = download_interior<double>(c, c->f64.qy, hv);
-    } else {
-        st = download_interior<float>(c, c->f32.h, h);
-        if (!st) st = download_interior<float>(c, c->f32.qx, hu);
-        if (!st) st = download_interior<float>(c, c->f32.qy, hv);
-    }
+    int st = ensure_staging(c);
     if (st) return st;
+    const size_t n = (size_t)c->P.nx * c->P.ny;
+    double *s0 = c->staging, *s1 = s0 + n, *s2 = s1 + n;
+    st = cuda_err((cudaError_t)c->L->pack(c->P, c->fields(), s0, s1, s2, SWOF_FP64, c->stream));
+    if (st) return st;
+    cudaError_t e = cudaMemcpyAsync(h, s0, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hu, s1, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hv, s2, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return SWOF_ECUDA;
     DevCtl d;
     st = read_ctl(c, &d);
-    return st ? st : d.status;
+    if (st) return st;
+    return d.status;
 }
 
 int swof_set_state_device(swof_ctx *c, const void *h, const void *hu, const void *hv, int dtype)

@@ -44,6 +44,9 @@ struct swof_ctx {
     std::vector<cudaEvent_t> ev;
     int ev_used = 0;
     int launches_last = 0;
+    // device staging of host state exchange: [3][ny][nx] doubles + a flag word
+    double *staging = nullptr;
+    int *d_flag = nullptr;
 
     void *fields() { return prec == SWOF_FP64 ? (void *)&f64 : (void *)&f32; }
 };
