@@ -439,7 +439,7 @@ def measure_surrogate(sw, torch, args, peak_tf):
     ds = S.generate(works, f, dt, span_steps, n_spans)
     gen_s = time.perf_counter() - t0
     pairs = ds.pairs(range(n_tr))
-    net = S.make_net(ds, pairs, base=32, max_batch=32, seed=0)
+    net = S.make_net(ds, pairs, base=32, max_batch=64, seed=0)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     t0 = time.perf_counter()
@@ -478,7 +478,7 @@ def measure_surrogate(sw, torch, args, peak_tf):
     e_judge = S.rel_l1(judge[sel], j64)
     ro.close()
     # forward throughput of the network alone (tensor cores)
-    B = 32
+    B = 64
     x = ro.states[:B].contiguous()
     y = torch.empty((B, S.OUT_CH) + tuple(x.shape[-2:]), device="cuda")
     for _ in range(2):

@@ -109,7 +109,11 @@ struct ConvCfg {
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr int TC = NT < 32 ? 32 : NT;           // columns of one accumulator
     static constexpr int TMEM_COLS = 2 * TC;               // two accumulators
-    static constexpr int THREADS = 288;                    // 4 producer, 1 MMA, 4 epilogue warps
+#ifndef CONV_PRODUCER_WARPS
+#define CONV_PRODUCER_WARPS 4
+#endif
+    static constexpr int PRODUCER_WARPS = CONV_PRODUCER_WARPS;
+    static constexpr int THREADS = 32 * (PRODUCER_WARPS + 5);   // producers, 1 MMA, 4 epilogue warps
     static constexpr int BIAS_BYTES = 256 * 4;
     static constexpr int BAR_BYTES = (2 * STAGES + 4) * 8 + 16;
     static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + BIAS_BYTES + BAR_BYTES + 1024;
@@ -224,13 +228,16 @@ __global__ void __launch_bounds__(ConvCfg<NT>::THREADS) k_conv(ConvArgs A)
     const int my_tiles = (int)blockIdx.x < tiles ? (tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const int G = my_tiles * nk;
     if (G == 0) return;             // uniform: nothing allocated yet
-    if (warp == 4) {
+    constexpr int PW = Cfg::PRODUCER_WARPS, PT = 32 * PW;   // producer warps / threads
+    constexpr int RPT = 1024 / PT;                          // A rows per producer thread
+    constexpr int RSTEP = PT / 8;                           // row step between them
+    if (warp == PW) {
         tc05::tmem_alloc(tc05::smem_u32(tmem_word), Cfg::TMEM_COLS);
         tc05::tmem_relinquish();
     }
     if (tid == 0) {
         for (int q = 0; q < S; ++q) {
-            tc05::mbar_init(tc05::smem_u32(&full[q]), 128);
+            tc05::mbar_init(tc05::smem_u32(&full[q]), PT);
             tc05::mbar_init(tc05::smem_u32(&empty[q]), 1);
         }
         for (int q = 0; q < 2; ++q) {
@@ -247,20 +254,20 @@ __global__ void __launch_bounds__(ConvCfg<NT>::THREADS) k_conv(ConvArgs A)
     const uint32_t sbase = tc05::smem_u32(base);
     const int hw = A.H * A.W;
 
-    if (warp < 4) {
+    if (warp < PW) {
         // ---------------- producers ----------------
         const int j = tid & 7;
         const int taps = (A.gather == GATHER_SAME) ? A.ks * A.ks : 4;
         const int half = A.ks >> 1;
-        int ry[8], rx[8], rbase[8];
+        int ry[RPT], rx[RPT], rbase[RPT];
         int dec_tile = -1;
-        auto decode = [&](int ti) {           // rows r_i = r0 + 16 i, 16 pixels apart
+        auto decode = [&](int ti) {           // rows r_i = r0 + RSTEP i, RSTEP pixels apart
             const int m0 = ((int)blockIdx.x + ti * (int)gridDim.x) * 128;
             int p = m0 + (tid >> 3);
             int b = p / hw, rem = p - b * hw;
             int y = rem / A.W, x = rem - y * A.W;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
+            for (int i = 0; i < RPT; ++i) {
                 if (p < (int)M) {
                     ry[i] = y;
                     rx[i] = x;
@@ -269,8 +276,8 @@ __global__ void __launch_bounds__(ConvCfg<NT>::THREADS) k_conv(ConvArgs A)
                     ry[i] = rx[i] = 0;
                     rbase[i] = -1;
                 }
-                p += 16;
-                x += 16;
+                p += RSTEP;
+                x += RSTEP;
                 while (x >= A.W) {
                     x -= A.W;
                     if (++y == A.H) {
@@ -301,8 +308,8 @@ __global__ void __launch_bounds__(ConvCfg<NT>::THREADS) k_conv(ConvArgs A)
                 toff = (tap >> 1) * (2 * A.W) + (tap & 1);
             }
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int r = (tid >> 3) + 16 * i;
+            for (int i = 0; i < RPT; ++i) {
+                const int r = (tid >> 3) + RSTEP * i;
                 bool ok = rbase[i] >= 0 && tap < taps;
                 if (A.gather == GATHER_SAME) {
                     const int sy = ry[i] + dy, sx = rx[i] + dx;
@@ -311,7 +318,7 @@ __global__ void __launch_bounds__(ConvCfg<NT>::THREADS) k_conv(ConvArgs A)
                 const __nv_bfloat16 *src = ok ? A.x + (long long)(rbase[i] + toff) * A.cx + A.xc0 + c : A.x;
                 cp_async16(sa + tc05::canon_off(r, 8 * j), src, ok ? 16u : 0u);
             }
-            for (int v = tid; v < NT * 8; v += 128) {
+            for (int v = tid; v < NT * 8; v += PT) {
                 const int r = v >> 3, jj = v & 7;
                 cp_async16(sb + tc05::canon_off(r, 8 * jj), A.w + (long long)(n0 + r) * A.Kp + kc * 64 + 8 * jj, 16u);
             }
@@ -326,7 +333,7 @@ __global__ void __launch_bounds__(ConvCfg<NT>::THREADS) k_conv(ConvArgs A)
         tc05::fence_async_smem();
         if (g == G)
             for (int q = (G > S - 2 ? G - (S - 2) : 0); q < G; ++q) mbar_arrive(tc05::smem_u32(&full[q % S]));
-    } else if (warp == 4) {
+    } else if (warp == PW) {
         // ---------------- MMA issue ----------------
         if (lane == 0) {
             const uint32_t idesc = tc05::idesc_bf16(128, NT);
@@ -374,7 +381,7 @@ __global__ void __launch_bounds__(ConvCfg<NT>::THREADS) k_conv(ConvArgs A)
     tc05::fence_before();
     __syncthreads();
     if (*abort && tid == 0 && A.err) atomicExch(A.err, 1);
-    if (warp == 4) tc05::tmem_dealloc(tmem, Cfg::TMEM_COLS);
+    if (warp == PW) tc05::tmem_dealloc(tmem, Cfg::TMEM_COLS);
 }
 
 
