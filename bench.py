@@ -43,9 +43,12 @@ BYTES = {
     "fp64": {"lambda": 24, "stage1": 24 + 8 + 24, "stage2": 24 + 8 + 24 + 24},
 }
 # Algorithmic bytes of a whole step with the wave speeds fused away: U^n and
-# z read and U* written in stage 1, U*, z, U^n read and U^{n+1} written in
-# stage 2 (17 words per cell).
-STEP_BYTES = {"fp32": 68, "fp64": 136}
+# the bed read and U* written in stage 1, U*, the bed, U^n read and U^{n+1}
+# written in stage 2.  FP64 reads z (17 words, 136 B); the FP32 layout reads
+# the two per-face differences dz_x, dz_y instead of z (19 words, 76 B) --
+# the sum of the per-kernel figures above.
+STEP_BYTES = {"fp32": 76, "fp64": 136}
+NOMINAL_HBM_GBS = 8000.0
 
 
 def parse():
@@ -275,6 +278,9 @@ def measure(sw, torch, w, precision: str, steps: int, warmup: int, ws: int, cloc
                 "stage2": list(sw.tile_shapes()[shape2])}
     else:
         tune = s.autotune(reps=3, cache=os.path.join(ROOT, "paper_1307_4839_gb300", "_build", "autotune.json"))
+    # per-kernel device time over the timed region itself: CUDA events
+    # around each launch, on the stream the kernels run on
+    s.enable_timing(True)
     torch.cuda.synchronize()
     barrier(ws)
     e0 = torch.cuda.Event(enable_timing=True)
@@ -289,15 +295,23 @@ def measure(sw, torch, w, precision: str, steps: int, warmup: int, ws: int, cloc
     clk = clocks.stop() if clocks else None
     barrier(ws)
     ms = e0.elapsed_time(e1)
-    info = s.step(0)
-    assert info.status == 0, f"device status {info.status}"
-    # per-kernel device time, CUDA events around each launch on the same stream
-    s.enable_timing(True)
-    s.step(steps, sync=False)
     t = s.timing()
     s.enable_timing(False)
+    info = s.step(0)
+    assert info.status == 0, f"device status {info.status}"
+    # repetitions: 10 blocks of steps/10 (>= 10 steps each), best and median ms per step
+    per = max(10, steps // 10)
+    reps = []
+    for _ in range(10):
+        e0.record(stream)
+        s.step(per, sync=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        reps.append(e0.elapsed_time(e1) / per)
     d = s.diagnostics()
     d["tile"] = {k: tune[k] for k in ("stage1", "stage2", "ms_stage1", "ms_stage2") if k in tune}
+    d["reps"] = {"blocks": 10, "steps_each": per, "ms_per_step_best": min(reps),
+                 "ms_per_step_median": statistics.median(reps)}
     return ms, t, clk, d, s
 
 
@@ -597,7 +611,13 @@ def main():
                 "traffic": recorded_traffic(dom, P, diag["tile"].get(dom)) if dom != "lambda" else None,
                 "algorithmic_bytes_per_cell": BYTES[P][dom],
                 "kernel_ms": {kk: round(v, 5) for kk, v in avg.items()},
-                "step_frac_of_hbm": STEP_BYTES[P] * cells / (ms_step * 1e-3) * 1e-9 / hbm}
+                "step_frac_of_hbm": STEP_BYTES[P] * cells / (ms_step * 1e-3) * 1e-9 / hbm,
+                "step_bytes_per_cell": STEP_BYTES[P],
+                "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS,
+                "timing": "per-kernel CUDA events around every launch of the timed region"}
+    if roofline["traffic"]:
+        roofline["traffic_gbs"] = roofline["traffic"] / (avg[dom] * 1e-3) * 1e-9
+        roofline["traffic_frac"] = roofline["traffic_gbs"] / hbm
 
     variants = {}
     if not args.no_fp64 and P == "fp32":
@@ -683,7 +703,7 @@ def main():
                    "l2": f"inputs larger than L2 (working set {(9 * (w.ny + 4) * (w.nx + 8) * 4) / 1e6:.0f} MB)",
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "counted": "all interior cells, dry cells included",
-                   "tile": diag["tile"]},
+                   "tile": diag["tile"], "repetitions": diag["reps"]},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
