@@ -93,6 +93,27 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def recorded_metric(kernel: str, precision: str, tile, name: str):
+    """A figure from the committed ncu summary of this kernel (current source
+    and tile shape only), else None."""
+    if tile is None:
+        return None
+    csrc = os.path.join(ROOT, "paper_1307_4839_gb300", "csrc")
+    src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("swof_kernels.cuh", "swof_sweep.cuh"))
+    sha = hashlib.sha256(src).hexdigest()[:16]
+    f = os.path.join(ROOT, "profiles", f"k_sweep_{kernel}_{precision}_valley4096_{tile[0]}x{tile[1]}.txt")
+    if not os.path.exists(f):
+        return None
+    vals = dict(line.split(":", 1) for line in open(f) if ":" in line)
+    vals = {k.strip(): v.strip() for k, v in vals.items()}
+    if vals.get("kernel_source_sha256_16") != sha or f", {tile[0]}, {tile[1]}>" not in vals.get("kernel", ""):
+        return None
+    try:
+        return float(vals[name])
+    except Exception:
+        return None
+
+
 def bf16_peak() -> float:
     try:
         return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
@@ -632,7 +653,10 @@ def main():
                             "fp32_over_fp64": value / v64,
                             "kernel_ms": {kk: round(v, 4) for kk, v in avg64.items()},
                             "hbm_frac_algorithmic": STEP_BYTES["fp64"] * cells / (ms64 / k64 * 1e-3) * 1e-9 / hbm,
-                            "bound": "alu (FP64 pipe)", "tile": d64["tile"]}
+                            "bound": "alu (FP64 pipe)", "tile": d64["tile"],
+                            "fp64_pipe_active_pct_ncu": {
+                                st: recorded_metric(st, "fp64", d64["tile"].get(st), "FP64 pipe %")
+                                for st in ("stage1", "stage2")}}
         del s64
 
     if P == "fp32" and not args.no_wet:
