@@ -7,6 +7,7 @@
 // grid) for every member whose check fails.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -211,18 +212,65 @@ struct Scratch {
     }
 };
 
+// A member slot (dense fp32 planes h, hu, hv[, V_inf] of H x W) into a
+// context's padded state, with its time; the latched status and the wave-
+// speed words are cleared (what swof_set_state_device + set_infiltrated +
+// swof_set_time do, in one launch).
+template <typename T>
+__global__ void k_member_in(Params P, Fields<T> F, DevCtl *ctl, const float *sb, long long HW, int vinf, double t)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < HW; i += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(i / P.nx), x = (int)(i - (long long)j * P.nx);
+        const size_t o = (size_t)(j + 2) * P.pitch + (size_t)(x + P.lpad);
+        F.h[o] = (T)sb[i];
+        F.qx[o] = (T)sb[HW + i];
+        F.qy[o] = (T)sb[2 * HW + i];
+        if (vinf) F.vinf[o] = (T)sb[3 * HW + i];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->t = t;
+        ctl->status = 0;
+        ctl->lam_bits[0] = 0ull;
+        ctl->lam_bits[1] = 0ull;
+    }
+}
+
+// The context's state (and V_inf) back into the member slot.
+template <typename T>
+__global__ void k_member_out(Params P, Fields<T> F, float *sb, long long HW, int vinf)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < HW; i += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(i / P.nx), x = (int)(i - (long long)j * P.nx);
+        const size_t o = (size_t)(j + 2) * P.pitch + (size_t)(x + P.lpad);
+        sb[i] = (float)F.h[o];
+        sb[HW + i] = (float)F.qx[o];
+        sb[2 * HW + i] = (float)F.qy[o];
+        if (vinf) sb[3 * HW + i] = (float)F.vinf[o];
+    }
+}
+
 // Enqueue, on the fallback context's stream, the plain solver's advance of
 // member slot sb over the span: the context takes the member's pre-call
-// state, V_inf and time, takes `steps` steps and writes its state back.
+// state, V_inf and time, takes `steps` steps and writes its state back
+// (four launches: load, ghosts, the n-step sequence, store).
 int enqueue_fallback(swof_ctx *c, float *sb, int C, long long HW, int out_ch, double t, int steps)
 {
-    int st = swof_set_state_device(c, sb, sb + HW, sb + 2 * HW, SWOF_FP32);
-    if (!st && out_ch >= 4 && C >= 4) st = vinf_copy<true>(c, sb + 3 * HW, SWOF_FP32);
-    if (!st) st = swof_set_time(c, t);
+    const int vinf = out_ch >= 4 && C >= 4;
+    const int g = grid_for(HW);
+    if (c->prec == SWOF_FP64)
+        k_member_in<double><<<g, 256, 0, c->stream>>>(c->P, c->f64, c->ctl, sb, HW, vinf, t);
+    else
+        k_member_in<float><<<g, 256, 0, c->stream>>>(c->P, c->f32, c->ctl, sb, HW, vinf, t);
+    int st = cuerr(cudaGetLastError());
+    if (!st) st = cuerr((cudaError_t)c->L->ghosts(c->P, c->fields(), c->stream));
+    c->lam_valid = false;
     if (!st) st = swof_step(c, steps, nullptr);
-    if (!st) st = swof_get_state_device(c, sb, sb + HW, sb + 2 * HW, SWOF_FP32);
-    if (!st && out_ch >= 4 && C >= 4) st = vinf_copy<false>(c, sb + 3 * HW, SWOF_FP32);
-    return st;
+    if (st) return st;
+    if (c->prec == SWOF_FP64)
+        k_member_out<double><<<g, 256, 0, c->stream>>>(c->P, c->f64, sb, HW, vinf);
+    else
+        k_member_out<float><<<g, 256, 0, c->stream>>>(c->P, c->f32, sb, HW, vinf);
+    return cuerr(cudaGetLastError());
 }
 
 }  // namespace
@@ -339,10 +387,12 @@ int swof_surrogate_rollout(swof_unet *u, float *states, int B, double *t, const 
                     status = SWOF_ESTATE;   // no solver to fall back on: this member stops here
                     continue;
                 }
-                if (cudaStreamWaitEvent(fc->stream, ev, 0) != cudaSuccess) return SWOF_ECUDA;
+                if (std::find(used.begin(), used.end(), fc) == used.end()) {
+                    if (cudaStreamWaitEvent(fc->stream, ev, 0) != cudaSuccess) return SWOF_ECUDA;
+                    used.push_back(fc);
+                }
                 if ((st = enqueue_fallback(fc, states + (size_t)b * C * HW, C, HW, Co, t[b], o->fallback_steps)))
                     return st;
-                used.push_back(fc);
             }
             t[b] += o->span;
         }
