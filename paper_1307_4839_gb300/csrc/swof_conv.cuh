@@ -559,6 +559,162 @@ __global__ void __launch_bounds__(HaloCfg<NT, CB>::THREADS)
     if (warp == 1) tc05::tmem_dealloc(tmem, Cfg::TMEM_COLS);
 }
 
+
+// ---------------------------------------------------------------------------
+// Same-resolution convolutions (3x3 or 1x1) with both operands loaded by TMA.
+// A 128-pixel tile is a box of the NHWC input: a segment of one image row
+// (W a multiple of 128) or 128 / W whole rows (W dividing 128).  For each
+// 64-wide K chunk the producer issues one box per 8-channel group -- the
+// tile shifted by its tap (dx, dy), zero-filled outside the image -- which
+// lands as 128 rows of 16 bytes, one K-major core-matrix plane; and one box
+// per 8-column group of the weight rows.  No thread touches an operand.
+// Warp roles as in k_conv_halo.  K columns past the last tap (zero weights)
+// read whatever finite values the slot holds; the ring is zeroed at start.
+template <int NT>
+struct TmaCfg {
+    static constexpr int STAGES = NT >= 256 ? 4 : 6;
+    static constexpr int A_BYTES = 8 * 128 * 16;
+    static constexpr int B_BYTES = 8 * NT * 16;
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr int TC = NT < 32 ? 32 : NT;
+    static constexpr int TMEM_COLS = 2 * TC;
+    static constexpr int THREADS = 192;
+    static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 256 * 4 + (2 * STAGES + 4) * 8 + 16 + 1024;
+};
+
+template <int NT>
+__global__ void __launch_bounds__(TmaCfg<NT>::THREADS)
+    k_conv_tma(ConvArgs A, const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap wmap)
+{
+    using Cfg = TmaCfg<NT>;
+    constexpr int S = Cfg::STAGES;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *base = smem_raw + ((1024 - (reinterpret_cast<uintptr_t>(smem_raw) & 1023)) & 1023);
+    float *sbias = reinterpret_cast<float *>(base + S * Cfg::STAGE_BYTES);
+    unsigned long long *full = reinterpret_cast<unsigned long long *>(sbias + 256);
+    unsigned long long *empty = full + S;
+    unsigned long long *accf = empty + S;
+    unsigned long long *acce = accf + 2;
+    uint32_t *tmem_word = reinterpret_cast<uint32_t *>(acce + 2);
+    volatile int *abort = reinterpret_cast<volatile int *>(tmem_word + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long M = (long long)A.B * A.H * A.W;
+    const int tiles = (int)(M / 128);
+    const int n0 = blockIdx.y * NT;
+    const int nk = A.Kp / 64;
+    const int my_tiles = (int)blockIdx.x < tiles ? (tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int G = my_tiles * nk;
+    if (G == 0) return;
+    if (warp == 1) {
+        tc05::tmem_alloc(tc05::smem_u32(tmem_word), Cfg::TMEM_COLS);
+        tc05::tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int q = 0; q < S; ++q) {
+            tc05::mbar_init(tc05::smem_u32(&full[q]), 1);
+            tc05::mbar_init(tc05::smem_u32(&empty[q]), 1);
+        }
+        for (int q = 0; q < 2; ++q) {
+            tc05::mbar_init(tc05::smem_u32(&accf[q]), 1);
+            tc05::mbar_init(tc05::smem_u32(&acce[q]), 128);
+        }
+        *abort = 0;
+    }
+    for (int i = tid; i < NT; i += Cfg::THREADS) sbias[i] = A.bias ? A.bias[n0 + i] : 0.0f;
+    {
+        uint4 *z = reinterpret_cast<uint4 *>(base);
+        for (int i = tid; i < S * Cfg::STAGE_BYTES / 16; i += Cfg::THREADS) z[i] = make_uint4(0, 0, 0, 0);
+    }
+    tc05::fence_async_smem();
+    tc05::fence_before();
+    __syncthreads();
+    tc05::fence_after();
+    const uint32_t tmem = *tmem_word;
+    const uint32_t sbase = tc05::smem_u32(base);
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            const int taps = A.ks * A.ks, half = A.ks >> 1;
+            const int rows = A.W >= 128 ? 1 : 128 / A.W;          // image rows per tile
+            const int segs = A.W >= 128 ? A.W / 128 : 1;          // tiles per image row
+#pragma unroll 1
+            for (int g = 0; g < G; ++g) {
+                const int slot = g % S;
+                if (!conv_wait(tc05::smem_u32(&empty[slot]), (uint32_t)(((g / S) & 1) ^ 1), abort)) break;
+                const int lt = g / nk, kc = g - lt * nk;
+                const int t = (int)blockIdx.x + lt * (int)gridDim.x;
+                const int rowi = (t / segs) * rows, x0 = (t - (t / segs) * segs) * 128;
+                const int b = rowi / A.H, y0 = rowi - b * A.H;
+                const uint32_t sa = sbase + slot * Cfg::STAGE_BYTES, sb = sa + Cfg::A_BYTES;
+                const uint32_t bar = tc05::smem_u32(&full[slot]);
+                int nA = 0;
+                for (int j = 0; j < 8; ++j) nA += ((kc * 64 + 8 * j) >> A.cin_shift) < taps;
+                tc05::mbar_arrive_expect_tx(bar, (uint32_t)(nA * 128 * 16 + 8 * NT * 16));
+                for (int j = 0; j < 8; ++j) {
+                    const int k = kc * 64 + 8 * j;
+                    const int tap = k >> A.cin_shift, c = k & (A.cin - 1);
+                    if (tap >= taps) continue;
+                    const int ty = A.ks == 3 ? (tap * 11) >> 5 : 0;    // tap / 3 for tap < 9
+                    const int dy = ty - half, dx = tap - ty * A.ks - half;
+                    tc05::tma_load_4d(sa + j * 2048, &xmap, c, x0 + dx, y0 + dy, b, bar);
+                }
+                for (int j = 0; j < 8; ++j)
+                    tc05::tma_load_2d(sb + j * (NT * 16), &wmap, kc * 64 + 8 * j, n0, bar);
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---------------- MMA issue ----------------
+        if (lane == 0) {
+            const uint32_t idesc = tc05::idesc_bf16(128, NT);
+            bool ok = true;
+#pragma unroll 1
+            for (int lt = 0; lt < my_tiles && ok; ++lt) {
+                const int acc = lt & 1;
+                if (!conv_wait(tc05::smem_u32(&acce[acc]), (uint32_t)(((lt >> 1) & 1) ^ 1), abort)) break;
+                tc05::fence_after();
+                const uint32_t d = tmem + (uint32_t)(acc * Cfg::TC);
+#pragma unroll 1
+                for (int kc = 0; kc < nk; ++kc) {
+                    const int g = lt * nk + kc, slot = g % S;
+                    if (!conv_wait(tc05::smem_u32(&full[slot]), (uint32_t)((g / S) & 1), abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc05::fence_after();
+                    const uint32_t a0 = sbase + slot * Cfg::STAGE_BYTES, b0 = a0 + Cfg::A_BYTES;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        tc05::mma_bf16(d, tc05::sdesc(a0 + q * 2 * 2048, 2048, 128),
+                                       tc05::sdesc(b0 + q * 2 * (NT * 16), NT * 16, 128), idesc,
+                                       (kc > 0 || q > 0) ? 1u : 0u);
+                    tc05::mma_commit(tc05::smem_u32(&empty[slot]));
+                }
+                if (ok) tc05::mma_commit(tc05::smem_u32(&accf[acc]));
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue ----------------
+        const int quarter = warp & 3;
+#pragma unroll 1
+        for (int lt = 0; lt < my_tiles; ++lt) {
+            const int acc = lt & 1;
+            if (!conv_wait(tc05::smem_u32(&accf[acc]), (uint32_t)((lt >> 1) & 1), abort)) break;
+            tc05::fence_after();
+            const long long m0 = ((long long)blockIdx.x + (long long)lt * gridDim.x) * 128;
+            conv_tile_epilogue<NT>(A, tmem, acc * Cfg::TC, quarter, m0, n0, M, sbias);
+            tc05::fence_before();
+            mbar_arrive(tc05::smem_u32(&acce[acc]));
+        }
+    }
+    tc05::fence_before();
+    __syncthreads();
+    if (*abort && tid == 0 && A.err) atomicExch(A.err, 1);
+    if (warp == 1) tc05::tmem_dealloc(tmem, Cfg::TMEM_COLS);
+}
+
 }  // namespace swof
 
 namespace swof {

@@ -316,6 +316,63 @@ int conv_halo_launch(const ConvArgs &A, cudaStream_t s)
     return cudaGetLastError() == cudaSuccess ? SWOF_OK : SWOF_ECUDA;
 }
 
+// TMA maps of a same-resolution layer: the input slice (NHWC, channel
+// stride cx, offset xc0) with a 128-pixel tile box of 8 channels, and the
+// weight rows [ntot][Kp] with a box of 8 columns x NT rows.
+template <int NT>
+int conv_tma_launch(const ConvArgs &A, cudaStream_t s)
+{
+    using Cfg = TmaCfg<NT>;
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return SWOF_ECUDA;
+    CUtensorMap xmap, wmap;
+    const int bw = A.W >= 128 ? 128 : A.W, bh = A.W >= 128 ? 1 : 128 / A.W;
+    cuuint64_t xd[4] = {(cuuint64_t)A.cin, (cuuint64_t)A.W, (cuuint64_t)A.H, (cuuint64_t)A.B};
+    cuuint64_t xs[3] = {(cuuint64_t)A.cx * 2, (cuuint64_t)A.W * A.cx * 2, (cuuint64_t)A.H * A.W * A.cx * 2};
+    cuuint32_t xb[4] = {8, (cuuint32_t)bw, (cuuint32_t)bh, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    if (enc(&xmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)(A.x + A.xc0), xd, xs, xb, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return SWOF_ECUDA;
+    cuuint64_t wd[2] = {(cuuint64_t)A.Kp, (cuuint64_t)A.ntot};
+    cuuint64_t ws[1] = {(cuuint64_t)A.Kp * 2};
+    cuuint32_t wb[2] = {8, (cuuint32_t)NT};
+    if (enc(&wmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)A.w, wd, ws, wb, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+        return SWOF_ECUDA;
+    static int per_sm = 0;
+    if (!per_sm) {
+        if (cudaFuncSetAttribute(k_conv_tma<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM) !=
+            cudaSuccess)
+            return SWOF_ECUDA;
+        int n = 0, dev = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_conv_tma<NT>, Cfg::THREADS, Cfg::SMEM) != cudaSuccess ||
+            n < 1)
+            n = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        per_sm = n * (sms > 0 ? sms : 152);
+    }
+    const long long tiles = (long long)A.B * A.H * A.W / 128;
+    const long long gy = A.ntot / NT;
+    long long gx = (per_sm + gy - 1) / gy;
+    if (gx > tiles) gx = tiles;
+    if (gx < 1) gx = 1;
+    k_conv_tma<NT><<<dim3((unsigned)gx, (unsigned)gy), Cfg::THREADS, Cfg::SMEM, s>>>(A, xmap, wmap);
+    return cudaGetLastError() == cudaSuccess ? SWOF_OK : SWOF_ECUDA;
+}
+
+// Same-resolution layers whose 128-pixel tiles are boxes of the image (a
+// segment of one row, or whole rows) take the TMA-operand kernel.
+bool tma_ok(const ConvArgs &A)
+{
+    const bool box = (A.W % 128 == 0) || (128 % A.W == 0 && A.H % (128 / A.W) == 0);
+    return A.gather == GATHER_SAME && (A.ks == 1 || A.ks == 3) && box && ((A.xc0 * 2) % 16 == 0) &&
+           ((A.cx * 2) % 16 == 0) && A.H <= 65535 && A.Kp % 64 == 0;
+}
+
 // Channel block of the halo kernel: the widest of 64, 32, 16 (dividing cin)
 // whose halo stages fit in shared memory beside the resident weight tile;
 // 0 if none does.
@@ -371,6 +428,16 @@ int conv(ConvArgs A, cudaStream_t s)
         case 32: return conv_halo<32>(A, s);
         case 64: return conv_halo<64>(A, s);
         case 128: return conv_halo<128>(A, s);
+        default: break;
+        }
+    }
+    if (tma_ok(A)) {
+        switch (nt) {
+        case 16: return conv_tma_launch<16>(A, s);
+        case 32: return conv_tma_launch<32>(A, s);
+        case 64: return conv_tma_launch<64>(A, s);
+        case 128: return conv_tma_launch<128>(A, s);
+        case 256: return conv_tma_launch<256>(A, s);
         default: break;
         }
     }
