@@ -43,11 +43,13 @@ class OracleParams(ctypes.Structure):
                 ("h_dry", ctypes.c_double), ("dt_max", ctypes.c_double),
                 ("t_end", ctypes.c_double), ("cfl_mode", ctypes.c_int),
                 ("bc", ctypes.c_int * 4), ("friction", ctypes.c_int),
-                ("manning_n", ctypes.c_double), ("rain_rate", ctypes.c_double),
+                ("fric_coef", ctypes.c_double), ("rain_rate", ctypes.c_double),
                 ("rain_t_on", ctypes.c_double), ("rain_t_off", ctypes.c_double),
                 ("infiltration", ctypes.c_int), ("ks", ctypes.c_double),
                 ("psi", ctypes.c_double), ("dtheta", ctypes.c_double),
-                ("check_cfl", ctypes.c_int), ("dt_fixed", ctypes.c_double)]
+                ("check_cfl", ctypes.c_int), ("dt_fixed", ctypes.c_double),
+                ("order", ctypes.c_int), ("bc_h", ctypes.c_double * 4),
+                ("bc_q", ctypes.c_double * 4)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -90,6 +92,22 @@ def _declare(L):
     L.oracle_icbrt.argtypes = [ctypes.c_double]
     L.oracle_hll.argtypes = [ctypes.c_double] * 7 + [_D]
     L.oracle_threads.restype = ctypes.c_int
+    L.oracle_friction_cf.restype = ctypes.c_double
+    L.oracle_friction_cf.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
+    L.oracle_inflow_celerity.restype = ctypes.c_double
+    L.oracle_inflow_celerity.argtypes = [ctypes.c_double, ctypes.c_double]
+    L.oracle_imposed_state.argtypes = ([ctypes.c_double, ctypes.c_double, ctypes.c_int]
+                                       + [ctypes.c_double] * 5 + [_D])
+    L.oracle_track_max.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    L.oracle_get_max.argtypes = [ctypes.c_void_p, _D]
+    L.oracle_get_max.restype = ctypes.c_int
+    L.oracle_set_gauges.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                    ctypes.c_int]
+    L.oracle_set_gauges.restype = ctypes.c_int
+    L.oracle_get_gauges.argtypes = [ctypes.c_void_p, _D, ctypes.c_int]
+    L.oracle_get_gauges.restype = ctypes.c_int
+    L.oracle_d8.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.c_int,
+                            ctypes.c_float, ctypes.POINTER(ctypes.c_uint8)]
 
 
 def _ptr(a: np.ndarray):
@@ -118,6 +136,33 @@ def threads() -> int:
     return lib().oracle_threads()
 
 
+def friction_cf(law: int, g: float, coef: float) -> float:
+    """C_f of Sec. 2.1 for law 1 Manning n, 2 Strickler K, 3 Darcy-Weisbach f, 4 Chezy C."""
+    return lib().oracle_friction_cf(int(law), g, coef)
+
+
+def inflow_celerity(R: float, Q: float) -> float:
+    """Positive root c of 2c^3 + R c^2 - Q (imposed-discharge boundary state, Sec. 2.2)."""
+    return lib().oracle_inflow_celerity(R, Q)
+
+
+def imposed_state(g, h_dry, kind, hset, qset, h1, qn1, qt1) -> np.ndarray:
+    """Boundary state (h, normal q inwards, tangential q) of an imposed edge."""
+    out = np.zeros(3)
+    lib().oracle_imposed_state(g, h_dry, int(kind), hset, qset, h1, qn1, qt1, _ptr(out))
+    return out
+
+
+def d8(z, nodata: float = -np.inf) -> np.ndarray:
+    """D8 flow-direction codes (uint8, 0 = no lower neighbour) of a float32 DEM [ny][nx]."""
+    z = np.ascontiguousarray(z, dtype=np.float32)
+    ny, nx = z.shape
+    out = np.zeros((ny, nx), dtype=np.uint8)
+    lib().oracle_d8(z.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), nx, ny, float(nodata),
+                    out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+    return out
+
+
 class OracleError(RuntimeError):
     pass
 
@@ -133,7 +178,13 @@ class Oracle:
                  friction=0, manning_n=0.0, n_map=None, rain_rate=0.0,
                  rain_t_on=0.0, rain_t_off=0.0, infiltration=0, ks=0.0,
                  ks_map=None, psi=0.0, dtheta=0.0, check_cfl=0, dt_fixed=0.0,
+                 friction_coef=None, order=2, bc_h=(0.0,) * 4, bc_q=(0.0,) * 4,
                  library=None):
+        """friction: 0 none, 1 Manning, 2 Strickler, 3 Darcy-Weisbach, 4 Chezy,
+        with its coefficient in friction_coef (manning_n is the same value
+        under its older name); n_map is then a per-cell map of that
+        coefficient.  bc: 0 wall, 1 outflow, 2 imposed h (bc_h), 3 imposed
+        discharge (bc_q, into the domain), 4 both.  order 1: first order."""
         self._L = library if library is not None else lib()
         self.nx, self.ny = int(nx), int(ny)
         p = OracleParams()
@@ -141,7 +192,11 @@ class Oracle:
         p.cfl_mode = cfl_mode
         for k in range(4):
             p.bc[k] = int(bc[k])
-        p.friction, p.manning_n = int(friction), manning_n
+        p.friction = int(friction)
+        p.fric_coef = manning_n if friction_coef is None else friction_coef
+        p.order = int(order)
+        for k in range(4):
+            p.bc_h[k], p.bc_q[k] = float(bc_h[k]), float(bc_q[k])
         p.rain_rate, p.rain_t_on, p.rain_t_off = rain_rate, rain_t_on, rain_t_off
         p.infiltration, p.ks, p.psi, p.dtheta = int(infiltration), ks, psi, dtheta
         p.check_cfl, p.dt_fixed = int(check_cfl), dt_fixed
@@ -221,6 +276,31 @@ class Oracle:
         ly = ctypes.c_double()
         self._L.oracle_lambda(self._o, ctypes.byref(lx), ctypes.byref(ly))
         return lx.value, ly.value
+
+    def track_max(self, on: bool = True):
+        self._L.oracle_track_max(self._o, int(bool(on)))
+
+    def max_depth(self) -> np.ndarray:
+        out = np.empty((self.ny, self.nx))
+        if self._L.oracle_get_max(self._o, _ptr(out)) != 0:
+            raise OracleError("maximum depth not tracked")
+        return out
+
+    def set_gauges(self, cells, capacity: int):
+        ij = np.ascontiguousarray(np.asarray(cells, dtype=np.int32).reshape(-1, 2))
+        self._gauges = ij
+        st = self._L.oracle_set_gauges(self._o, ij.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                       int(ij.shape[0]), int(capacity))
+        if st != 0:
+            raise OracleError("gauge outside the grid")
+
+    def gauges(self) -> np.ndarray:
+        """Records [n][1 + 3G]: t, then h, qx, qy at each gauge."""
+        G = self._gauges.shape[0]
+        cap = 1 << 20
+        buf = np.zeros((cap, 1 + 3 * G)) if G else np.zeros((0, 1))
+        n = self._L.oracle_get_gauges(self._o, _ptr(buf), cap) if G else 0
+        return buf[:n].copy()
 
     def diag(self) -> dict:
         out = np.zeros(10)

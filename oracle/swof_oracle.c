@@ -22,6 +22,15 @@
  *   - Sec. 3.5: modified Green-Ampt infiltration.
  *   - Algorithm 1: per stage BC -> reconstruction -> hydrostatic ->
  *     flux -> scheme -> friction; then the Heun combine.
+ *   - Sec. 2.1: the two friction families, Manning-Strickler (C_f = n^2 or
+ *     1/K^2, S_f = C_f |u| u / h^{4/3}) and Darcy-Weisbach-Chezy (C_f =
+ *     f/(8g) or 1/C^2, S_f = C_f |u| u / h), each semi-implicit (Sec. 3.2).
+ *   - Sec. 2.2: boundary values through ghost cells, the missing ones from
+ *     the Riemann invariant that leaves the domain (one imposed variable, h
+ *     or q, for a fluvial boundary; both for a torrential inflow).
+ *   - Sec. 3.3: the first-order variant (no reconstruction, n_CFL = 1 is
+ *     the caller's choice) advanced by one explicit Euler stage.
+ *   - Sec. 6 (SkelGIS example): the D8 flow direction of a DEM.
  *
  * Readings where the paper is silent (each also listed in the design notes):
  *   2-D: F = (hu, hu^2 + g h^2/2, huv), G = (hv, huv, hv^2 + g h^2/2); the
@@ -35,7 +44,14 @@
  *   (A = 1, suction psi > 0: I_C = K_s (1 + (psi + h) dtheta / V_inf),
  *   everything infiltrates while V_inf = 0), then q = 0 where h <= h_dry,
  *   once per step after the Heun combine.  Walls mirror 2 ghost layers
- *   (normal discharge negated), outflow extends the edge cell.
+ *   (normal discharge negated), outflow extends the edge cell.  Imposed
+ *   boundaries fill both ghost layers with one boundary state built from the
+ *   edge cell; the tangential velocity is the edge cell's (imposed h or q) or
+ *   zero (both imposed); no switching by flow regime.  First order: face
+ *   values are the cell values, one Euler stage per step, the rain /
+ *   infiltration / clean-up sequence unchanged.  Gauges record t, h, qx, qy
+ *   after every step; the maximum depth is a running max over the states
+ *   after each step (starting from the state when tracking is switched on).
  *
  * Rounding order: the expressions below are the ones the CUDA FP64 path must
  * reproduce bit for bit; each is written out plainly (compile with
@@ -52,14 +68,18 @@
 typedef struct {
     double g, cfl, h_dry, dt_max, t_end;
     int cfl_mode;          /* 0: n_CFL/(lx/dx+ly/dy), 1: n_CFL*min(dx/lx, dy/ly) */
-    int bc[4];             /* W, E, S, N: 0 wall, 1 outflow */
-    int friction;          /* 0 none, 1 Manning */
-    double manning_n;
+    int bc[4];             /* W, E, S, N: 0 wall, 1 outflow, 2 imposed h,
+                              3 imposed discharge, 4 imposed h and discharge */
+    int friction;          /* 0 none, 1 Manning, 2 Strickler, 3 Darcy-Weisbach, 4 Chezy */
+    double fric_coef;      /* n, K, f or C of that law */
     double rain_rate, rain_t_on, rain_t_off;
     int infiltration;
     double ks, psi, dtheta;
     int check_cfl;         /* count dt > CFL bound of U* */
     double dt_fixed;       /* > 0: fixed dt; a CFL violation is an error */
+    int order;             /* 1: first order (Euler); else second order (Heun) */
+    double bc_h[4];        /* imposed depth per edge [m] */
+    double bc_q[4];        /* imposed discharge per unit width, into the domain [m^2/s] */
 } oracle_params;
 
 typedef struct {
@@ -67,7 +87,8 @@ typedef struct {
     double dx, dy;
     oracle_params p;
     double *z, *h, *qx, *qy, *h1, *qx1, *qy1, *h2, *qx2, *qy2;
-    double *n2;      /* per-cell n^2 (interior), or NULL */
+    double *cf;      /* per-cell friction factor C_f (interior), or NULL */
+    double p_cf;     /* C_f from the scalar coefficient */
     double *ksmap;   /* per-cell K_s (interior), or NULL */
     double *vinf;    /* infiltrated depth (interior) */
     double *u, *v;   /* cell velocities (padded) */
@@ -79,6 +100,9 @@ typedef struct {
     double t, last_dt, rain_in, infiltrated, outflow;
     long steps, cfl_viol;
     double *dt_seq; int dt_seq_n, dt_seq_pos;
+    double *hmax;    /* running max depth (interior), or NULL */
+    int *gauge_ij; int n_gauges, gauge_cap, gauge_n;
+    double *gauge_rec;   /* [gauge_cap][1 + 3 n_gauges]: t, (h, qx, qy) per gauge */
 } oracle_t;
 
 #define IDX(o, i, j) ((size_t)((j) + 2) * (size_t)(o)->px + (size_t)((i) + 2))
@@ -191,6 +215,56 @@ static void fill_ghost_y(oracle_t *o, double *a, double wall_sign)
     }
 }
 
+/* Speed of the boundary state for an imposed discharge (Sec. 2.2): with
+ * c = sqrt(g h), the invariant w - 2c carried out of the domain (w = normal
+ * velocity, positive inwards) and w = q / h give q g / c^2 - 2c = R, i.e.
+ * p(c) = 2c^3 + R c^2 - q g = 0.  For q g = Q > 0 there is one positive
+ * root, p is increasing and convex to its right, and c0 = (max(-R, 0) +
+ * (Q/2)^{1/3}) lies to its right; Newton's iteration from there decreases
+ * monotonically to it and stops when an update no longer decreases c. */
+double oracle_inflow_celerity(double R, double Q)
+{
+    if (!(Q > 0.0)) return R < 0.0 ? -0.5 * R : 0.0;
+    double a = R < 0.0 ? -R : 0.0;
+    double x = 0.5 * Q;
+    double y = oracle_icbrt(x);             /* x^{-1/3} */
+    double c = (a + x * y * y) * 1.0625;    /* above the root */
+    for (int it = 0; it < 64; ++it) {
+        double p = (2.0 * c + R) * (c * c) - Q;
+        double dp = (6.0 * c + 2.0 * R) * c;
+        double cn = c - p / dp;
+        if (!(cn < c)) break;
+        c = cn;
+    }
+    return c;
+}
+
+/* Boundary state of an imposed edge from its edge cell (depth h1, normal
+ * discharge qn1 positive inwards, tangential discharge qt1), Sec. 2.2.  The
+ * outgoing Riemann invariant R = w1 - 2 sqrt(g h1) is kept; the imposed
+ * variable replaces the incoming one. */
+void oracle_imposed_state(double g, double h_dry, int type, double hset, double qset,
+                          double h1, double qn1, double qt1, double out[3])
+{
+    double w1 = 0.0, t1 = 0.0;
+    if (h1 > h_dry) {
+        double r = 1.0 / h1;
+        w1 = qn1 * r;
+        t1 = qt1 * r;
+    }
+    double R = w1 - 2.0 * sqrt(g * h1);
+    if (type == 4) {                    /* torrential inflow: h and q imposed */
+        out[0] = hset; out[1] = qset; out[2] = 0.0;
+    } else if (type == 2) {             /* fluvial, h imposed */
+        double w = R + 2.0 * sqrt(g * hset);
+        out[0] = hset; out[1] = hset * w; out[2] = hset * t1;
+    } else {                            /* fluvial, discharge imposed */
+        double c = oracle_inflow_celerity(R, qset * g);
+        double h = (c * c) / g;
+        out[0] = h; out[1] = qset; out[2] = h * t1;
+    }
+}
+
 static void boundary_conditions(oracle_t *o, double *h, double *qx, double *qy)
 {
     fill_ghost_x(o, h, 1.0);
@@ -199,6 +273,32 @@ static void boundary_conditions(oracle_t *o, double *h, double *qx, double *qy)
     fill_ghost_y(o, h, 1.0);
     fill_ghost_y(o, qx, 1.0);
     fill_ghost_y(o, qy, -1.0);
+    /* imposed edges: both ghost layers hold the boundary state of the edge
+     * cell; sides W, E, S, N have inward normals +x, -x, +y, -y */
+    for (int side = 0; side < 4; ++side) {
+        int type = o->p.bc[side];
+        if (type < 2) continue;
+        int along = side < 2 ? o->ny : o->nx;
+        for (int k = 0; k < along; ++k) {
+            int i = side == 0 ? 0 : side == 1 ? o->nx - 1 : k;
+            int j = side == 2 ? 0 : side == 3 ? o->ny - 1 : k;
+            size_t c = IDX(o, i, j);
+            double sgn = (side == 1 || side == 3) ? -1.0 : 1.0;
+            double qn = side < 2 ? sgn * qx[c] : sgn * qy[c];
+            double qt = side < 2 ? qy[c] : qx[c];
+            double b[3];
+            oracle_imposed_state(o->p.g, o->p.h_dry, type, o->p.bc_h[side], o->p.bc_q[side],
+                                 h[c], qn, qt, b);
+            for (int l = 1; l <= 2; ++l) {
+                int gi = side == 0 ? -l : side == 1 ? o->nx - 1 + l : i;
+                int gj = side == 2 ? -l : side == 3 ? o->ny - 1 + l : j;
+                size_t gc = IDX(o, gi, gj);
+                h[gc] = b[0];
+                if (side < 2) { qx[gc] = sgn * b[1]; qy[gc] = b[2]; }
+                else          { qy[gc] = sgn * b[1]; qx[gc] = b[2]; }
+            }
+        }
+    }
 }
 
 /* ---------------- the steps of Algorithm 1 ---------------- */
@@ -282,6 +382,29 @@ static void second_order_reconstruction(oracle_t *o, const double *h)
         }
 }
 
+/* First order (Sec. 3.3, n_CFL = 1): the face values are the cell values,
+ * so z_- = z_+ = z_i and the centred term Fc vanishes. */
+static void first_order_reconstruction(oracle_t *o, const double *h)
+{
+    int nx = o->nx, ny = o->ny;
+    const double *z = o->z;
+#pragma omp parallel for schedule(static)
+    for (int j = -1; j <= ny; ++j)
+        for (int i = -1; i <= nx; ++i) {
+            size_t c = IDX(o, i, j);
+            o->xhm[c] = o->xhp[c] = o->yhm[c] = o->yhp[c] = h[c];
+            o->xzm[c] = o->xzp[c] = o->yzm[c] = o->yzp[c] = z[c];
+            o->xum[c] = o->xup[c] = o->yum[c] = o->yup[c] = o->u[c];
+            o->xvm[c] = o->xvp[c] = o->yvm[c] = o->yvp[c] = o->v[c];
+        }
+}
+
+static void reconstruction(oracle_t *o, const double *h)
+{
+    if (o->p.order == 1) first_order_reconstruction(o, h);
+    else second_order_reconstruction(o, h);
+}
+
 /* Hydrostatic reconstruction (Sec. 3.1) + HLL (Sec. 3.3) + the
  * well-balancing corrections S_L, S_R for one face between cell a (left,
  * its plus side) and cell b (right, its minus side). */
@@ -346,12 +469,20 @@ static void scheme_and_friction(oracle_t *o, const double *h, const double *qx, 
             double qys = qy[c] - dtdx * (o->fx3[c] - o->fx3[w])
                                - dtdy * ((o->fy2l[c] - o->fy2r[s]) + fcy);
             if (hs > hdry) {
-                if (o->p.friction == 1) {
-                    double n2 = o->n2 ? o->n2[(size_t)j * nx + i] : o->p.manning_n * o->p.manning_n;
+                if (o->p.friction != 0) {
+                    /* q = q* / (1 + dt g C_f |u^s| / h*^p): p = 4/3 for the
+                     * Manning-Strickler family, 1 for Darcy-Weisbach-Chezy
+                     * (whose g C_f |u| / h is the paper's (f/8)|q|/(h h*)) */
+                    double cf = o->cf ? o->cf[(size_t)j * nx + i] : o->p_cf;
                     double speed = sqrt(o->u[c] * o->u[c] + o->v[c] * o->v[c]);
-                    double y = oracle_icbrt(hs);          /* h*^{-1/3} */
-                    double hinv43 = (y * y) * (y * y);    /* h*^{-4/3} */
-                    double den = 1.0 + (dt * g * n2) * speed * hinv43;
+                    double hinv;
+                    if (o->p.friction <= 2) {
+                        double y = oracle_icbrt(hs);      /* h*^{-1/3} */
+                        hinv = (y * y) * (y * y);         /* h*^{-4/3} */
+                    } else {
+                        hinv = 1.0 / hs;
+                    }
+                    double den = 1.0 + (dt * g * cf) * speed * hinv;
                     double rden = 1.0 / den;
                     qxs = qxs * rden;
                     qys = qys * rden;
@@ -383,6 +514,20 @@ static void cfl_lambda(const oracle_t *o, double *lx, double *ly)
             if (a > ax) ax = a;
             if (b > ay) ay = b;
         }
+    /* an imposed edge feeds its boundary state into the edge faces' fluxes,
+     * so the face value of the first ghost layer facing the domain counts
+     * too (both ghost layers are equal, so it is the ghost state itself) */
+    for (int j = 0; j < ny; ++j) {
+        size_t w = IDX(o, -1, j), e = IDX(o, nx, j);
+        if (o->p.bc[0] >= 2) ax = fmax(ax, fabs(o->xup[w]) + sqrt(g * o->xhp[w]));
+        if (o->p.bc[1] >= 2) ax = fmax(ax, fabs(o->xum[e]) + sqrt(g * o->xhm[e]));
+    }
+    for (int i = 0; i < nx; ++i) {
+        size_t s = IDX(o, i, -1), n = IDX(o, i, ny);
+        if (o->p.bc[2] >= 2) ay = fmax(ay, fabs(o->yvp[s]) + sqrt(g * o->yhp[s]));
+        if (o->p.bc[3] >= 2) ay = fmax(ay, fabs(o->yvm[n]) + sqrt(g * o->yhm[n]));
+    }
+    if (!isfinite(ax) || !isfinite(ay)) bad = 1;
     *lx = bad ? NAN : ax;
     *ly = bad ? NAN : ay;
 }
@@ -406,13 +551,26 @@ static double heun_stage(oracle_t *o, double *h, double *qx, double *qy,
 {
     boundary_conditions(o, h, qx, qy);
     velocities(o, h, qx, qy);
-    second_order_reconstruction(o, h);
+    reconstruction(o, h);
     numerical_flux(o);
     scheme_and_friction(o, h, qx, qy, ho, qxo, qyo, dt);
     return boundary_outflow(o);
 }
 
 /* ---------------- public API ---------------- */
+
+/* Friction factor C_f of Sec. 2.1 from the law's coefficient: Manning n^2,
+ * Strickler 1/K^2, Darcy-Weisbach f/(8g), Chezy 1/C^2. */
+double oracle_friction_cf(int law, double g, double coef)
+{
+    switch (law) {
+    case 1: return coef * coef;
+    case 2: return 1.0 / (coef * coef);
+    case 3: return coef / (8.0 * g);
+    case 4: return 1.0 / (coef * coef);
+    default: return 0.0;
+    }
+}
 
 oracle_t *oracle_create(int nx, int ny, double dx, double dy, const double *z,
                         const oracle_params *p, const double *n_map, const double *ks_map)
@@ -429,9 +587,10 @@ oracle_t *oracle_create(int nx, int ny, double dx, double dy, const double *z,
     for (size_t k = 0; k < sizeof pads / sizeof pads[0]; ++k) *pads[k] = alloc_padded(o);
     size_t ni = (size_t)nx * (size_t)ny;
     o->vinf = (double *)calloc(ni, sizeof(double));
+    o->p_cf = oracle_friction_cf(p->friction, p->g, p->fric_coef);
     if (n_map) {
-        o->n2 = (double *)malloc(ni * sizeof(double));
-        for (size_t c = 0; c < ni; ++c) o->n2[c] = n_map[c] * n_map[c];
+        o->cf = (double *)malloc(ni * sizeof(double));
+        for (size_t c = 0; c < ni; ++c) o->cf[c] = oracle_friction_cf(p->friction, p->g, n_map[c]);
     }
     if (ks_map) {
         o->ksmap = (double *)malloc(ni * sizeof(double));
@@ -451,8 +610,9 @@ void oracle_destroy(oracle_t *o)
                       o->u, o->v, o->xhm, o->xhp, o->xzm, o->xzp, o->xum, o->xup, o->xvm, o->xvp,
                       o->yhm, o->yhp, o->yzm, o->yzp, o->yum, o->yup, o->yvm, o->yvp,
                       o->fx1, o->fx2l, o->fx2r, o->fx3, o->fy1, o->fy2l, o->fy2r, o->fy3,
-                      o->vinf, o->n2, o->ksmap, o->dt_seq};
+                      o->vinf, o->cf, o->ksmap, o->dt_seq, o->hmax, o->gauge_rec};
     for (size_t k = 0; k < sizeof ptrs / sizeof ptrs[0]; ++k) free(ptrs[k]);
+    free(o->gauge_ij);
     free(o);
 }
 
@@ -505,7 +665,7 @@ static int compute_dt(oracle_t *o, double *dt_out, double *tnext)
     double lx, ly;
     boundary_conditions(o, o->h, o->qx, o->qy);
     velocities(o, o->h, o->qx, o->qy);
-    second_order_reconstruction(o, o->h);
+    reconstruction(o, o->h);
     cfl_lambda(o, &lx, &ly);
     if (!isfinite(lx) || !isfinite(ly)) return -4;
     double t = o->t, dt;
@@ -558,12 +718,17 @@ int oracle_step(oracle_t *o, int n, double *dts_out)
             double lx, ly;
             boundary_conditions(o, o->h1, o->qx1, o->qy1);
             velocities(o, o->h1, o->qx1, o->qy1);
-            second_order_reconstruction(o, o->h1);
+            reconstruction(o, o->h1);
             cfl_lambda(o, &lx, &ly);
             if (dt * (lx / o->dx + ly / o->dy) > o->p.cfl) o->cfl_viol++;
         }
-        double b2 = heun_stage(o, o->h1, o->qx1, o->qy1, o->h2, o->qx2, o->qy2, dt);
-        o->outflow += 0.5 * dt * (b1 + b2);
+        const int euler = o->p.order == 1;
+        if (euler) {
+            o->outflow += dt * b1;
+        } else {
+            double b2 = heun_stage(o, o->h1, o->qx1, o->qy1, o->h2, o->qx2, o->qy2, dt);
+            o->outflow += 0.5 * dt * (b1 + b2);
+        }
         int rain = o->p.rain_rate > 0.0 && o->t >= o->p.rain_t_on && o->t < o->p.rain_t_off;
         double rdt = dt * o->p.rain_rate;
         double infil = 0.0;
@@ -571,10 +736,15 @@ int oracle_step(oracle_t *o, int n, double *dts_out)
             double row_inf = 0.0;
             for (int i = 0; i < nx; ++i) {
                 size_t c = IDX(o, i, j), ci = (size_t)j * nx + i;
-                /* Heun combine U^{n+1} = (U^n + U**)/2 */
-                double h = 0.5 * (o->h[c] + o->h2[c]);
-                double qx = 0.5 * (o->qx[c] + o->qx2[c]);
-                double qy = 0.5 * (o->qy[c] + o->qy2[c]);
+                /* Heun combine U^{n+1} = (U^n + U**)/2; first order: U* */
+                double h, qx, qy;
+                if (euler) {
+                    h = o->h1[c]; qx = o->qx1[c]; qy = o->qy1[c];
+                } else {
+                    h = 0.5 * (o->h[c] + o->h2[c]);
+                    qx = 0.5 * (o->qx[c] + o->qx2[c]);
+                    qy = 0.5 * (o->qy[c] + o->qy2[c]);
+                }
                 if (rain) h = h + rdt;                      /* explicit rain */
                 if (o->p.infiltration) {                    /* Green-Ampt, Sec. 3.5 */
                     double vi = o->vinf[ci];
@@ -601,8 +771,99 @@ int oracle_step(oracle_t *o, int n, double *dts_out)
         o->last_dt = dt;
         o->steps++;
         if (dts_out) dts_out[s] = dt;
+        if (o->hmax)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    size_t ci = (size_t)j * nx + i;
+                    o->hmax[ci] = fmax(o->hmax[ci], o->h[IDX(o, i, j)]);
+                }
+        if (o->n_gauges > 0 && o->gauge_n < o->gauge_cap) {
+            double *r = o->gauge_rec + (size_t)o->gauge_n * (size_t)(1 + 3 * o->n_gauges);
+            r[0] = o->t;
+            for (int g = 0; g < o->n_gauges; ++g) {
+                size_t c = IDX(o, o->gauge_ij[2 * g], o->gauge_ij[2 * g + 1]);
+                r[1 + 3 * g] = o->h[c];
+                r[2 + 3 * g] = o->qx[c];
+                r[3 + 3 * g] = o->qy[c];
+            }
+            o->gauge_n++;
+        }
     }
     return 0;
+}
+
+/* Running maximum of the depth (flood-extent output): on = 1 starts it
+ * from the current state, 0 stops it. */
+void oracle_track_max(oracle_t *o, int on)
+{
+    free(o->hmax);
+    o->hmax = NULL;
+    if (!on) return;
+    o->hmax = (double *)malloc((size_t)o->nx * o->ny * sizeof(double));
+    for (int j = 0; j < o->ny; ++j)
+        for (int i = 0; i < o->nx; ++i) o->hmax[(size_t)j * o->nx + i] = o->h[IDX(o, i, j)];
+}
+
+int oracle_get_max(const oracle_t *o, double *out)
+{
+    if (!o->hmax) return -10;
+    memcpy(out, o->hmax, (size_t)o->nx * o->ny * sizeof(double));
+    return 0;
+}
+
+/* Gauges at cells (i, j) = ij[2g], ij[2g+1]; up to cap records of
+ * t, then (h, qx, qy) per gauge, one after every step. */
+int oracle_set_gauges(oracle_t *o, const int *ij, int n, int cap)
+{
+    free(o->gauge_ij);
+    free(o->gauge_rec);
+    o->gauge_ij = NULL; o->gauge_rec = NULL;
+    o->n_gauges = 0; o->gauge_cap = 0; o->gauge_n = 0;
+    if (n <= 0) return 0;
+    for (int g = 0; g < n; ++g)
+        if (ij[2 * g] < 0 || ij[2 * g] >= o->nx || ij[2 * g + 1] < 0 || ij[2 * g + 1] >= o->ny) return -1;
+    o->gauge_ij = (int *)malloc((size_t)2 * n * sizeof(int));
+    memcpy(o->gauge_ij, ij, (size_t)2 * n * sizeof(int));
+    o->gauge_rec = (double *)calloc((size_t)cap * (1 + 3 * (size_t)n), sizeof(double));
+    o->n_gauges = n;
+    o->gauge_cap = cap;
+    return 0;
+}
+
+int oracle_get_gauges(const oracle_t *o, double *out, int max)
+{
+    int n = o->gauge_n < max ? o->gauge_n : max;
+    memcpy(out, o->gauge_rec, (size_t)n * (1 + 3 * (size_t)o->n_gauges) * sizeof(double));
+    return n;
+}
+
+/* D8 flow direction (Sec. 6, the SkelGIS example): for each cell, the
+ * neighbour of smallest elevation among those strictly below the cell;
+ * code k = 1..8 for the neighbours E, NE, N, NW, W, SW, S, SE (counter-
+ * clockwise from +x, rows growing northwards), 0 when no neighbour is
+ * lower.  Ties go to the first in that order.  Neighbours outside the grid
+ * and those with z <= nodata are not candidates.  Comparisons in float,
+ * the type of the DEM. */
+void oracle_d8(const float *z, int nx, int ny, float nodata, unsigned char *dir)
+{
+    static const int di[8] = {1, 1, 0, -1, -1, -1, 0, 1};
+    static const int dj[8] = {0, 1, 1, 1, 0, -1, -1, -1};
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            float best = z[(size_t)j * nx + i];
+            int code = 0;
+            for (int k = 0; k < 8; ++k) {
+                int a = i + di[k], b = j + dj[k];
+                if (a < 0 || a >= nx || b < 0 || b >= ny) continue;
+                float v = z[(size_t)b * nx + a];
+                if (v > nodata && v < best) {
+                    best = v;
+                    code = k + 1;
+                }
+            }
+            dir[(size_t)j * nx + i] = (unsigned char)code;
+        }
 }
 
 /* Pairwise sum (fixed order) of a contiguous array. */
@@ -641,7 +902,7 @@ void oracle_lambda(oracle_t *o, double *lx, double *ly)
 {
     boundary_conditions(o, o->h, o->qx, o->qy);
     velocities(o, o->h, o->qx, o->qy);
-    second_order_reconstruction(o, o->h);
+    reconstruction(o, o->h);
     cfl_lambda(o, lx, ly);
 }
 

@@ -18,6 +18,7 @@ import oracle
 import swof_inputs as si
 from mp_scheme import MPScheme
 from swe_closed_forms import dam_break_profile
+from test_oracle_extensions import _d8_brute, _textbook_hll_step
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "swof_oracle.c")
 
@@ -37,9 +38,30 @@ MUTATIONS = {
     "wall_no_negate": ("fill_ghost_x(o, qx, -1.0);", "fill_ghost_x(o, qx, 1.0);"),
     "west_index": ("double hs = h[c] - dtdx * (o->fx1[c] - o->fx1[w])", "double hs = h[c] - dtdx * (o->fx1[c] - o->fx1[s])"),
     "transverse_flux_axis": ("- dtdy * (o->fy3[c] - o->fy3[s]);", "- dtdy * (o->fx3[c] - o->fx3[s]);"),
-    "friction_h_power": ("double hinv43 = (y * y) * (y * y);", "double hinv43 = (y * y) * y;"),
-    "friction_old_speed_dropped": ("double den = 1.0 + (dt * g * n2) * speed * hinv43;", "double den = 1.0 + (dt * g * n2) * hinv43;"),
-    "heun_no_average": ("double h = 0.5 * (o->h[c] + o->h2[c]);", "double h = o->h2[c];"),
+    "friction_h_power": ("hinv = (y * y) * (y * y);", "hinv = (y * y) * y;"),
+    "friction_old_speed_dropped": ("double den = 1.0 + (dt * g * cf) * speed * hinv;", "double den = 1.0 + (dt * g * cf) * hinv;"),
+    "heun_no_average": ("h = 0.5 * (o->h[c] + o->h2[c]);", "h = o->h2[c];"),
+    "darcy_power_4_3": ("if (o->p.friction <= 2) {", "if (o->p.friction <= 3) {"),
+    "darcy_cf_without_g": ("case 3: return coef / (8.0 * g);", "case 3: return coef / 8.0;"),
+    "strickler_not_inverse": ("case 2: return 1.0 / (coef * coef);", "case 2: return coef * coef;"),
+    "chezy_not_squared": ("case 4: return 1.0 / (coef * coef);", "case 4: return 1.0 / coef;"),
+    "riemann_invariant_sign": ("double R = w1 - 2.0 * sqrt(g * h1);", "double R = w1 + 2.0 * sqrt(g * h1);"),
+    "imposed_h_velocity_sign": ("double w = R + 2.0 * sqrt(g * hset);", "double w = R - 2.0 * sqrt(g * hset);"),
+    "imposed_outward_normal": ("double sgn = (side == 1 || side == 3) ? -1.0 : 1.0;", "double sgn = 1.0;"),
+    "imposed_tangent_axis": ("double qt = side < 2 ? qy[c] : qx[c];", "double qt = side < 2 ? qx[c] : qy[c];"),
+    "inflow_newton_one_step": ("for (int it = 0; it < 64; ++it) {", "for (int it = 0; it < 1; ++it) {"),
+    "cfl_ignores_boundary_state": ("if (o->p.bc[0] >= 2) ax = fmax(ax, fabs(o->xup[w]) + sqrt(g * o->xhp[w]));", ""),
+    "first_order_runs_heun": ("const int euler = o->p.order == 1;", "const int euler = 0;"),
+    "first_order_outflow_halved": ("o->outflow += dt * b1;", "o->outflow += 0.5 * dt * b1;"),
+    "first_order_z_from_h": ("o->xzm[c] = o->xzp[c] = o->yzm[c] = o->yzp[c] = z[c];",
+                             "o->xzm[c] = o->xzp[c] = o->yzm[c] = o->yzp[c] = h[c];"),
+    "d8_tie_goes_last": ("if (v > nodata && v < best) {", "if (v > nodata && v <= best) {"),
+    "d8_nodata_ignored": ("if (v > nodata && v < best) {", "if (v < best) {"),
+    "d8_ne_nw_swapped": ("static const int di[8] = {1, 1, 0, -1, -1, -1, 0, 1};",
+                         "static const int di[8] = {1, -1, 0, 1, -1, -1, 0, 1};"),
+    "gauge_qx_qy_swapped": ("r[2 + 3 * g] = o->qx[c];", "r[2 + 3 * g] = o->qy[c];"),
+    "hmax_is_min": ("o->hmax[ci] = fmax(o->hmax[ci], o->h[IDX(o, i, j)]);",
+                    "o->hmax[ci] = fmin(o->hmax[ci], o->h[IDX(o, i, j)]);"),
     "ga_psi_sign": ("(1.0 + ((o->p.psi + h) * o->p.dtheta) / vi)", "(1.0 + ((o->p.psi - h) * o->p.dtheta) / vi)"),
     "ga_suction_dropped": ("(1.0 + ((o->p.psi + h) * o->p.dtheta) / vi)", "(1.0 + (h * o->p.dtheta) / vi)"),
     "cfl_dy_as_dx": ("double den = lx / o->dx + ly / o->dy;", "double den = lx / o->dx + ly / o->dx;"),
@@ -186,9 +208,118 @@ def pin_ponding_time(L):
     return abs(t - tp) <= 2.0 and math.isclose(o.diag()["rain_in"], R * n * n * t, rel_tol=1e-12)
 
 
+def pin_friction_laws_ode(L):
+    n, h0, qx0, qy0, T, dt = 4, 2.0, 1.2, -0.7, 10.0, 0.01
+    ok = True
+    for law, coef, p in ((2, 1.0 / 0.15, 4.0 / 3.0), (3, 1.2, 1.0), (4, 8.0, 1.0)):
+        cf = {2: 1.0 / coef ** 2, 3: coef / (8.0 * 9.81), 4: 1.0 / coef ** 2}[law]
+        o = oracle.Oracle(n, n, 1.0, 1.0, np.zeros((n, n)), bc=(1, 1, 1, 1), friction=law,
+                          friction_coef=coef, dt_fixed=dt, dt_max=1.0, library=L)
+        o.set_state(np.full((n, n), h0), np.full((n, n), qx0), np.full((n, n), qy0))
+        o.step(int(round(T / dt)))
+        q0 = math.hypot(qx0, qy0)
+        qe = q0 / (1.0 + 9.81 * cf / h0 ** (p + 1.0) * q0 * T)
+        _, qx, qy = o.state()
+        ok &= abs(math.hypot(qx[0, 0], qy[0, 0]) / qe - 1.0) < 3e-4
+    return ok
+
+
+def pin_imposed_uniform_channels(L):
+    h0, q0, qt0, n, w = 1.0, 0.5, 0.2, 16, 3
+    ok = True
+    for up, down, sgn in ((0, 1, 1.0), (1, 0, -1.0)):
+        bc, bh, bq = [0, 0, 1, 1], [0.0] * 4, [0.0] * 4
+        bc[up], bc[down], bq[up], bh[down] = 3, 2, q0, h0
+        o = oracle.Oracle(n, w, 1.0, 1.0, np.zeros((w, n)), bc=bc, bc_h=bh, bc_q=bq, dt_max=1.0, library=L)
+        st = (np.full((w, n), h0), np.full((w, n), sgn * q0), np.full((w, n), qt0))
+        o.set_state(*st)
+        o.step(60)
+        ok &= all(np.max(np.abs(a - b)) <= 1e-14 for a, b in zip(o.state(), st))
+    o = oracle.Oracle(w, n, 1.0, 1.0, np.zeros((n, w)), bc=(1, 1, 3, 2), bc_q=(0, 0, q0, 0),
+                      bc_h=(0, 0, 0, h0), dt_max=1.0, library=L)
+    st = (np.full((n, w), h0), np.full((n, w), qt0), np.full((n, w), q0))
+    o.set_state(*st)
+    o.step(60)
+    ok &= all(np.max(np.abs(a - b)) <= 1e-14 for a, b in zip(o.state(), st))
+    return ok
+
+
+def pin_torrential_fill(L):
+    nx, ny = 16, 3
+    o = oracle.Oracle(nx, ny, 1.0, 1.0, np.zeros((ny, nx)), bc=(4, 1, 0, 0), bc_h=(0.5, 0, 0, 0),
+                      bc_q=(5.0, 0, 0, 0), dt_max=1.0, library=L)
+    o.set_state(np.zeros((ny, nx)), np.zeros((ny, nx)), np.zeros((ny, nx)))
+    o.step(200)
+    h, qx, _ = o.state()
+    return bool(np.max(np.abs(h - 0.5)) <= 1e-12 and np.max(np.abs(qx - 5.0)) <= 1e-11)
+
+
+def pin_first_order_textbook(L):
+    rng = np.random.default_rng(0)
+    n, ny, dx = 12, 3, 0.7
+    h = 0.5 + rng.random(n)
+    q = 0.8 * rng.standard_normal(n)
+    o = oracle.Oracle(n, ny, dx, 1.0, np.zeros((ny, n)), order=1, cfl=1.0, bc=(1, 1, 0, 0),
+                      dt_max=10.0, library=L)
+    o.set_state(np.tile(h, (ny, 1)), np.tile(q, (ny, 1)), np.zeros((ny, n)))
+    dt = o.step(1)[0]
+    H, QX, _ = o.state()
+    hn, qn = _textbook_hll_step(h, q, dx, dt)
+    return bool(np.max(np.abs(H - hn)) <= 1e-14 and np.max(np.abs(QX - qn)) <= 1e-14)
+
+
+def pin_first_order_lake_and_budget(L):
+    w = si.lake_at_rest(n=24, level=1.0)
+    o = oracle.Oracle(w.nx, w.ny, w.dx, w.dy, w.z, order=1, cfl=1.0, library=L)
+    o.set_state(w.h, w.qx, w.qy)
+    o.step(100)
+    h, qx, qy = o.state()
+    wet = w.h > 0
+    ok = bool(np.max(np.abs((h + w.z)[wet] - 1.0)) <= 1e-12 and np.max(np.abs(qx)) <= 1e-12)
+    r = si.random_state(16, 12, seed=2, dry_frac=0.2, vel=1.0)
+    o = oracle.Oracle(r.nx, r.ny, r.dx, r.dy, r.z, order=1, cfl=1.0, bc=(3, 1, 0, 1),
+                      bc_q=(0.4, 0, 0, 0), library=L)
+    o.set_state(r.h, r.qx, r.qy)
+    v0 = o.diag()["volume"]
+    o.step(40)
+    d = o.diag()
+    return ok and abs(d["volume"] - v0 + d["outflow"]) <= 1e-12 * v0 and d["outflow"] != 0.0
+
+
+def pin_d8_brute_force(L):
+    rng = np.random.default_rng(1)
+    z = rng.integers(0, 4, size=(7, 9)).astype(np.float32)
+    z[rng.random(z.shape) < 0.15] = -9999.0
+    ok = True
+    for nodata in (-np.inf, -9999.0):
+        out = np.zeros(z.shape, np.uint8)
+        L.oracle_d8(z.ctypes.data_as(oracle.ctypes.POINTER(oracle.ctypes.c_float)), z.shape[1], z.shape[0],
+                    float(nodata), out.ctypes.data_as(oracle.ctypes.POINTER(oracle.ctypes.c_uint8)))
+        ok &= bool(np.array_equal(out, _d8_brute(z, nodata)))
+    return ok
+
+
+def pin_gauges_and_max(L):
+    w = si.random_state(10, 8, seed=7, dry_frac=0.2, vel=1.0)
+    cells = [(0, 0), (9, 7), (4, 3)]
+    o = oracle.Oracle(w.nx, w.ny, w.dx, w.dy, w.z, library=L)
+    o.set_state(w.h, w.qx, w.qy)
+    o.track_max(True)
+    o.set_gauges(cells, 16)
+    hmax, recs = w.h.copy(), []
+    for _ in range(6):
+        o.step(1)
+        h, qx, qy = o.state()
+        hmax = np.maximum(hmax, h)
+        recs.append([o.diag()["t"]] + [v for i, j in cells for v in (h[j, i], qx[j, i], qy[j, i])])
+    return bool(np.array_equal(o.gauges(), np.array(recs)) and np.array_equal(o.max_depth(), hmax))
+
+
 BATTERY = [pin_mp_second_implementation, pin_lake_at_rest, pin_mass_and_positivity,
            pin_stoker, pin_symmetry, pin_cfl_uniform, pin_cfl_muscl_faces,
-           pin_friction_uniform, pin_ponding_time]
+           pin_friction_uniform, pin_ponding_time, pin_friction_laws_ode,
+           pin_imposed_uniform_channels, pin_torrential_fill, pin_first_order_textbook,
+           pin_first_order_lake_and_budget, pin_d8_brute_force, pin_gauges_and_max]
 
 
 def _run_battery(L):
