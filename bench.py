@@ -29,6 +29,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -68,6 +70,10 @@ def parse():
     ap.add_argument("--tile", type=int, default=-1, help="fixed tile shape (skips the autotuner)")
     ap.add_argument("--tile2", type=int, default=-1, help="fixed stage-2 tile shape (with --tile)")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-skip", action="store_true", help="skip the dry-tile-skipping variant")
+    ap.add_argument("--no-order1", action="store_true", help="skip the first-order variant")
+    ap.add_argument("--no-d8", action="store_true", help="skip the D8 flow-direction variant")
+    ap.add_argument("--d8-side", type=int, default=16384)
     ap.add_argument("--no-wet", action="store_true")
     ap.add_argument("--ens-members", type=int, default=256)
     ap.add_argument("--ens-steps", type=int, default=1000)
@@ -144,6 +150,28 @@ def recorded_traffic(kernel: str, precision: str, tile):
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def recorded_d8_traffic(n: int):
+    """DRAM bytes per launch of the D8 kernel from its committed ncu summary
+    (taken on a smaller DEM and scaled by cells, see the summary), if the
+    kernel source is unchanged since (else None)."""
+    src = open(os.path.join(ROOT, "paper_1307_4839_gb300", "csrc", "swof_d8.cu"), "rb").read()
+    sha = hashlib.sha256(src).hexdigest()[:16]
+    f = os.path.join(ROOT, "profiles", "k_d8_vec_dem.txt")
+    if not os.path.exists(f):
+        return None
+    vals = {}
+    for line in open(f):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha256_16") != sha:
+        return None
+    try:
+        return float(vals["dram_bytes_per_cell"]) * n * n
     except Exception:
         return None
 
@@ -284,12 +312,13 @@ def run_reference(args, ws, rank):
 
 
 def measure(sw, torch, w, precision: str, steps: int, warmup: int, ws: int, clocks: Clocks | None,
-            autotune: bool = True, tile: int = -1, tile2: int = -1):
+            autotune: bool = True, tile: int = -1, tile2: int = -1, over: dict | None = None,
+            skip: bool = False):
     prec = sw.FP32 if precision == "fp32" else sw.FP64
     # a dedicated (non-null) stream: the kernels and the timing events share it
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    s = sw.Solver.from_workload(w, prec, stream=stream.cuda_stream)
+    s = sw.Solver.from_workload(w, prec, stream=stream.cuda_stream, **(over or {}))
     s.step(warmup)
     if tile >= 0 or not autotune:
         shape = max(tile, 0)
@@ -299,6 +328,9 @@ def measure(sw, torch, w, precision: str, steps: int, warmup: int, ws: int, cloc
                 "stage2": list(sw.tile_shapes()[shape2])}
     else:
         tune = s.autotune(reps=3, cache=os.path.join(ROOT, "paper_1307_4839_gb300", "_build", "autotune.json"))
+    if skip:
+        s.set_dry_tile_skip(True)
+    act0 = s.tile_activity() if skip else None
     # per-kernel device time over the timed region itself: CUDA events
     # around each launch, on the stream the kernels run on
     s.enable_timing(True)
@@ -320,6 +352,7 @@ def measure(sw, torch, w, precision: str, steps: int, warmup: int, ws: int, cloc
     s.enable_timing(False)
     info = s.step(0)
     assert info.status == 0, f"device status {info.status}"
+    act1 = s.tile_activity() if skip else None
     # repetitions: 10 blocks of steps/10 (>= 10 steps each), best and median ms per step
     per = max(10, steps // 10)
     reps = []
@@ -333,7 +366,42 @@ def measure(sw, torch, w, precision: str, steps: int, warmup: int, ws: int, cloc
     d["tile"] = {k: tune[k] for k in ("stage1", "stage2", "ms_stage1", "ms_stage2") if k in tune}
     d["reps"] = {"blocks": 10, "steps_each": per, "ms_per_step_best": min(reps),
                  "ms_per_step_median": statistics.median(reps)}
+    if skip:
+        d["live_tile_fraction"] = (act1[0] - act0[0]) / max(act1[1] - act0[1], 1)
     return ms, t, clk, d, s
+
+
+def measure_d8(sw, torch, n: int, reps: int = 20):
+    """D8 flow directions (Sec. 6) of an n x n float32 DEM: 4 B read and 1 B
+    written per cell; the DEM (n^2 x 4 B) is larger than L2."""
+    import swof_inputs as si
+    z = torch.from_numpy(si.dem(n, n, seed=7, quantum=0.01)).cuda()
+    out = torch.empty((n, n), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            sw.flow_directions(z, out, stream=stream.cuda_stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            sw.flow_directions(z, out, stream=stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    hbm, _ = peaks()
+    gbs = 5.0 * n * n / (ms * 1e-3) * 1e-9
+    rec = recorded_d8_traffic(n)
+    r = {"value": n * n / (ms * 1e-3) * 1e-9, "unit": "Gcells/s", "ms_per_launch": ms, "grid": [n, n],
+         "launches": reps, "roofline": {"bound": "hbm", "kernel": "k_d8_vec", "achieved": gbs, "peak": hbm,
+                                        "unit": "GB/s", "frac": gbs / hbm, "algorithmic_bytes_per_cell": 5,
+                                        "traffic": rec},
+         "what": "float32 DEM (tilted fractal, quantised to 0.01 m) -> uint8 D8 codes, one kernel"}
+    if rec:
+        r["roofline"]["traffic_gbs"] = rec / (ms * 1e-3) * 1e-9
+    del z, out
+    return r
 
 
 def measure_ensemble(sw, torch, args, ws):
@@ -676,6 +744,44 @@ def main():
             "stage2_hbm_frac": BYTES["fp32"]["stage2"] * cells / (avgw["stage2"] * 1e-3) * 1e-9 / hbm,
             "what": "valley DEM with 0.5 m of water added to every cell"}
         del sw_
+
+    if P == "fp32" and not args.no_skip:
+        # the same workload with dry-tile skipping (all cells still counted):
+        # exact, so its state must equal the full step's after the same steps
+        mss, ts, _, ds, ss = measure(sw, torch, w, "fp32", args.steps, args.warmup, ws, None,
+                                     not args.no_autotune, args.tile, args.tile2, skip=True)
+        mss = max_over_ranks(mss, ws)
+        ks = args.steps
+        avgs = {"lambda": ts["lambda_ms"] / ks, "stage1": ts["stage1_ms"] / ks, "stage2": ts["stage2_ms"] / ks}
+        same = all(np.array_equal(a, b) for a, b in zip(ss.state(), solver.state()))
+        variants["fp32_dry_tile_skip"] = {
+            "value": ws * cells / (mss / ks * 1e-3) * 1e-9, "unit": UNIT, "ms_per_step": mss / ks, "steps": ks,
+            "over_full_step": (ms_step) / (mss / ks),
+            "live_tile_fraction": ds["live_tile_fraction"],
+            "tile": {"stage1": list(sw.tile_shapes()[4]), "stage2": list(sw.tile_shapes()[4])},
+            "kernel_ms": {kk: round(v, 5) for kk, v in avgs.items()},
+            "state_equal_to_full_step": bool(same),
+            "what": "same valley and steps; a tile whose 3x3 tile neighbourhood held no water after the last "
+                    "step (no rain, no imposed edge) is left alone; all cells counted"}
+        del ss
+
+    if P == "fp32" and not args.no_order1:
+        k1 = max(20, args.steps // 4)
+        ms1, t1, _, d1, s1 = measure(sw, torch, w, "fp32", k1, args.warmup, ws, None, not args.no_autotune,
+                                     args.tile, args.tile2, over={"order": sw.ORDER_1, "cfl": 1.0})
+        ms1 = max_over_ranks(ms1, ws)
+        avg1 = {"dt": t1["lambda_ms"] / k1, "stage": t1["stage1_ms"] / k1, "commit": t1["stage2_ms"] / k1}
+        variants["fp32_first_order"] = {
+            "value": ws * cells / (ms1 / k1 * 1e-3) * 1e-9, "unit": UNIT, "ms_per_step": ms1 / k1, "steps": k1,
+            "kernel_ms": {kk: round(v, 5) for kk, v in avg1.items()},
+            "step_bytes_per_cell": 56,
+            "step_frac_of_hbm": 56 * cells / (ms1 / k1 * 1e-3) * 1e-9 / hbm,
+            "what": "same valley, first-order variant (Sec. 3.3): no reconstruction, one Euler stage, "
+                    "n_CFL = 1; stage (32 B/cell) + step end (24 B/cell)"}
+        del s1
+
+    if not args.no_d8 and P == "fp32":
+        variants["d8"] = measure_d8(sw, torch, args.d8_side)
 
     if not args.no_ensemble and P == "fp32":
         variants["ensemble"] = measure_ensemble(sw, torch, args, ws)

@@ -5,13 +5,15 @@
  *
  * The problem (Sec. 2.1, Eq. (SW2D)): unknowns h [m], qx = hu, qy = hv
  * [m^2/s] on an nx x ny Cartesian grid of cells dx x dy, fixed topography z,
- * rain R(t), Green-Ampt infiltration I (Sec. 3.5), Manning friction
- * (Sec. 2.1), ghost-cell boundary conditions (Sec. 2.2).  One step
+ * rain R(t), Green-Ampt infiltration I (Sec. 3.5), the friction laws of
+ * Sec. 2.1, ghost-cell boundary conditions (Sec. 2.2).  One step
  * (Algorithm 1) is two Heun stages (Sec. 3.2), each: boundary conditions ->
  * MUSCL-minmod reconstruction (Sec. 3.4) -> hydrostatic reconstruction ->
  * HLL flux (Sec. 3.3) -> scheme Eq. (SW1Dscheme) in x and y -> semi-implicit
  * friction (Sec. 3.2); then the Heun average, rain and infiltration, with dt
- * from the CFL condition Eq. (cfl) on the MUSCL face values.
+ * from the CFL condition Eq. (cfl) on the MUSCL face values.  The
+ * first-order variant (Sec. 3.3) drops the reconstruction and takes one
+ * explicit Euler stage per step.
  *
  * Conventions (all entry points):
  *   - Return SWOF_OK (0) or a negative SWOF_E* code; nothing throws or exits.
@@ -59,8 +61,25 @@ extern "C" {
 #define SWOF_CFL_MIN 1         /* dt = n_CFL * min(dx/lx, dy/ly) */
 #define SWOF_BC_WALL 0         /* mirror ghosts, normal discharge negated */
 #define SWOF_BC_OUTFLOW 1      /* free outflow: edge cell extended */
+/* Imposed edges (Sec. 2.2): both ghost layers hold one boundary state made
+ * from the edge cell.  The Riemann invariant w - 2 sqrt(g h) that leaves the
+ * domain (w = normal velocity, positive inwards) is kept and the imposed
+ * value replaces the entering one (fluvial edges); a torrential inflow
+ * imposes both.  The tangential velocity is the edge cell's (H, Q) or zero
+ * (HQ).  No switching by flow regime: the caller picks the type.  The
+ * boundary state also enters the CFL speed. */
+#define SWOF_BC_IMPOSED_H 2    /* depth bc_h imposed */
+#define SWOF_BC_IMPOSED_Q 3    /* discharge per unit width bc_q >= 0 imposed (inflow) */
+#define SWOF_BC_IMPOSED_HQ 4   /* both imposed (supercritical inflow) */
+/* Friction laws (Sec. 2.1), S_f = C_f |u| u / h^p, semi-implicit (Sec. 3.2):
+ * q = q* / (1 + dt g C_f |u^s| / (h*)^p), u^s the stage input's velocity. */
 #define SWOF_FRIC_NONE 0
-#define SWOF_FRIC_MANNING 1    /* S_f = n^2 |u| u / h^{4/3}, Sec. 2.1 */
+#define SWOF_FRIC_MANNING 1    /* C_f = n^2, p = 4/3 */
+#define SWOF_FRIC_STRICKLER 2  /* C_f = 1/K^2, p = 4/3 */
+#define SWOF_FRIC_DARCY 3      /* Darcy-Weisbach, C_f = f/(8g), p = 1 */
+#define SWOF_FRIC_CHEZY 4      /* C_f = 1/C^2, p = 1 */
+#define SWOF_ORDER_2 0         /* MUSCL + Heun (n_CFL 0.5 in the paper); 2 means the same */
+#define SWOF_ORDER_1 1         /* no reconstruction, one Euler stage (n_CFL 1 in the paper) */
 
 typedef struct swof_ctx swof_ctx;
 
@@ -73,10 +92,10 @@ typedef struct swof_params {
     double t_end;          /* the last step is clamped to end here */
     int precision;         /* SWOF_FP64 | SWOF_FP32 */
     int cfl_mode;          /* SWOF_CFL_SUM | SWOF_CFL_MIN */
-    int bc[4];             /* W, E, S, N edges: SWOF_BC_WALL | SWOF_BC_OUTFLOW */
-    int friction;          /* SWOF_FRIC_NONE | SWOF_FRIC_MANNING */
-    double manning_n;      /* Manning n [s m^-1/3] when friction_map is NULL */
-    const double *friction_map;  /* per-cell n [ny][nx], host, copied; nullable */
+    int bc[4];             /* W, E, S, N edges: SWOF_BC_* */
+    int friction;          /* SWOF_FRIC_* */
+    double friction_coef;  /* the law's coefficient (n, K, f or C) when friction_map is NULL */
+    const double *friction_map;  /* per-cell coefficient [ny][nx], host, copied; nullable */
     double rain_rate;      /* uniform rain R [m/s] (Eq. (SW2D)) */
     double rain_t_on, rain_t_off;  /* rain falls for t in [on, off) */
     int infiltration;      /* 1: Green-Ampt (Sec. 3.5) */
@@ -89,6 +108,10 @@ typedef struct swof_params {
     void *stream;          /* cudaStream_t to enqueue on; NULL: an internal
                               non-blocking stream (the legacy default stream
                               is handle 0, so it cannot be selected here) */
+    int order;             /* SWOF_ORDER_2 (default) | SWOF_ORDER_1 */
+    double bc_h[4];        /* imposed depth per edge [m] (SWOF_BC_IMPOSED_H, _HQ) */
+    double bc_q[4];        /* imposed discharge per unit width into the domain
+                              [m^2/s] (SWOF_BC_IMPOSED_Q, _HQ) */
 } swof_params;
 
 typedef struct swof_step_info {
@@ -110,7 +133,8 @@ typedef struct swof_diag {
 } swof_diag;
 
 /* Fill *p with the defaults: g 9.81, cfl 0.5, h_dry 1e-6, dt_max 0.1,
- * dt_min 0, t_end 1e30, FP64, CFL_SUM, walls, no friction/rain/infiltration. */
+ * dt_min 0, t_end 1e30, FP64, CFL_SUM, second order, walls, no
+ * friction/rain/infiltration. */
 SWOF_API void swof_default_params(swof_params *p);
 
 /* Create a solver for an nx x ny grid (nx, ny >= 2) of cells dx x dy with
@@ -157,7 +181,8 @@ SWOF_API int swof_get_infiltrated_device(swof_ctx *ctx, void *vinf, int dtype);
  * later steps); resets nothing else. */
 SWOF_API int swof_set_time(swof_ctx *ctx, double t);
 
-/* Advance n full Heun steps (Algorithm 1), each with one dt from Eq. (cfl)
+/* Advance n full steps (Algorithm 1: two Heun stages; one Euler stage at
+ * first order), each with one dt from Eq. (cfl)
  * (or the replayed sequence, or dt_fixed).  Asynchronous when info is NULL;
  * with info non-NULL the call synchronises and reports t, dt, steps and the
  * latched status (also the return value). n = 0 is allowed. */
@@ -200,6 +225,51 @@ SWOF_API int swof_get_diagnostics(swof_ctx *ctx, swof_diag *d);
 #define SWOF_NOALLOC_MAX_ROWS 65536
 SWOF_API int swof_volume_noalloc(const void *h, int nx, int ny, int dtype, double dx, double dy,
                                  double *out, void *stream);
+
+/* ---- outputs along the run ---------------------------------------------
+ * Maximum water depth (flood extent): swof_track_max_depth(ctx, 1) starts a
+ * running maximum from the current depth, updated after every later step by
+ * one small pass (launched only while tracking); 0 stops it and frees it.  swof_get_max_depth
+ * copies it to a host array [ny][nx] (float64); the maximum water level is
+ * that plus z.  Synchronises.  Errors: SWOF_ESTATE when not tracking. */
+SWOF_API int swof_track_max_depth(swof_ctx *ctx, int on);
+SWOF_API int swof_get_max_depth(swof_ctx *ctx, double *hmax);
+
+/* Gauges: record, after every step, t and (h, hu, hv) at n cells given as
+ * (i, j) pairs in cells[2n] (host, copied), up to `capacity` records (later
+ * steps are not recorded).  Replaces earlier gauges; n = 0 switches them
+ * off.  swof_get_gauges copies up to max_records records of 1 + 3n doubles
+ * (t, then h, hu, hv per gauge) to host out and the number recorded to
+ * *count.  Synchronises.  Errors: SWOF_EINVAL (cell outside the grid). */
+SWOF_API int swof_set_gauges(swof_ctx *ctx, const int *cells, int n, int capacity);
+SWOF_API int swof_get_gauges(swof_ctx *ctx, double *out, int max_records, int *count);
+
+/* Dry-tile skipping (second order only): a stage tile whose cells and those
+ * of its 8 neighbour tiles all hold h = 0 exactly, with no rain falling and
+ * no imposed edge beside it, keeps U^{n+1} = U^n (every flux of the step is
+ * zero there), so both stage kernels leave it after one flag test.  The
+ * results are bit for bit those of the full step.  Switching it on selects
+ * the shallowest tile shape (64 threads x 16 rows) for both stages: a sparse
+ * wet region then spreads over many short column walks (a later
+ * swof_set_tile_shape(s) may pick another; both stages keep one shape).
+ * Every state change marks all tiles wet again.
+ * swof_get_tile_activity reports the tiles processed and the tiles offered
+ * since the last swof_set_dry_tile_skip(ctx, 1).  Synchronises.  Not in the
+ * paper: an activity mask over the GPU tiles. */
+SWOF_API int swof_set_dry_tile_skip(swof_ctx *ctx, int on);
+SWOF_API int swof_get_tile_activity(swof_ctx *ctx, long long *live_tiles, long long *tiles);
+
+/* D8 flow direction of a DEM (Sec. 6, the eight-neighbour example): for
+ * each cell the neighbour of smallest elevation among those strictly below
+ * it, as code 1..8 = E, NE, N, NW, W, SW, S, SE (counter-clockwise from +x,
+ * row j + 1 north of row j), 0 when none is lower; ties go to the first
+ * code.  Neighbours outside the grid are no candidates, nor those with
+ * z <= *nodata when nodata (a host pointer) is not NULL (0: the
+ * non-positive no-data convention).  NaN never compares lower.  z: device
+ * float [ny][nx]; dir: device uint8 [ny][nx]; both caller-owned, enqueued
+ * on stream.  Errors: SWOF_EINVAL. */
+SWOF_API int swof_flow_directions(const float *z, int nx, int ny, const float *nodata, unsigned char *dir,
+                                  void *stream);
 
 /* Device time of the last swof_step call's kernels, split per kernel
  * family (wave-speed/dt, stage 1, stage 2) in milliseconds, when timing was

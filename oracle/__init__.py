@@ -106,7 +106,7 @@ def _declare(L):
     L.oracle_set_gauges.restype = ctypes.c_int
     L.oracle_get_gauges.argtypes = [ctypes.c_void_p, _D, ctypes.c_int]
     L.oracle_get_gauges.restype = ctypes.c_int
-    L.oracle_d8.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.c_int,
+    L.oracle_d8.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                             ctypes.c_float, ctypes.POINTER(ctypes.c_uint8)]
 
 
@@ -153,12 +153,15 @@ def imposed_state(g, h_dry, kind, hset, qset, h1, qn1, qt1) -> np.ndarray:
     return out
 
 
-def d8(z, nodata: float = -np.inf) -> np.ndarray:
-    """D8 flow-direction codes (uint8, 0 = no lower neighbour) of a float32 DEM [ny][nx]."""
+def d8(z, nodata: float | None = None) -> np.ndarray:
+    """D8 flow-direction codes (uint8, 0 = no lower neighbour) of a float32
+    DEM [ny][nx]; neighbours with z <= nodata are no candidates (None: no
+    no-data value)."""
     z = np.ascontiguousarray(z, dtype=np.float32)
     ny, nx = z.shape
     out = np.zeros((ny, nx), dtype=np.uint8)
-    lib().oracle_d8(z.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), nx, ny, float(nodata),
+    lib().oracle_d8(z.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), nx, ny, int(nodata is not None),
+                    float(nodata if nodata is not None else 0.0),
                     out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
     return out
 

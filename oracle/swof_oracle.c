@@ -842,9 +842,9 @@ int oracle_get_gauges(const oracle_t *o, double *out, int max)
  * code k = 1..8 for the neighbours E, NE, N, NW, W, SW, S, SE (counter-
  * clockwise from +x, rows growing northwards), 0 when no neighbour is
  * lower.  Ties go to the first in that order.  Neighbours outside the grid
- * and those with z <= nodata are not candidates.  Comparisons in float,
- * the type of the DEM. */
-void oracle_d8(const float *z, int nx, int ny, float nodata, unsigned char *dir)
+ * are not candidates, nor (with use_nodata) those with z <= nodata.
+ * Comparisons in float, the type of the DEM. */
+void oracle_d8(const float *z, int nx, int ny, int use_nodata, float nodata, unsigned char *dir)
 {
     static const int di[8] = {1, 1, 0, -1, -1, -1, 0, 1};
     static const int dj[8] = {0, 1, 1, 1, 0, -1, -1, -1};
@@ -857,7 +857,7 @@ void oracle_d8(const float *z, int nx, int ny, float nodata, unsigned char *dir)
                 int a = i + di[k], b = j + dj[k];
                 if (a < 0 || a >= nx || b < 0 || b >= ny) continue;
                 float v = z[(size_t)b * nx + a];
-                if (v > nodata && v < best) {
+                if ((!use_nodata || v > nodata) && v < best) {
                     best = v;
                     code = k + 1;
                 }

@@ -18,14 +18,17 @@ from .build import LIB as _LIB_PATH
 from .build import build
 
 __all__ = ["build", "load", "Solver", "SwofError", "SwofParams", "SwofDiag", "SwofStepInfo",
-           "FP64", "FP32", "BC_WALL", "BC_OUTFLOW", "FRIC_NONE", "FRIC_MANNING"]
+           "FP64", "FP32", "BC_WALL", "BC_OUTFLOW", "BC_IMPOSED_H", "BC_IMPOSED_Q", "BC_IMPOSED_HQ",
+           "FRIC_NONE", "FRIC_MANNING", "FRIC_STRICKLER", "FRIC_DARCY", "FRIC_CHEZY", "ORDER_1",
+           "ORDER_2", "flow_directions"]
 
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ENEGATIVE, ECFL, EDTSEQ, ETIMEOUT, EDTUNDERFLOW, ESTATE = (
     0, -1, -2, -3, -4, -5, -6, -7, -8, -9, -10)
 FP64, FP32 = 0, 1
 CFL_SUM, CFL_MIN = 0, 1
-BC_WALL, BC_OUTFLOW = 0, 1
-FRIC_NONE, FRIC_MANNING = 0, 1
+BC_WALL, BC_OUTFLOW, BC_IMPOSED_H, BC_IMPOSED_Q, BC_IMPOSED_HQ = 0, 1, 2, 3, 4
+FRIC_NONE, FRIC_MANNING, FRIC_STRICKLER, FRIC_DARCY, FRIC_CHEZY = 0, 1, 2, 3, 4
+ORDER_2, ORDER_1 = 0, 1
 NOALLOC_MAX_ROWS = 65536
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -35,12 +38,13 @@ class SwofParams(ctypes.Structure):
     _fields_ = [("g", ctypes.c_double), ("cfl", ctypes.c_double), ("h_dry", ctypes.c_double),
                 ("dt_max", ctypes.c_double), ("dt_min", ctypes.c_double), ("t_end", ctypes.c_double),
                 ("precision", ctypes.c_int), ("cfl_mode", ctypes.c_int), ("bc", ctypes.c_int * 4),
-                ("friction", ctypes.c_int), ("manning_n", ctypes.c_double),
+                ("friction", ctypes.c_int), ("friction_coef", ctypes.c_double),
                 ("friction_map", _D), ("rain_rate", ctypes.c_double),
                 ("rain_t_on", ctypes.c_double), ("rain_t_off", ctypes.c_double),
                 ("infiltration", ctypes.c_int), ("ks", ctypes.c_double), ("ks_map", _D),
                 ("psi", ctypes.c_double), ("dtheta", ctypes.c_double), ("check_cfl", ctypes.c_int),
-                ("dt_fixed", ctypes.c_double), ("stream", ctypes.c_void_p)]
+                ("dt_fixed", ctypes.c_double), ("stream", ctypes.c_void_p), ("order", ctypes.c_int),
+                ("bc_h", ctypes.c_double * 4), ("bc_q", ctypes.c_double * 4)]
 
 
 class SwofStepInfo(ctypes.Structure):
@@ -138,6 +142,15 @@ _SIGS = {
     "swof_batch_stats": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 5 + [ctypes.c_double] * 2
                          + [ctypes.c_void_p, ctypes.c_void_p]),
     "swof_surrogate_rollout": (ctypes.c_int, [ctypes.c_void_p] * 2 + [ctypes.c_int] + [ctypes.c_void_p] * 8),
+    "swof_track_max_depth": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "swof_get_max_depth": (ctypes.c_int, [ctypes.c_void_p, _D]),
+    "swof_set_gauges": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int]),
+    "swof_get_gauges": (ctypes.c_int, [ctypes.c_void_p, _D, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "swof_set_dry_tile_skip": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "swof_get_tile_activity": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong),
+                                              ctypes.POINTER(ctypes.c_longlong)]),
+    "swof_flow_directions": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_float), ctypes.c_void_p, ctypes.c_void_p]),
     "swof_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "swof_version": (ctypes.c_char_p, []),
 }
@@ -186,9 +199,10 @@ def default_params(**kw) -> SwofParams:
     p = SwofParams()
     load().swof_default_params(ctypes.byref(p))
     for k, v in kw.items():
-        if k == "bc":
+        if k in ("bc", "bc_h", "bc_q"):
+            arr = getattr(p, k)
             for i in range(4):
-                p.bc[i] = int(v[i])
+                arr[i] = int(v[i]) if k == "bc" else float(v[i])
         else:
             setattr(p, k, v)
     return p
@@ -202,8 +216,14 @@ class Solver:
                  dt_max=0.1, dt_min=0.0, t_end=1e30, cfl_mode=CFL_SUM, bc=(0, 0, 0, 0),
                  friction=FRIC_NONE, manning_n=0.0, friction_map=None, rain_rate=0.0,
                  rain_t_on=0.0, rain_t_off=0.0, infiltration=0, ks=0.0, ks_map=None, psi=0.0,
-                 dtheta=0.0, check_cfl=0, dt_fixed=0.0, stream=None):
+                 dtheta=0.0, check_cfl=0, dt_fixed=0.0, stream=None, friction_coef=None,
+                 order=ORDER_2, bc_h=(0.0,) * 4, bc_q=(0.0,) * 4):
+        """friction: FRIC_* with its coefficient in friction_coef (manning_n
+        is the same value under its older name); friction_map is a per-cell
+        map of that coefficient.  bc: BC_* per edge W, E, S, N with bc_h /
+        bc_q for the imposed ones.  order: ORDER_2 or ORDER_1."""
         L = load()
+        coef = manning_n if friction_coef is None else friction_coef
         self.nx, self.ny, self.precision = int(nx), int(ny), int(precision)
         self._ctx = None
         keep = []
@@ -216,7 +236,8 @@ class Solver:
             keep.append(km)
         p = default_params(g=g, cfl=cfl, h_dry=h_dry, dt_max=dt_max, dt_min=dt_min, t_end=t_end,
                            precision=int(precision), cfl_mode=int(cfl_mode), bc=bc,
-                           friction=int(friction), manning_n=float(manning_n),
+                           friction=int(friction), friction_coef=float(coef),
+                           order=int(order), bc_h=bc_h, bc_q=bc_q,
                            rain_rate=float(rain_rate), rain_t_on=float(rain_t_on),
                            rain_t_off=float(rain_t_off), infiltration=int(infiltration),
                            ks=float(ks), psi=float(psi), dtheta=float(dtheta),
@@ -321,6 +342,40 @@ class Solver:
         _check(load().swof_step(self._ctx, int(n), ctypes.byref(info)), "swof_step")
         return info
 
+    def track_max_depth(self, on: bool = True):
+        _check(load().swof_track_max_depth(self._ctx, int(bool(on))), "swof_track_max_depth")
+
+    def max_depth(self) -> np.ndarray:
+        out = np.empty((self.ny, self.nx))
+        _check(load().swof_get_max_depth(self._ctx, _ptr(out)), "swof_get_max_depth")
+        return out
+
+    def set_gauges(self, cells, capacity: int):
+        ij = np.ascontiguousarray(np.asarray(cells, dtype=np.int32).reshape(-1, 2))
+        self._n_gauges = int(ij.shape[0])
+        self._gauge_cap = int(capacity)
+        _check(load().swof_set_gauges(self._ctx, ij.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                      self._n_gauges, int(capacity)), "swof_set_gauges")
+
+    def gauges(self) -> np.ndarray:
+        """Records [n][1 + 3G]: t, then h, hu, hv at each gauge."""
+        G = getattr(self, "_n_gauges", 0)
+        cap = getattr(self, "_gauge_cap", 0)
+        buf = np.zeros((max(cap, 1), 1 + 3 * G))
+        cnt = ctypes.c_int()
+        _check(load().swof_get_gauges(self._ctx, _ptr(buf), cap, ctypes.byref(cnt)), "swof_get_gauges")
+        return buf[:cnt.value].copy()
+
+    def set_dry_tile_skip(self, on: bool = True):
+        _check(load().swof_set_dry_tile_skip(self._ctx, int(bool(on))), "swof_set_dry_tile_skip")
+
+    def tile_activity(self):
+        """(tiles processed, tiles offered) since skipping was switched on."""
+        a, b = ctypes.c_longlong(), ctypes.c_longlong()
+        _check(load().swof_get_tile_activity(self._ctx, ctypes.byref(a), ctypes.byref(b)),
+               "swof_get_tile_activity")
+        return a.value, b.value
+
     def set_dt_sequence(self, dts):
         d = _f64(dts).ravel()
         _check(load().swof_set_dt_sequence(self._ctx, _ptr(d) if d.size else None, int(d.size)),
@@ -395,6 +450,25 @@ class Solver:
                 json.dump(data, f, indent=1, sort_keys=True)
             os.replace(tmp, cache)
         return dict(rec, cached=False)
+
+
+def flow_directions(z, out=None, nodata: float | None = None, stream=None):
+    """D8 flow-direction codes (uint8 torch tensor [ny][nx], 0 = no lower
+    neighbour, 1..8 = E, NE, N, NW, W, SW, S, SE) of a float32 CUDA DEM
+    tensor [ny][nx] (Sec. 6's eight-neighbour example), in one kernel;
+    neighbours at z <= nodata are no candidates (None: no no-data value)."""
+    import torch
+    if z.dtype != torch.float32 or not z.is_cuda or z.dim() != 2 or not z.is_contiguous():
+        raise ValueError("z must be a contiguous float32 CUDA tensor [ny][nx]")
+    ny, nx = z.shape
+    if out is None:
+        out = torch.empty((ny, nx), dtype=torch.uint8, device=z.device)
+    s = stream if stream is not None else torch.cuda.current_stream(z.device).cuda_stream
+    nd = None if nodata is None else ctypes.byref(ctypes.c_float(nodata))
+    _check(load().swof_flow_directions(ctypes.c_void_p(z.data_ptr()), int(nx), int(ny), nd,
+                                       ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(s)),
+           "swof_flow_directions")
+    return out
 
 
 def tile_shapes() -> list[tuple[int, int]]:

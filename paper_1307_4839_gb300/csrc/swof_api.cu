@@ -102,6 +102,18 @@ int read_ctl(swof_ctx *c, DevCtl *h)
     return cuda_err(e);
 }
 
+// Friction factor C_f of Sec. 2.1 from the law's coefficient.
+double friction_cf(int law, double g, double coef)
+{
+    switch (law) {
+    case SWOF_FRIC_MANNING: return coef * coef;
+    case SWOF_FRIC_STRICKLER: return 1.0 / (coef * coef);
+    case SWOF_FRIC_DARCY: return coef / (8.0 * g);
+    case SWOF_FRIC_CHEZY: return 1.0 / (coef * coef);
+    default: return 0.0;
+    }
+}
+
 template <typename T>
 int alloc_fields(swof_ctx *c, Fields<T> &F, const double *z, const swof_params *p)
 {
@@ -140,10 +152,10 @@ int alloc_fields(swof_ctx *c, Fields<T> &F, const double *z, const swof_params *
     }
     if (st) return st;
     if (p->friction_map) {
-        std::vector<double> n2((size_t)P.nx * P.ny);
-        for (size_t k = 0; k < n2.size(); ++k) n2[k] = p->friction_map[k] * p->friction_map[k];
-        F.n2map = dalloc<T>(c, n, &st);
-        if (!st) st = upload_interior<T>(c, F.n2map, n2.data());
+        std::vector<double> cf((size_t)P.nx * P.ny);
+        for (size_t k = 0; k < cf.size(); ++k) cf[k] = friction_cf(p->friction, p->g, p->friction_map[k]);
+        F.cfmap = dalloc<T>(c, n, &st);
+        if (!st) st = upload_interior<T>(c, F.cfmap, cf.data());
     }
     if (!st && p->ks_map) {
         F.ksmap = dalloc<T>(c, n, &st);
@@ -218,6 +230,9 @@ int update_rings(swof_ctx *c)
     c->f64.ring_rows = c->f32.ring_rows = c->d_ring_rows;
     c->f64.n_ring_cols = c->f32.n_ring_cols = (int)cols.size();
     c->f64.n_ring_rows = c->f32.n_ring_rows = (int)rows.size();
+    c->f64.ring_tw = c->f32.ring_tw = w;
+    c->f64.ring_th = c->f32.ring_th = h;
+    c->f64.ring_tgx = c->f32.ring_tgx = (P.nx + w - 1) / w;
     c->gen++;
     int st = cuda_err(e);
     return st ? st : invalidate_lambda(c);
@@ -230,11 +245,27 @@ int swof_ctx_ensure_hist(swof_ctx *c, long long more) { return ensure_hist(c, mo
 
 namespace {
 
+// One step is three launches: wave speeds + dt (the full pass after a state
+// change, else the tile-edge ring), then the two Heun stages.  First order:
+// dt (from the speeds the previous step's end left; the full pass after a
+// state change), the Euler stage, and its end (sources, ghosts, the speeds
+// for the next dt).  With gauges, one more small launch records them.
 int enqueue_steps(swof_ctx *c, int n)
 {
     void *f = c->fields();
+    const bool o1 = c->P.order == 1;
+    // first order: the dt launch merges nothing of its own (empty ring)
+    Fields<double> f64 = c->f64;
+    Fields<float> f32 = c->f32;
+    f64.n_ring_cols = f64.n_ring_rows = f32.n_ring_cols = f32.n_ring_rows = 0;
+    void *fdt = o1 ? (c->prec == SWOF_FP64 ? (void *)&f64 : (void *)&f32) : f;
     int r = 0;
     c->launches_last = 0;
+    auto first = [&]() {
+        return c->lam_valid ? c->L->lambda_ring(c->P, fdt, c->stream) : c->L->lambda(c->P, f, c->stream);
+    };
+    auto s1 = [&]() { return o1 ? c->L->stage1_o1(c->P, f, c->stream) : c->L->stage1(c->P, f, c->stream); };
+    auto s2 = [&]() { return o1 ? c->L->commit_o1(c->P, f, c->stream) : c->L->stage2(c->P, f, c->stream); };
     for (int s = 0; s < n && !r; ++s) {
         if (c->timing) {
             while ((int)c->ev.size() < c->ev_used + 4) {
@@ -243,22 +274,40 @@ int enqueue_steps(swof_ctx *c, int n)
                 c->ev.push_back(e);
             }
             cudaEventRecord(c->ev[c->ev_used + 0], c->stream);
-            r = c->lam_valid ? c->L->lambda_ring(c->P, f, c->stream) : c->L->lambda(c->P, f, c->stream);
+            r = first();
             cudaEventRecord(c->ev[c->ev_used + 1], c->stream);
-            if (!r) r = c->L->stage1(c->P, f, c->stream);
+            if (!r) r = s1();
             cudaEventRecord(c->ev[c->ev_used + 2], c->stream);
-            if (!r) r = c->L->stage2(c->P, f, c->stream);
+            if (!r) r = s2();
             cudaEventRecord(c->ev[c->ev_used + 3], c->stream);
             c->ev_used += 4;
         } else {
-            r = c->lam_valid ? c->L->lambda_ring(c->P, f, c->stream) : c->L->lambda(c->P, f, c->stream);
-            if (!r) r = c->L->stage1(c->P, f, c->stream);
-            if (!r) r = c->L->stage2(c->P, f, c->stream);
+            r = first();
+            if (!r) r = s1();
+            if (!r) r = s2();
         }
-        c->lam_valid = c->P.fuse_lambda != 0;
+        if (!r && c->hmax) {
+            r = c->L->hmax(c->P, f, c->stream);
+            c->launches_last += 1;
+        }
+        if (!r && c->n_gauges > 0) {
+            r = c->L->gauges(c->P, f, c->stream);
+            c->launches_last += 1;
+        }
+        c->lam_valid = o1 || c->P.fuse_lambda != 0;
         c->launches_last += 3;
     }
     return r ? SWOF_ECUDA : SWOF_OK;
+}
+
+// Every tile wet and processed: the state changed (or skipping starts).
+int reset_activity(swof_ctx *c)
+{
+    if (!c->d_tile_act) return SWOF_OK;
+    size_t nt = (size_t)c->nslots;
+    cudaError_t e = cudaMemsetAsync(c->d_tile_act, 1, nt, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_tile_live, 1, nt, c->stream);
+    return cuda_err(e);
 }
 
 bool all_finite(const double *a, size_t n)
@@ -296,9 +345,20 @@ int swof_create(int nx, int ny, double dx, double dy, const double *z, const swo
     if ((long long)nx * (long long)ny > (1LL << 33) || nx > (1 << 28) || ny > (1 << 25)) return SWOF_EINVAL;
     if (p->precision != SWOF_FP64 && p->precision != SWOF_FP32) return SWOF_EINVAL;
     if (p->cfl_mode != SWOF_CFL_SUM && p->cfl_mode != SWOF_CFL_MIN) return SWOF_EINVAL;
-    if (p->friction != SWOF_FRIC_NONE && p->friction != SWOF_FRIC_MANNING) return SWOF_EINVAL;
-    for (int k = 0; k < 4; ++k)
-        if (p->bc[k] != SWOF_BC_WALL && p->bc[k] != SWOF_BC_OUTFLOW) return SWOF_EINVAL;
+    if (p->friction < SWOF_FRIC_NONE || p->friction > SWOF_FRIC_CHEZY) return SWOF_EINVAL;
+    if (p->friction != SWOF_FRIC_NONE && !p->friction_map &&
+        !(std::isfinite(p->friction_coef) && p->friction_coef >= 0.0))
+        return SWOF_EINVAL;
+    if ((p->friction == SWOF_FRIC_STRICKLER || p->friction == SWOF_FRIC_CHEZY) && !p->friction_map &&
+        !(p->friction_coef > 0.0))
+        return SWOF_EINVAL;
+    if (p->order != SWOF_ORDER_1 && p->order != SWOF_ORDER_2 && p->order != 2) return SWOF_EINVAL;
+    for (int k = 0; k < 4; ++k) {
+        if (p->bc[k] < SWOF_BC_WALL || p->bc[k] > SWOF_BC_IMPOSED_HQ) return SWOF_EINVAL;
+        if (p->bc[k] >= SWOF_BC_IMPOSED_H &&
+            !(std::isfinite(p->bc_h[k]) && p->bc_h[k] >= 0.0 && std::isfinite(p->bc_q[k]) && p->bc_q[k] >= 0.0))
+            return SWOF_EINVAL;
+    }
     if (!(p->g > 0) || !(p->cfl > 0) || !(p->h_dry >= 0) || !(p->dt_max > 0) || !(p->dt_min >= 0)) return SWOF_EINVAL;
     if (p->infiltration && !(p->dtheta > 0)) return SWOF_EINVAL;
     if (p->rain_rate < 0 || !(p->dt_fixed >= 0)) return SWOF_EINVAL;
@@ -331,8 +391,15 @@ int swof_create(int nx, int ny, double dx, double dy, const double *z, const swo
     P.friction = p->friction;
     P.infiltration = p->infiltration ? 1 : 0;
     P.check_cfl = p->check_cfl ? 1 : 0;
-    for (int k = 0; k < 4; ++k) P.bc[k] = p->bc[k];
-    P.n2 = p->manning_n * p->manning_n;
+    for (int k = 0; k < 4; ++k) {
+        P.bc[k] = p->bc[k];
+        P.bc_h[k] = p->bc_h[k];
+        P.bc_q[k] = p->bc_q[k];
+        P.fbc_h[k] = (float)p->bc_h[k];
+        P.fbc_q[k] = (float)p->bc_q[k];
+    }
+    P.order = p->order == SWOF_ORDER_1 ? 1 : 2;
+    P.cf = friction_cf(p->friction, p->g, p->friction_coef);
     P.rain_rate = p->rain_rate;
     P.rain_t_on = p->rain_t_on;
     P.rain_t_off = p->rain_t_off;
@@ -343,7 +410,7 @@ int swof_create(int nx, int ny, double dx, double dy, const double *z, const swo
     P.area = dx * dy;
     P.fg = (float)P.g;
     P.fh_dry = (float)P.h_dry;
-    P.fn2 = (float)P.n2;
+    P.fcf = (float)P.cf;
     P.fpsi = (float)P.psi;
     P.fdtheta = (float)P.dtheta;
     P.fks = (float)P.ks;
@@ -393,6 +460,11 @@ void swof_destroy(swof_ctx *c)
     if (c->dt_hist) cudaFree(c->dt_hist);
     if (c->staging) cudaFree(c->staging);
     if (c->d_flag) cudaFree(c->d_flag);
+    if (c->hmax) cudaFree(c->hmax);
+    if (c->d_gauge_off) cudaFree(c->d_gauge_off);
+    if (c->d_gauge_rec) cudaFree(c->d_gauge_rec);
+    if (c->d_tile_act) cudaFree(c->d_tile_act);
+    if (c->d_tile_live) cudaFree(c->d_tile_live);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     cudaSetDevice(dev);
     delete c;
@@ -459,9 +531,10 @@ int swof_set_state(swof_ctx *c, const double *h, const double *hu, const double 
     if (flag & 1) return SWOF_ENONFINITE;
     if (flag & 2) return SWOF_ENEGATIVE;
     st = cuda_err((cudaError_t)c->L->unpack(c->P, c->fields(), s0, s1, s2, SWOF_FP64, c->stream));
-    if (!st) st = cuda_err((cudaError_t)c->L->ghosts(c->P, c->fields(), c->stream));
+    if (!st) st = cuda_err((cudaError_t)c->L->ghosts(c->P, c->fields(), 0, c->stream));
     if (!st) st = clear_status(c);
     if (!st) st = invalidate_lambda(c);
+    if (!st) st = reset_activity(c);
     return st;
 }
 
@@ -489,9 +562,10 @@ int swof_set_state_device(swof_ctx *c, const void *h, const void *hu, const void
 {
     if (!c || !h || !hu || !hv || (dtype != SWOF_FP64 && dtype != SWOF_FP32)) return SWOF_EINVAL;
     int st = cuda_err((cudaError_t)c->L->unpack(c->P, c->fields(), h, hu, hv, dtype, c->stream));
-    if (!st) st = cuda_err((cudaError_t)c->L->ghosts(c->P, c->fields(), c->stream));
+    if (!st) st = cuda_err((cudaError_t)c->L->ghosts(c->P, c->fields(), 0, c->stream));
     if (!st) st = clear_status(c);
     if (!st) st = invalidate_lambda(c);
+    if (!st) st = reset_activity(c);
     return st;
 }
 
@@ -554,8 +628,8 @@ int swof_step(swof_ctx *c, int n, swof_step_info *info)
                 c->graph_gen = c->gen;
             }
             if (cudaGraphLaunch(c->gexec, c->stream) != cudaSuccess) return SWOF_ECUDA;
-            c->launches_last = 3 * n;
-            c->lam_valid = c->P.fuse_lambda != 0;
+            c->launches_last = (3 + (c->n_gauges > 0) + (c->hmax != nullptr)) * n;
+            c->lam_valid = c->P.order == 1 || c->P.fuse_lambda != 0;
         } else {
             st = enqueue_steps(c, n);
             if (st) return st;
@@ -699,11 +773,150 @@ int swof_set_tile_shapes(swof_ctx *c, int shape1, int shape2)
 {
     if (!c || shape1 < 0 || shape1 >= swof::N_TILE_SHAPES || shape2 < 0 || shape2 >= swof::N_TILE_SHAPES)
         return SWOF_EINVAL;
+    if (c->skip_dry) shape1 = shape2;        // the tile flags need one tiling
+    if (c->skip_dry && c->P.tile_cfg2 != shape2) {
+        int st = reset_activity(c);
+        if (st) return st;
+    }
     c->P.tile_cfg = shape1;
     c->gen++;
     if (c->P.tile_cfg2 == shape2) return SWOF_OK;
     c->P.tile_cfg2 = shape2;
     return update_rings(c);
+}
+
+int swof_track_max_depth(swof_ctx *c, int on)
+{
+    if (!c) return SWOF_EINVAL;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SWOF_ECUDA;
+    if (c->hmax) cudaFree(c->hmax);
+    c->hmax = nullptr;
+    c->f64.hmax = nullptr;
+    c->f32.hmax = nullptr;
+    c->gen++;
+    if (!on) return SWOF_OK;
+    size_t bytes = padded_elems(c) * c->esize;
+    if (cudaMalloc(&c->hmax, bytes) != cudaSuccess) {
+        c->hmax = nullptr;
+        return SWOF_ENOMEM;
+    }
+    const void *h = c->prec == SWOF_FP64 ? (const void *)c->f64.h : (const void *)c->f32.h;
+    cudaError_t e = cudaMemcpyAsync(c->hmax, h, bytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (c->prec == SWOF_FP64) c->f64.hmax = (double *)c->hmax;
+    else c->f32.hmax = (float *)c->hmax;
+    return cuda_err(e);
+}
+
+int swof_get_max_depth(swof_ctx *c, double *out)
+{
+    if (!c || !out) return SWOF_EINVAL;
+    if (!c->hmax) return SWOF_ESTATE;
+    int st = ensure_staging(c);
+    if (st) return st;
+    const size_t n = (size_t)c->P.nx * c->P.ny;
+    st = cuda_err((cudaError_t)c->L->pack1(c->P, c->hmax, c->staging, c->stream));
+    if (st) return st;
+    cudaError_t e = cudaMemcpyAsync(out, c->staging, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return cuda_err(e);
+}
+
+int swof_set_gauges(swof_ctx *c, const int *cells, int n, int capacity)
+{
+    if (!c || n < 0 || (n > 0 && (!cells || capacity < 1))) return SWOF_EINVAL;
+    const Params &P = c->P;
+    std::vector<long long> off((size_t)n);
+    for (int g = 0; g < n; ++g) {
+        int i = cells[2 * g], j = cells[2 * g + 1];
+        if (i < 0 || i >= P.nx || j < 0 || j >= P.ny) return SWOF_EINVAL;
+        off[g] = (long long)(j + 2) * P.pitch + (i + P.lpad);
+    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SWOF_ECUDA;
+    if (c->d_gauge_off) cudaFree(c->d_gauge_off);
+    if (c->d_gauge_rec) cudaFree(c->d_gauge_rec);
+    c->d_gauge_off = nullptr;
+    c->d_gauge_rec = nullptr;
+    c->n_gauges = 0;
+    c->gauge_cap = 0;
+    c->gen++;
+    auto wire = [&](auto &F) {
+        F.gauge_off = c->d_gauge_off;
+        F.gauge_rec = c->d_gauge_rec;
+        F.n_gauges = c->n_gauges;
+        F.gauge_cap = c->gauge_cap;
+    };
+    cudaError_t e = cudaMemsetAsync(&c->ctl->gauge_n, 0, sizeof(long long), c->stream);
+    if (n > 0 && e == cudaSuccess) {
+        if (cudaMalloc(&c->d_gauge_off, (size_t)n * sizeof(long long)) != cudaSuccess ||
+            cudaMalloc(&c->d_gauge_rec, (size_t)capacity * (1 + 3 * (size_t)n) * sizeof(double)) != cudaSuccess) {
+            wire(c->f64);
+            wire(c->f32);
+            return SWOF_ENOMEM;
+        }
+        e = cudaMemcpyAsync(c->d_gauge_off, off.data(), (size_t)n * sizeof(long long), cudaMemcpyHostToDevice,
+                            c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        c->n_gauges = n;
+        c->gauge_cap = capacity;
+    }
+    wire(c->f64);
+    wire(c->f32);
+    return cuda_err(e);
+}
+
+int swof_get_gauges(swof_ctx *c, double *out, int max_records, int *count)
+{
+    if (!c || !count || max_records < 0 || (max_records > 0 && !out)) return SWOF_EINVAL;
+    DevCtl d;
+    int st = read_ctl(c, &d);
+    if (st) return st;
+    long long n = c->n_gauges > 0 ? d.gauge_n : 0;
+    if (n > max_records) n = max_records;
+    if (n > 0 && cudaMemcpy(out, c->d_gauge_rec, (size_t)n * (1 + 3 * (size_t)c->n_gauges) * sizeof(double),
+                            cudaMemcpyDeviceToHost) != cudaSuccess)
+        return SWOF_ECUDA;
+    *count = (int)n;
+    return SWOF_OK;
+}
+
+int swof_set_dry_tile_skip(swof_ctx *c, int on)
+{
+    if (!c) return SWOF_EINVAL;
+    if (on && c->P.order == 1) return SWOF_EINVAL;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SWOF_ECUDA;
+    c->gen++;
+    if (!on) {
+        c->skip_dry = false;
+        c->f64.tile_act = c->f32.tile_act = nullptr;
+        c->f64.tile_live = c->f32.tile_live = nullptr;
+        return SWOF_OK;
+    }
+    if (!c->d_tile_act) {
+        if (cudaMalloc(&c->d_tile_act, (size_t)c->nslots) != cudaSuccess ||
+            cudaMalloc(&c->d_tile_live, (size_t)c->nslots) != cudaSuccess)
+            return SWOF_ENOMEM;
+    }
+    c->skip_dry = true;
+    c->f64.tile_act = c->f32.tile_act = c->d_tile_act;
+    c->f64.tile_live = c->f32.tile_live = c->d_tile_live;
+    long long z[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(&c->ctl->live_tiles, z, sizeof z, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return SWOF_ECUDA;
+    int st = reset_activity(c);
+    if (!st) st = swof_set_tile_shapes(c, swof::SHALLOW_SHAPE, swof::SHALLOW_SHAPE);
+    if (!st) st = cuda_err(cudaStreamSynchronize(c->stream));
+    return st;
+}
+
+int swof_get_tile_activity(swof_ctx *c, long long *live, long long *tiles)
+{
+    if (!c || !live || !tiles) return SWOF_EINVAL;
+    DevCtl d;
+    int st = read_ctl(c, &d);
+    if (st) return st;
+    *live = d.live_tiles;
+    *tiles = d.tiles;
+    return SWOF_OK;
 }
 
 }  // extern "C"
@@ -718,7 +931,10 @@ int time_stage(swof_ctx *c, const Params &P0, void *fields, int stage, int k, in
     Params P = P0;
     P.tile_cfg = k;
     P.tile_cfg2 = k;
-    auto launch = [&]() { return stage == 1 ? c->L->stage1(P, fields, c->stream) : c->L->stage2(P, fields, c->stream); };
+    auto launch = [&]() {
+        if (stage == 2) return c->L->stage2(P, fields, c->stream);
+        return P.order == 1 ? c->L->stage1_o1(P, fields, c->stream) : c->L->stage1(P, fields, c->stream);
+    };
     if (launch()) return SWOF_ECUDA;
     if (cudaEventRecord(e0, c->stream) != cudaSuccess) return SWOF_ECUDA;
     for (int r = 0; r < reps; ++r)
@@ -741,7 +957,10 @@ int autotune_t(swof_ctx *c, Fields<T> &F, int reps, double *ms, int *best)
     size_t n = padded_elems(c);
     std::vector<void *> scratch;
     int st = SWOF_OK;
-    Fields<T> G = F;
+    Fields<T> F1 = F;             // timed launches touch no output or tile flag
+    F1.hmax = nullptr;
+    F1.tile_act = F1.tile_live = nullptr;
+    Fields<T> G = F1;
     for (T **dst : {&G.h, &G.qx, &G.qy, &G.vinf}) {
         void *p = nullptr;
         if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) {
@@ -761,7 +980,7 @@ int autotune_t(swof_ctx *c, Fields<T> &F, int reps, double *ms, int *best)
         double bms = INFINITY;
         for (int k = 0; k < swof::N_TILE_SHAPES && !st; ++k) {
             double m = 0.0;
-            st = time_stage(c, P, stage == 1 ? (void *)&F : (void *)&G, stage, k, reps, e0, e1, &m);
+            st = time_stage(c, P, stage == 1 ? (void *)&F1 : (void *)&G, stage, k, reps, e0, e1, &m);
             if (st) break;
             if (ms) ms[(stage - 1) * swof::N_TILE_SHAPES + k] = m;
             if (m < bms) {

@@ -47,6 +47,14 @@ struct swof_ctx {
     // device staging of host state exchange: [3][ny][nx] doubles + a flag word
     double *staging = nullptr;
     int *d_flag = nullptr;
+    // outputs along the run: running max depth, gauges; dry-tile flags
+    void *hmax = nullptr;
+    long long *d_gauge_off = nullptr;
+    double *d_gauge_rec = nullptr;
+    int n_gauges = 0;
+    long long gauge_cap = 0;
+    unsigned char *d_tile_act = nullptr, *d_tile_live = nullptr;
+    bool skip_dry = false;
 
     void *fields() { return prec == SWOF_FP64 ? (void *)&f64 : (void *)&f32; }
 };

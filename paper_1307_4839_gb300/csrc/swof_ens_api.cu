@@ -198,6 +198,12 @@ int swof_ensemble_create(int count, const swof_scenario *specs, const swof_param
     *out = nullptr;
     if (count < 1 || !specs || !common) return SWOF_EINVAL;
     if (common->precision != SWOF_FP64 && common->precision != SWOF_FP32) return SWOF_EINVAL;
+    // the persistent kernel runs the second-order Heun step between walls /
+    // free outflow edges (its wave-speed phases know no imposed edge)
+    if (common->order == SWOF_ORDER_1) return SWOF_EINVAL;
+    for (int k = 0; k < count; ++k)
+        for (int b = 0; b < 4; ++b)
+            if (specs[k].bc[b] != SWOF_BC_WALL && specs[k].bc[b] != SWOF_BC_OUTFLOW) return SWOF_EINVAL;
     swof_ens *e = new (std::nothrow) swof_ens();
     if (!e) return SWOF_ENOMEM;
     e->n = count;
@@ -216,7 +222,7 @@ int swof_ensemble_create(int count, const swof_scenario *specs, const swof_param
             break;
         }
         swof_params p = *common;
-        p.manning_n = sc.manning_n;
+        p.friction_coef = sc.manning_n;
         p.friction = sc.manning_n > 0.0 ? SWOF_FRIC_MANNING : common->friction;
         p.rain_rate = sc.rain_rate;
         p.rain_t_on = sc.rain_t_on;

@@ -9,6 +9,8 @@ const Launch &launch_fp64()
 {
     static const Launch L = {configure_t<double>, launch_ghosts_t<double>, launch_lambda_t<double>, launch_lambda_ring_t<double>,
                              launch_stage_t<double, 1>, launch_stage_t<double, 2>,
+                             launch_stage1_o1_t<double>, launch_commit_o1_t<double>, launch_gauges_t<double>, launch_hmax_t<double>,
+                             launch_pack1_t<double>,
                              launch_reduce_t<double>, stage_slots, launch_unpack_t<double>,
                              launch_pack_t<double>};
     return L;

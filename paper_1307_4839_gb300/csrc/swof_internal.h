@@ -33,6 +33,8 @@ struct DevCtl {
     double rain_in;                   // FP64 budget: rain volume
     int dt_seq_pos, dt_seq_n;
     float fdt, fdtdx, fdtdy, frdt;    // the same four in FP32 for the FP32 kernels
+    long long gauge_n;                // gauge records written
+    long long live_tiles, tiles;      // dry-tile skipping: tiles processed / offered
 };
 
 // Scalar parameters (by value into every kernel).
@@ -41,14 +43,17 @@ struct Params {
     double dx, dy;
     double g, cfl, h_dry, dt_max, dt_min, t_end;
     int cfl_mode, friction, infiltration, check_cfl;
-    int bc[4];
-    double n2;                 // Manning n^2 (scalar)
+    int bc[4];                 // SWOF_BC_* per edge W, E, S, N
+    int order;                 // 1: first order (one Euler stage); else 2
+    double bc_h[4], bc_q[4];   // imposed edge depth / discharge
+    double cf;                 // friction factor C_f (scalar, Sec. 2.1)
     double rain_rate, rain_t_on, rain_t_off;
     double ks, psi, dtheta;
     double dt_fixed;
     double area;               // unused by the arithmetic; dx*dy
     // FP32 copies of the scalars the FP32 kernels use (no FP64 on their path)
-    float fg, fh_dry, fn2, fpsi, fdtheta, fks;
+    float fg, fh_dry, fcf, fpsi, fdtheta, fks;
+    float fbc_h[4], fbc_q[4];
     int tile_cfg;              // stage-1 kernel shape, index into the sweep shapes
     int tile_cfg2;             // stage-2 kernel shape
     int no_budget;             // 1: stage kernels leave the budget slots alone (timing runs)
@@ -61,8 +66,9 @@ struct Params {
 struct TileShape {
     int ntx, h;
 };
-constexpr int N_TILE_SHAPES = 4;
-constexpr TileShape TILE_SHAPES[N_TILE_SHAPES] = {{128, 32}, {128, 64}, {256, 32}, {64, 64}};
+constexpr int N_TILE_SHAPES = 5;
+constexpr TileShape TILE_SHAPES[N_TILE_SHAPES] = {{128, 32}, {128, 64}, {256, 32}, {64, 64}, {64, 16}};
+constexpr int SHALLOW_SHAPE = 4;      // dry-tile skipping: short column walks
 inline int max_stage_blocks(int nx, int ny)
 {
     int m = 0;
@@ -81,7 +87,7 @@ struct Fields {
     T *h1, *qx1, *qy1;         // U* (stage-1 output)
     T *z;                      // FP64 path: topography (padded)
     T *dzx, *dzy;              // FP32 path: z(i+1)-z(i), z(j+1)-z(j) per face (padded)
-    T *n2map;                  // per-cell n^2 (padded) or nullptr
+    T *cfmap;                  // per-cell friction factor C_f (padded) or nullptr
     T *ksmap;                  // per-cell K_s (padded) or nullptr
     T *vinf;                   // infiltrated depth (padded)
     double *outflow_slots;     // per-block FP64 budget accumulators
@@ -89,21 +95,34 @@ struct Fields {
     const int *ring_cols;      // columns / rows whose wave speeds stage 2 leaves out
     const int *ring_rows;      //   (tile-edge columns/rows for the current tile shape)
     int n_ring_cols, n_ring_rows;
+    int ring_tw, ring_th, ring_tgx;   // that shape's tile width, height, tiles per row
     const double *dt_seq;      // replayed dt values or nullptr
     double *dt_hist;           // dt of every step
     long long dt_hist_cap;
     DevCtl *ctl;
+    T *hmax;                   // running maximum depth (padded) or nullptr
+    const long long *gauge_off;  // padded offsets of the gauge cells
+    int n_gauges;
+    long long gauge_cap;
+    double *gauge_rec;         // [gauge_cap][1 + 3 n_gauges]
+    unsigned char *tile_act;   // dry-tile skipping: tile holds water after the step
+    unsigned char *tile_live;  //   tile processed in the current step (nullptr: off)
 };
 
 // Launchers, one set per precision (swof_fp64.cu, swof_fp32.cu).  All
 // enqueue on `stream` and return cudaError_t as int.
 struct Launch {
     int (*configure)();              // per-device kernel attributes
-    int (*ghosts)(const Params &, void *fields, void *stream);
+    int (*ghosts)(const Params &, void *fields, int which, void *stream);   // 0: U^n, 1: U*
     int (*lambda)(const Params &, void *fields, void *stream);
     int (*lambda_ring)(const Params &, void *fields, void *stream);
     int (*stage1)(const Params &, void *fields, void *stream);
     int (*stage2)(const Params &, void *fields, void *stream);
+    int (*stage1_o1)(const Params &, void *fields, void *stream);   // first-order stage
+    int (*commit_o1)(const Params &, void *fields, void *stream);   // first-order step end
+    int (*gauges)(const Params &, void *fields, void *stream);
+    int (*hmax)(const Params &, void *fields, void *stream);
+    int (*pack1)(const Params &, const void *src, double *dst, void *stream);
     int (*reduce)(const Params &, void *fields, double *out, int nslots, void *stream);
     int (*slots)(const Params &);    // number of per-block slots the stage kernels use
     // dense [ny][nx] device arrays (dtype SWOF_FP64/FP32) <-> padded state

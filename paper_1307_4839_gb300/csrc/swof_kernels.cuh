@@ -75,15 +75,15 @@ __device__ __forceinline__ float rcp(float a)
 // Scalar parameters in the kernel's precision (no conversions on the path).
 template <typename T>
 struct Scal {
-    T g, hdry, n2, psi, dtheta, ks;
+    T g, hdry, cf, psi, dtheta, ks;
 };
 template <typename T>
 __device__ __forceinline__ Scal<T> scal(const Params &P)
 {
     if constexpr (std::is_same<T, double>::value)
-        return {P.g, P.h_dry, P.n2, P.psi, P.dtheta, P.ks};
+        return {P.g, P.h_dry, P.cf, P.psi, P.dtheta, P.ks};
     else
-        return {P.fg, P.fh_dry, P.fn2, P.fpsi, P.fdtheta, P.fks};
+        return {P.fg, P.fh_dry, P.fcf, P.fpsi, P.fdtheta, P.fks};
 }
 
 // minmod limiter (Sec. 3.4): the value of smaller magnitude when a and b
@@ -158,10 +158,86 @@ __device__ __forceinline__ float icbrt(float x)
     return r;
 }
 
+// Speed c = sqrt(g h) of the boundary state of an imposed discharge
+// (Sec. 2.2): the invariant w - 2c leaving the domain (R) and w = q / h
+// give p(c) = 2c^3 + R c^2 - Q = 0 with Q = q g.  For Q > 0 the positive
+// root is unique and p is increasing and convex to its right; Newton's
+// iteration starts above it, at (max(-R, 0) + (Q/2)^{1/3}) (1 + 1/16), and
+// decreases monotonically until an update no longer decreases c.
+template <typename T>
+__device__ __forceinline__ T inflow_celerity(T R, T Q)
+{
+    if (!(Q > T(0))) return R < T(0) ? T(-0.5) * R : T(0);
+    T a = R < T(0) ? -R : T(0);
+    T x = T(0.5) * Q;
+    T y = icbrt(x);                       // x^{-1/3}
+    T c = (a + x * y * y) * T(1.0625);
+    for (int it = 0; it < 64; ++it) {
+        T p = (T(2) * c + R) * (c * c) - Q;
+        T dp = (T(6) * c + T(2) * R) * c;
+        T cn = c - p / dp;
+        if (!(cn < c)) break;
+        c = cn;
+    }
+    return c;
+}
+
+// Boundary state of an imposed edge from its edge cell (Sec. 2.2): depth
+// h1, normal discharge qn1 (positive into the domain), tangential discharge
+// qt1 -> (hb, qnb, qtb).  The invariant R = w1 - 2 sqrt(g h1) leaving the
+// domain is kept, the imposed value replaces the entering one; a torrential
+// inflow (HQ) imposes both.  Out of line: only edge cells call it, and a
+// call keeps its code out of the column sweep's register allocation.
+template <typename T>
+__device__ __noinline__ void imposed_state(const Params &P, int side, T h1, T qn1, T qt1, T &hb, T &qnb, T &qtb)
+{
+    const Scal<T> C = scal<T>(P);
+    T bh, bq;
+    if constexpr (std::is_same<T, double>::value) {
+        bh = P.bc_h[side];
+        bq = P.bc_q[side];
+    } else {
+        bh = P.fbc_h[side];
+        bq = P.fbc_q[side];
+    }
+    T w1 = T(0), t1 = T(0);
+    if (h1 > C.hdry) {
+        T r = rcp(h1);
+        w1 = qn1 * r;
+        t1 = qt1 * r;
+    }
+    T R = w1 - T(2) * sq(C.g * h1);
+    const int type = P.bc[side];
+    if (type == SWOF_BC_IMPOSED_HQ) {
+        hb = bh;
+        qnb = bq;
+        qtb = T(0);
+    } else if (type == SWOF_BC_IMPOSED_H) {
+        T w = R + T(2) * sq(C.g * bh);
+        hb = bh;
+        qnb = bh * w;
+        qtb = bh * t1;
+    } else {
+        T c = inflow_celerity(R, bq * C.g);
+        T h = (c * c) / C.g;
+        hb = h;
+        qnb = bq;
+        qtb = h * t1;
+    }
+}
+
 template <typename T>
 struct Rec {
     T hm, hp, zm, zp, unm, unp, utm, utp;
 };
+
+// First order (Sec. 3.3): the face values are the cell values (z_- = z_+,
+// so the centred term Fc vanishes).  FP32: z relative to the cell = 0.
+template <typename T>
+__device__ __forceinline__ Rec<T> rec1(T h, T z, T un, T ut)
+{
+    return {h, h, z, z, un, un, ut, ut};
+}
 
 // MUSCL reconstruction of the middle cell of (0, 1, 2) along one direction:
 // h, h + z and the velocities (normal un, transverse ut) with the
@@ -464,10 +540,22 @@ __global__ void __launch_bounds__(NT) k_lambda(Params P, Fields<T> F)
             if (gi < P.nx && gj < P.ny) {
                 int c = (tj + 1) * LX + (ti + 1);
                 V4<T> m = st[c], w = st[c - 1], e = st[c + 1], s_ = st[c - LX], n = st[c + LX];
-                T ax = cell_speed(w.x, m.x, e.x, w.y, m.y, e.y, m.w, C.hdry, C.g);
-                T ay = cell_speed(s_.x, m.x, n.x, s_.z, m.z, n.z, m.w, C.hdry, C.g);
+                T ax, ay;
+                if (P.order == 1) {           // cell values (Eq. (cfl), first order)
+                    T cm = sq(C.g * m.x);
+                    ax = ab(m.y) + cm;
+                    ay = ab(m.z) + cm;
+                } else {
+                    ax = cell_speed(w.x, m.x, e.x, w.y, m.y, e.y, m.w, C.hdry, C.g);
+                    ay = cell_speed(s_.x, m.x, n.x, s_.z, m.z, n.z, m.w, C.hdry, C.g);
+                }
                 kx = kmax(kx, speed_key(ax));
                 ky = kmax(ky, speed_key(ay));
+                // an imposed edge's boundary state (the ghost beside the edge cell)
+                if (gi == 0 && P.bc[0] >= SWOF_BC_IMPOSED_H) kx = kmax(kx, speed_key(ab(w.y) + sq(C.g * w.x)));
+                if (gi == P.nx - 1 && P.bc[1] >= SWOF_BC_IMPOSED_H) kx = kmax(kx, speed_key(ab(e.y) + sq(C.g * e.x)));
+                if (gj == 0 && P.bc[2] >= SWOF_BC_IMPOSED_H) ky = kmax(ky, speed_key(ab(s_.z) + sq(C.g * s_.x)));
+                if (gj == P.ny - 1 && P.bc[3] >= SWOF_BC_IMPOSED_H) ky = kmax(ky, speed_key(ab(n.z) + sq(C.g * n.x)));
             }
         }
         __syncthreads();
@@ -515,17 +603,34 @@ __global__ void __launch_bounds__(NT) k_lambda_ring(Params P, Fields<T> F)
     const long long nxr = (long long)F.n_ring_cols * P.ny;
     const long long total = nxr + (long long)F.n_ring_rows * P.nx;
     for (long long k = blockIdx.x * (long long)NT + threadIdx.x; k < total; k += (long long)gridDim.x * NT) {
+        if (F.tile_live) {
+            // a tile left alone in the last step holds U^{n+1} = U^n = 0:
+            // every speed there is 0
+            int gi, gj;
+            if (k < nxr) {
+                gj = (int)(k / F.n_ring_cols);
+                gi = F.ring_cols[k % F.n_ring_cols];
+            } else {
+                gj = F.ring_rows[(k - nxr) / P.nx];
+                gi = (int)((k - nxr) % P.nx);
+            }
+            if (!F.tile_live[(gj / F.ring_th) * F.ring_tgx + gi / F.ring_tw]) continue;
+        }
         if (k < nxr) {
             int gj = (int)(k / F.n_ring_cols), gi = F.ring_cols[k % F.n_ring_cols];
             V4<T> w = cell_rec(P, F, gi - 1, gj, C.hdry), m = cell_rec(P, F, gi, gj, C.hdry),
                   e = cell_rec(P, F, gi + 1, gj, C.hdry);
             kx = kmax(kx, speed_key(cell_speed(w.x, m.x, e.x, w.y, m.y, e.y, m.w, C.hdry, C.g)));
+            if (gi == 0 && P.bc[0] >= SWOF_BC_IMPOSED_H) kx = kmax(kx, speed_key(ab(w.y) + sq(C.g * w.x)));
+            if (gi == P.nx - 1 && P.bc[1] >= SWOF_BC_IMPOSED_H) kx = kmax(kx, speed_key(ab(e.y) + sq(C.g * e.x)));
         } else {
             long long q = k - nxr;
             int gj = F.ring_rows[q / P.nx], gi = (int)(q % P.nx);
             V4<T> s_ = cell_rec(P, F, gi, gj - 1, C.hdry), m = cell_rec(P, F, gi, gj, C.hdry),
                   n = cell_rec(P, F, gi, gj + 1, C.hdry);
             ky = kmax(ky, speed_key(cell_speed(s_.x, m.x, n.x, s_.z, m.z, n.z, m.w, C.hdry, C.g)));
+            if (gj == 0 && P.bc[2] >= SWOF_BC_IMPOSED_H) ky = kmax(ky, speed_key(ab(s_.z) + sq(C.g * s_.x)));
+            if (gj == P.ny - 1 && P.bc[3] >= SWOF_BC_IMPOSED_H) ky = kmax(ky, speed_key(ab(n.z) + sq(C.g * n.x)));
         }
     }
     kx = block_max(kx, red[0]);
@@ -540,25 +645,25 @@ __global__ void __launch_bounds__(NT) k_lambda_ring(Params P, Fields<T> F)
 }
 
 // ---------------------------------------------------------------------------
-// Write one interior cell of a stage output and the ghost cells that mirror
-// it (Sec. 2.2: wall = mirror with the normal discharge negated, outflow =
-// edge cell extended; two layers).
-template <typename T>
-__device__ __forceinline__ void store_cell(const Params &P, T *h, T *qx, T *qy, int gi, int gj,
-                                           T hv, T qxv, T qyv)
+// Ghost cells mirroring interior cell (gi, gj) of a state (Sec. 2.2): wall =
+// mirror image with the normal discharge negated (two layers), outflow =
+// edge cell extended, imposed = the boundary state of the edge cell in both
+// layers.  x: the W/E edges, y: the S/N edges.  IMPOSED = false writes an
+// imposed edge's ghosts as an outflow edge's (zero-filled tiles, which never
+// touch an imposed edge).
+template <typename T, bool IMPOSED = true>
+__device__ __forceinline__ void ghosts_x(const Params &P, T *h, T *qx, T *qy, int gi, int gj, T hv, T qxv, T qyv)
 {
-    size_t o = pidx(P, gi, gj);
-    h[o] = hv;
-    qx[o] = qxv;
-    qy[o] = qyv;
     if (gi < 2) {            // west
         if (P.bc[0] == SWOF_BC_WALL) {
             size_t g = pidx(P, -1 - gi, gj);
             h[g] = hv; qx[g] = -qxv; qy[g] = qyv;
         } else if (gi == 0) {
+            T gh = hv, gqx = qxv, gqy = qyv;
+            if (IMPOSED && P.bc[0] >= SWOF_BC_IMPOSED_H) imposed_state<T>(P, 0, hv, qxv, qyv, gh, gqx, gqy);
             size_t g1 = pidx(P, -1, gj), g2 = pidx(P, -2, gj);
-            h[g1] = hv; qx[g1] = qxv; qy[g1] = qyv;
-            h[g2] = hv; qx[g2] = qxv; qy[g2] = qyv;
+            h[g1] = gh; qx[g1] = gqx; qy[g1] = gqy;
+            h[g2] = gh; qx[g2] = gqx; qy[g2] = gqy;
         }
     }
     if (gi >= P.nx - 2) {    // east
@@ -566,19 +671,31 @@ __device__ __forceinline__ void store_cell(const Params &P, T *h, T *qx, T *qy, 
             size_t g = pidx(P, 2 * P.nx - 1 - gi, gj);
             h[g] = hv; qx[g] = -qxv; qy[g] = qyv;
         } else if (gi == P.nx - 1) {
+            T gh = hv, gqx = qxv, gqy = qyv;
+            if (IMPOSED && P.bc[1] >= SWOF_BC_IMPOSED_H) {
+                T qn;
+                imposed_state<T>(P, 1, hv, -qxv, qyv, gh, qn, gqy);
+                gqx = -qn;
+            }
             size_t g1 = pidx(P, P.nx, gj), g2 = pidx(P, P.nx + 1, gj);
-            h[g1] = hv; qx[g1] = qxv; qy[g1] = qyv;
-            h[g2] = hv; qx[g2] = qxv; qy[g2] = qyv;
+            h[g1] = gh; qx[g1] = gqx; qy[g1] = gqy;
+            h[g2] = gh; qx[g2] = gqx; qy[g2] = gqy;
         }
     }
+}
+template <typename T, bool IMPOSED = true>
+__device__ __forceinline__ void ghosts_y(const Params &P, T *h, T *qx, T *qy, int gi, int gj, T hv, T qxv, T qyv)
+{
     if (gj < 2) {            // south
         if (P.bc[2] == SWOF_BC_WALL) {
             size_t g = pidx(P, gi, -1 - gj);
             h[g] = hv; qx[g] = qxv; qy[g] = -qyv;
         } else if (gj == 0) {
+            T gh = hv, gqx = qxv, gqy = qyv;
+            if (IMPOSED && P.bc[2] >= SWOF_BC_IMPOSED_H) imposed_state<T>(P, 2, hv, qyv, qxv, gh, gqy, gqx);
             size_t g1 = pidx(P, gi, -1), g2 = pidx(P, gi, -2);
-            h[g1] = hv; qx[g1] = qxv; qy[g1] = qyv;
-            h[g2] = hv; qx[g2] = qxv; qy[g2] = qyv;
+            h[g1] = gh; qx[g1] = gqx; qy[g1] = gqy;
+            h[g2] = gh; qx[g2] = gqx; qy[g2] = gqy;
         }
     }
     if (gj >= P.ny - 2) {    // north
@@ -586,50 +703,53 @@ __device__ __forceinline__ void store_cell(const Params &P, T *h, T *qx, T *qy, 
             size_t g = pidx(P, gi, 2 * P.ny - 1 - gj);
             h[g] = hv; qx[g] = qxv; qy[g] = -qyv;
         } else if (gj == P.ny - 1) {
+            T gh = hv, gqx = qxv, gqy = qyv;
+            if (IMPOSED && P.bc[3] >= SWOF_BC_IMPOSED_H) {
+                T qn;
+                imposed_state<T>(P, 3, hv, -qyv, qxv, gh, qn, gqx);
+                gqy = -qn;
+            }
             size_t g1 = pidx(P, gi, P.ny), g2 = pidx(P, gi, P.ny + 1);
-            h[g1] = hv; qx[g1] = qxv; qy[g1] = qyv;
-            h[g2] = hv; qx[g2] = qxv; qy[g2] = qyv;
+            h[g1] = gh; qx[g1] = gqx; qy[g1] = gqy;
+            h[g2] = gh; qx[g2] = gqx; qy[g2] = gqy;
         }
     }
 }
 
+// Write one interior cell of a stage output and the ghost cells it defines.
+template <typename T, bool IMPOSED = true>
+__device__ __forceinline__ void store_cell(const Params &P, T *h, T *qx, T *qy, int gi, int gj,
+                                           T hv, T qxv, T qyv)
+{
+    size_t o = pidx(P, gi, gj);
+    h[o] = hv;
+    qx[o] = qxv;
+    qy[o] = qyv;
+    ghosts_x<T, IMPOSED>(P, h, qx, qy, gi, gj, hv, qxv, qyv);
+    ghosts_y<T, IMPOSED>(P, h, qx, qy, gi, gj, hv, qxv, qyv);
+}
+
 // ---------------------------------------------------------------------------
-// Ghost cells of U^n from its interior (used after a state is set).
+// Ghost cells of a state from its interior (after a state is set, and after
+// each stage when an edge is imposed): thread k < ny does the W/E ghosts of
+// row k, the next nx threads the S/N ghosts of one column each.
 template <typename T>
 __global__ void k_ghosts(Params P, Fields<T> F)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < P.ny) {
-        int gj = k;
-        for (int s = 0; s < 2; ++s) {
-            int gi = (s == 0) ? 0 : P.nx - 1;
-            for (int l = 0; l < 2; ++l) {
-                int src = (s == 0) ? l : P.nx - 1 - l;
-                int dst = (s == 0) ? -1 - l : P.nx + l;
-                int b = P.bc[s];
-                int from = (b == SWOF_BC_WALL) ? src : gi;
-                T sign = (b == SWOF_BC_WALL) ? T(-1) : T(1);
-                size_t o = pidx(P, from, gj), d = pidx(P, dst, gj);
-                F.h[d] = F.h[o];
-                F.qx[d] = sign * F.qx[o];
-                F.qy[d] = F.qy[o];
-            }
+        const int gj = k;
+        const int cols[4] = {0, 1, P.nx - 2, P.nx - 1};
+        for (int c = 0; c < 4; ++c) {
+            size_t o = pidx(P, cols[c], gj);
+            ghosts_x(P, F.h, F.qx, F.qy, cols[c], gj, F.h[o], F.qx[o], F.qy[o]);
         }
     } else if (k < P.ny + P.nx) {
-        int gi = k - P.ny;
-        for (int s = 0; s < 2; ++s) {
-            int gj = (s == 0) ? 0 : P.ny - 1;
-            for (int l = 0; l < 2; ++l) {
-                int src = (s == 0) ? l : P.ny - 1 - l;
-                int dst = (s == 0) ? -1 - l : P.ny + l;
-                int b = P.bc[2 + s];
-                int from = (b == SWOF_BC_WALL) ? src : gj;
-                T sign = (b == SWOF_BC_WALL) ? T(-1) : T(1);
-                size_t o = pidx(P, gi, from), d = pidx(P, gi, dst);
-                F.h[d] = F.h[o];
-                F.qx[d] = F.qx[o];
-                F.qy[d] = sign * F.qy[o];
-            }
+        const int gi = k - P.ny;
+        const int rows[4] = {0, 1, P.ny - 2, P.ny - 1};
+        for (int r = 0; r < 4; ++r) {
+            size_t o = pidx(P, gi, rows[r]);
+            ghosts_y(P, F.h, F.qx, F.qy, gi, rows[r], F.h[o], F.qx[o], F.qy[o]);
         }
     }
 }
@@ -675,11 +795,193 @@ __global__ void __launch_bounds__(NT) k_reduce(Params P, Fields<T> F, double *ou
 namespace swof {
 
 // ---------------------------------------------------------------------------
-// Launchers
+// End of a first-order step (Sec. 3.3): U^{n+1} = U* of the single Euler
+// stage, then rain, Green-Ampt and the dry clean-up in the order used after
+// the Heun average, the ghosts, and the wave
+// speeds of U^{n+1} on the cell values (plus an imposed edge's boundary
+// state) for the next step's dt; with the CFL check on, the same speeds of
+// U* first.  Blocks stride over rows, threads over the cells of a row.
 template <typename T>
-int launch_ghosts_t(const Params &P, void *f, void *stream)
+__device__ __forceinline__ void o1_speed(T h, T qx, T qy, T hdry, T g, T &ax, T &ay)
 {
-    const Fields<T> &F = *static_cast<const Fields<T> *>(f);
+    T u = T(0), v = T(0);
+    if (h > hdry) {
+        T r = rcp(h);
+        u = qx * r;
+        v = qy * r;
+    }
+    T c = sq(g * h);
+    ax = ab(u) + c;
+    ay = ab(v) + c;
+}
+
+// max speed of the ghosts an imposed edge holds beside cell (gi, gj)
+template <typename T, typename K>
+__device__ __forceinline__ void o1_ghost_speeds(const Params &P, const T *h, const T *qx, const T *qy, int gi, int gj,
+                                                T hdry, T g, K &kx, K &ky)
+{
+    T ax, ay;
+    if (gi == 0 && P.bc[0] >= SWOF_BC_IMPOSED_H) {
+        size_t o = pidx(P, -1, gj);
+        o1_speed(h[o], qx[o], qy[o], hdry, g, ax, ay);
+        kx = kmax(kx, speed_key(ax));
+    }
+    if (gi == P.nx - 1 && P.bc[1] >= SWOF_BC_IMPOSED_H) {
+        size_t o = pidx(P, P.nx, gj);
+        o1_speed(h[o], qx[o], qy[o], hdry, g, ax, ay);
+        kx = kmax(kx, speed_key(ax));
+    }
+    if (gj == 0 && P.bc[2] >= SWOF_BC_IMPOSED_H) {
+        size_t o = pidx(P, gi, -1);
+        o1_speed(h[o], qx[o], qy[o], hdry, g, ax, ay);
+        ky = kmax(ky, speed_key(ay));
+    }
+    if (gj == P.ny - 1 && P.bc[3] >= SWOF_BC_IMPOSED_H) {
+        size_t o = pidx(P, gi, P.ny);
+        o1_speed(h[o], qx[o], qy[o], hdry, g, ax, ay);
+        ky = kmax(ky, speed_key(ay));
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_commit1(Params P, Fields<T> F)
+{
+    using K = decltype(speed_key(T(0)));
+    __shared__ K red[2][NW];
+    __shared__ double sred[NW];
+    DevCtl *ctl = F.ctl;
+    if (ctl->status) return;
+    const Scal<T> C = scal<T>(P);
+    T dt, rdt;
+    if constexpr (std::is_same<T, double>::value) {
+        dt = ctl->dt; rdt = ctl->rdt;
+    } else {
+        dt = ctl->fdt; rdt = ctl->frdt;
+    }
+    const bool rain = ctl->rain_active != 0;
+    K kx = 0, ky = 0, cx = 0, cy = 0;
+    T infacc = T(0);
+    for (int gj = blockIdx.x; gj < P.ny; gj += gridDim.x)
+    for (int gi = threadIdx.x; gi < P.nx; gi += NT) {
+        const size_t o = pidx(P, gi, gj);
+        T h = F.h1[o], qx = F.qx1[o], qy = F.qy1[o];
+        T ax, ay;
+        if (P.check_cfl) {
+            o1_speed(h, qx, qy, C.hdry, C.g, ax, ay);
+            cx = kmax(cx, speed_key(ax));
+            cy = kmax(cy, speed_key(ay));
+            o1_ghost_speeds(P, F.h1, F.qx1, F.qy1, gi, gj, C.hdry, C.g, cx, cy);
+        }
+        if (rain) h = h + rdt;
+        if (P.infiltration) {
+            T vi = F.vinf[o];
+            T ks = F.ksmap ? F.ksmap[o] : C.ks;
+            T d;
+            if (vi > T(0)) {
+                T ic = ks * (T(1) + ((C.psi + h) * C.dtheta) / vi);
+                d = mn(h, dt * ic);
+            } else {
+                d = h;
+            }
+            h = h - d;
+            F.vinf[o] = vi + d;
+            infacc += d;
+        }
+        if (h <= C.hdry) {
+            qx = T(0);
+            qy = T(0);
+        }
+        store_cell<T>(P, F.h, F.qx, F.qy, gi, gj, h, qx, qy);
+        o1_speed(h, qx, qy, C.hdry, C.g, ax, ay);
+        kx = kmax(kx, speed_key(ax));
+        ky = kmax(ky, speed_key(ay));
+        o1_ghost_speeds(P, F.h, F.qx, F.qy, gi, gj, C.hdry, C.g, kx, ky);
+    }
+    if (P.infiltration && !P.no_budget) {
+        double s = block_sum_t(infacc, sred);
+        if (threadIdx.x == 0) F.infil_slots[blockIdx.x] += s;
+    }
+    kx = block_max(kx, red[0]);
+    ky = block_max(ky, red[1]);
+    if (threadIdx.x == 0) {
+        atomicMax(&ctl->lam_bits[0], key64(kx));
+        atomicMax(&ctl->lam_bits[1], key64(ky));
+    }
+    if (P.check_cfl) {
+        cx = block_max(cx, red[0]);
+        cy = block_max(cy, red[1]);
+        if (threadIdx.x == 0) {
+            atomicMax(&ctl->lam2_bits[0], key64(cx));
+            atomicMax(&ctl->lam2_bits[1], key64(cy));
+            __threadfence();
+            if (atomicAdd(&ctl->done2, 1u) == gridDim.x - 1) {
+                __threadfence();
+                double lx = __longlong_as_double((long long)atomicAdd(&ctl->lam2_bits[0], 0ull));
+                double ly = __longlong_as_double((long long)atomicAdd(&ctl->lam2_bits[1], 0ull));
+                ctl->lam2_bits[0] = 0ull;
+                ctl->lam2_bits[1] = 0ull;
+                ctl->done2 = 0u;
+                if (ctl->dt * (lx / P.dx + ly / P.dy) > P.cfl) ctl->cfl_viol++;
+            }
+        }
+    }
+}
+
+// Gauge record after a step: t, then (h, hu, hv) of each gauge cell (FP64).
+template <typename T>
+__global__ void k_gauges(Params P, Fields<T> F)
+{
+    DevCtl *ctl = F.ctl;
+    if (ctl->status) return;
+    const long long n = ctl->gauge_n;
+    if (n >= F.gauge_cap) return;
+    double *r = F.gauge_rec + n * (1 + 3LL * F.n_gauges);
+    for (int g = threadIdx.x; g < F.n_gauges; g += blockDim.x) {
+        const long long o = F.gauge_off[g];
+        r[1 + 3 * g] = (double)F.h[o];
+        r[2 + 3 * g] = (double)F.qx[o];
+        r[3 + 3 * g] = (double)F.qy[o];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        r[0] = ctl->t;
+        ctl->gauge_n = n + 1;
+    }
+}
+
+// Running maximum depth after a step (only while it is tracked): one pass
+// over the interior, hmax = max(hmax, h).
+template <typename T>
+__global__ void k_hmax(Params P, const T *h, T *hmax)
+{
+    for (int gj = blockIdx.x; gj < P.ny; gj += gridDim.x)
+        for (int gi = threadIdx.x; gi < P.nx; gi += blockDim.x) {
+            size_t o = pidx(P, gi, gj);
+            hmax[o] = mx(hmax[o], h[o]);
+        }
+}
+
+// Interior of one padded field -> dense [ny][nx] FP64.
+template <typename T>
+__global__ void k_pack1(Params P, const T *src, double *dst)
+{
+    size_t n = (size_t)P.nx * P.ny;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        dst[k] = (double)src[pidx(P, (int)(k % P.nx), (int)(k / P.nx))];
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// which = 0: U^n (h, qx, qy); 1: U* (h1, qx1, qy1)
+template <typename T>
+int launch_ghosts_t(const Params &P, void *f, int which, void *stream)
+{
+    Fields<T> F = *static_cast<const Fields<T> *>(f);
+    if (which == 1) {
+        F.h = F.h1;
+        F.qx = F.qx1;
+        F.qy = F.qy1;
+    }
     int n = P.nx + P.ny;
     k_ghosts<T><<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(P, F);
     return (int)cudaGetLastError();
@@ -734,8 +1036,69 @@ int launch_stage_t(const Params &P, void *f, void *stream)
     case 1: return launch_sweep<T, STAGE, 128, 64>(P, F, s);
     case 2: return launch_sweep<T, STAGE, 256, 32>(P, F, s);
     case 3: return launch_sweep<T, STAGE, 64, 64>(P, F, s);
+    case 4: return launch_sweep<T, STAGE, 64, 16>(P, F, s);
     default: return launch_sweep<T, STAGE, 128, 32>(P, F, s);
     }
+}
+
+template <typename T, int NTX, int H>
+int launch_sweep_o1(const Params &P, const Fields<T> &F, cudaStream_t s)
+{
+    dim3 grid((P.nx + NTX - 5) / (NTX - 4), (P.ny + H - 1) / H);
+    k_sweep<T, 1, NTX, H, true><<<grid, NTX, 0, s>>>(P, F);
+    return (int)cudaGetLastError();
+}
+
+template <typename T>
+int launch_stage1_o1_t(const Params &P, void *f, void *stream)
+{
+    const Fields<T> &F = *static_cast<const Fields<T> *>(f);
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (P.tile_cfg) {
+    case 1: return launch_sweep_o1<T, 128, 64>(P, F, s);
+    case 2: return launch_sweep_o1<T, 256, 32>(P, F, s);
+    case 3: return launch_sweep_o1<T, 64, 64>(P, F, s);
+    case 4: return launch_sweep_o1<T, 64, 16>(P, F, s);
+    default: return launch_sweep_o1<T, 128, 32>(P, F, s);
+    }
+}
+
+// grid of the first-order commit: at most one block per budget slot
+template <typename T>
+int launch_commit_o1_t(const Params &P, void *f, void *stream)
+{
+    const Fields<T> &F = *static_cast<const Fields<T> *>(f);
+    long long b = P.ny;
+    long long cap = 152 * 8;
+    long long slots = max_stage_blocks(P.nx, P.ny);
+    if (b > cap) b = cap;
+    if (b > slots) b = slots;
+    k_commit1<T><<<(int)b, NT, 0, (cudaStream_t)stream>>>(P, F);
+    return (int)cudaGetLastError();
+}
+
+template <typename T>
+int launch_gauges_t(const Params &P, void *f, void *stream)
+{
+    const Fields<T> &F = *static_cast<const Fields<T> *>(f);
+    k_gauges<T><<<1, 256, 0, (cudaStream_t)stream>>>(P, F);
+    return (int)cudaGetLastError();
+}
+
+template <typename T>
+int launch_hmax_t(const Params &P, void *f, void *stream)
+{
+    const Fields<T> &F = *static_cast<const Fields<T> *>(f);
+    int b = P.ny < 152 * 8 ? P.ny : 152 * 8;
+    k_hmax<T><<<b, 256, 0, (cudaStream_t)stream>>>(P, F.h, F.hmax);
+    return (int)cudaGetLastError();
+}
+
+template <typename T>
+int launch_pack1_t(const Params &P, const void *src, double *dst, void *stream)
+{
+    k_pack1<T><<<1216, 256, 0, (cudaStream_t)stream>>>(P, (const T *)src, dst);
+    return (int)cudaGetLastError();
 }
 
 template <typename T>

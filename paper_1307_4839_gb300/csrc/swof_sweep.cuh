@@ -68,6 +68,7 @@ struct SweepSmem {
     V4<T> nw[2][NTX];     // U^{n+1} {h, u, v, 1/h} of the finished row
     double red[NTX / 32];
     K redk[2][NTX / 32];
+    int flag;             // dry-tile skipping: bit 0 live now, bit 1 live last step
 };
 
 // One stage over the tile (bx, by) of a (gdx x gdy) tiling; the kernel
@@ -76,7 +77,13 @@ struct SweepSmem {
 // rows) that is dry across its columns -- exact, and a large saving on
 // mostly dry grids; grids that are wet everywhere (the ensemble's rain
 // scenarios) run without the vote.
-template <typename T, int STAGE, int NTX, int H, bool DRY_SKIP = true>
+// ORD1: the first-order stage (Sec. 3.3): face values = cell values.
+// With F.tile_act set (dry-tile skipping), a tile whose 3x3 tile
+// neighbourhood held no water after the last step, with no rain and no
+// imposed edge, is left alone: every flux of the step is exactly zero there
+// and U^{n+1} = U^n (stage 2 works in place); stage 1 writes its U* = 0 once
+// when the tile turns dry, for the neighbours' halos.
+template <typename T, int STAGE, int NTX, int H, bool DRY_SKIP = true, bool ORD1 = false>
 __device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, int bx, int by, int gdx, int gdy,
                                            SweepSmem<T, NTX> &S)
 {
@@ -95,8 +102,37 @@ __device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, 
     const int t = threadIdx.x;
     const int gi = bx * W - 2 + t;
     const int j0 = by * H;
+    const int blk = by * gdx + bx;
     const bool col_in = gi <= P.nx + 1;
     const bool out_col = t >= 2 && t < NTX - 2 && gi < P.nx;
+    bool dead = false;
+    if (F.tile_act) {
+        if (STAGE == 1) {
+            if (t == 0) {
+                int live = ctl->rain_active != 0;
+                live |= (bx == 0 && P.bc[0] >= SWOF_BC_IMPOSED_H) || (bx == gdx - 1 && P.bc[1] >= SWOF_BC_IMPOSED_H) ||
+                        (by == 0 && P.bc[2] >= SWOF_BC_IMPOSED_H) || (by == gdy - 1 && P.bc[3] >= SWOF_BC_IMPOSED_H);
+                for (int dj = -1; dj <= 1; ++dj)
+                    for (int di = -1; di <= 1; ++di) {
+                        int a = bx + di, b = by + dj;
+                        if (a >= 0 && a < gdx && b >= 0 && b < gdy) live |= F.tile_act[b * gdx + a];
+                    }
+                int was = F.tile_live[blk];
+                F.tile_live[blk] = (unsigned char)live;
+                S.flag = live | (was << 1);
+                if (live) atomicAdd((unsigned long long *)&F.ctl->live_tiles, 1ull);
+                if (blk == 0) atomicAdd((unsigned long long *)&F.ctl->tiles, (unsigned long long)(gdx * gdy));
+            }
+            cta_sync<NTX>();
+            const int fl = S.flag;
+            dead = !(fl & 1);
+            if (dead && (fl & 2) && out_col)      // turned dry: its U* is 0 from now on
+                for (int ro = j0; ro < j0 + H && ro < P.ny; ++ro)
+                    store_cell<T, false>(P, F.h1, F.qx1, F.qy1, gi, ro, T(0), T(0), T(0));
+        } else {
+            dead = F.tile_live[blk] == 0;
+        }
+    }
     const T *hin = (STAGE == 1) ? F.h : F.h1;
     const T *qxin = (STAGE == 1) ? F.qx : F.qx1;
     const T *qyin = (STAGE == 1) ? F.qy : F.qy1;
@@ -140,8 +176,8 @@ __device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, 
 
     // per-cell data of the row updated in the next iteration, fetched one
     // iteration ahead: U^n (stage 2), n^2 map, V_inf and K_s
-    T un_h = T(0), un_qx = T(0), un_qy = T(0), pn2 = C.n2, pvi = T(0), pks = C.ks;
-    const bool want_prefetch = STAGE == 2 || F.n2map != nullptr;
+    T un_h = T(0), un_qx = T(0), un_qy = T(0), pn2 = C.cf, pvi = T(0), pks = C.ks;
+    const bool want_prefetch = STAGE == 2 || F.cfmap != nullptr;
     auto prefetch = [&](int ro) {
         if (!want_prefetch || !(out_col && ro >= j0 && ro < j0 + H && ro < P.ny)) return;
         size_t o = pidx(P, gi, ro);
@@ -154,9 +190,11 @@ __device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, 
                 if (F.ksmap) pks = F.ksmap[o];
             }
         }
-        if (F.n2map) pn2 = F.n2map[o];
+        if (F.cfmap) pn2 = F.cfmap[o];
     };
 
+    bool anywet = false;                // a row of U^{n+1} of this tile holds water (stage 2, uniform)
+    if (!dead) {
     T nh, nqx, nqy, nzx, nzy;
     load(j0 - 2, nh, nqx, nqy, nzx, nzy);
     for (int k = 0; k < H + 4; ++k) {
@@ -180,7 +218,9 @@ __device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, 
             const bool rec = t >= 1 && t <= NTX - 2;
             if (rec) {
                 V4<T> L = s_st[t - 1], R = s_st[t + 1];
-                if constexpr (fp64)
+                if constexpr (ORD1)
+                    q = rec1<T>(rc.h, fp64 ? zx : T(0), rc.u, rc.v);
+                else if constexpr (fp64)
                     q = muscl<T>(L.x, rc.h, R.x, s_zx[t - 1], zx, s_zx[t + 1],
                                  L.y, rc.u, R.y, L.z, rc.v, R.z, rc.rh, C.hdry);
                 else
@@ -205,8 +245,8 @@ __device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, 
                 a1 = fe.x - fw.x;
                 a2 = (fe.y - fw.z) + fcx;
                 a3 = fe.w - fw.w;
-                if (gi == 0 && P.bc[0] == SWOF_BC_OUTFLOW) outacc -= fw.x * (T)P.dy;
-                if (gi == P.nx - 1 && P.bc[1] == SWOF_BC_OUTFLOW) outacc += fe.x * (T)P.dy;
+                if (gi == 0 && P.bc[0] != SWOF_BC_WALL) outacc -= fw.x * (T)P.dy;
+                if (gi == P.nx - 1 && P.bc[1] != SWOF_BC_WALL) outacc += fe.x * (T)P.dy;
             }
             }
         }
@@ -214,7 +254,9 @@ __device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, 
         // ---- y part: recon of row r-1, face between r-2 and r-1, update of r-2 ----
         if (k >= 2) {
             Rec<T> qb;
-            if constexpr (fp64)
+            if constexpr (ORD1)
+                qb = rec1<T>(rb.h, fp64 ? rb.zy : T(0), rb.v, rb.u);
+            else if constexpr (fp64)
                 qb = muscl<T>(ra.h, rb.h, rc.h, ra.zy, rb.zy, rc.zy, ra.v, rb.v, rc.v, ra.u, rb.u, rc.u,
                               rb.rh, C.hdry);
             else
@@ -237,12 +279,19 @@ __device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, 
                 T qys = ra.qy - dtdx * a3q[0] - dtdy * b2;
                 size_t o = pidx(P, gi, ro);
                 if (hs > C.hdry) {
-                    if (P.friction == SWOF_FRIC_MANNING) {
-                        T n2 = c_n2;
+                    if (P.friction != SWOF_FRIC_NONE) {
+                        // q / (1 + dt g C_f |u^s| / h*^p), p = 4/3 (Manning,
+                        // Strickler) or 1 (Darcy-Weisbach, Chezy), Sec. 2.1, 3.2
+                        T cf = c_n2;
                         T speed = sq(ra.u * ra.u + ra.v * ra.v);
-                        T y = icbrt(hs);
-                        T hinv43 = (y * y) * (y * y);
-                        T den = T(1) + (dt * C.g * n2) * speed * hinv43;
+                        T hinv;
+                        if (P.friction <= SWOF_FRIC_STRICKLER) {
+                            T y = icbrt(hs);
+                            hinv = (y * y) * (y * y);
+                        } else {
+                            hinv = rcp(hs);
+                        }
+                        T den = T(1) + (dt * C.g * cf) * speed * hinv;
                         T rden = rcp(den);
                         qxs = qxs * rden;
                         qys = qys * rden;
@@ -251,8 +300,8 @@ __device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, 
                     qxs = T(0);
                     qys = T(0);
                 }
-                if (ro == 0 && P.bc[2] == SWOF_BC_OUTFLOW) outacc -= gs.x * (T)P.dx;
-                if (ro == P.ny - 1 && P.bc[3] == SWOF_BC_OUTFLOW) outacc += gn.x * (T)P.dx;
+                if (ro == 0 && P.bc[2] != SWOF_BC_WALL) outacc -= gs.x * (T)P.dx;
+                if (ro == P.ny - 1 && P.bc[3] != SWOF_BC_WALL) outacc += gn.x * (T)P.dx;
                 if (STAGE == 1) {
                     store_cell<T>(P, F.h1, F.qx1, F.qy1, gi, ro, hs, qxs, qys);
                 } else {
@@ -294,8 +343,11 @@ __device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, 
                 V4<T> *buf = S.nw[k & 1];
                 buf[t] = {fh, fu, fv, frh};
                 // all three rows of U^{n+1} dry across the CTA: every speed is 0
-                if (!(DRY_SKIP ? cta_and<NTX>(fh == T(0) && y1h == T(0) && y2h == T(0)) : (cta_sync<NTX>(), 0)) && out_col &&
-                    ro < P.ny) {
+                // (the same vote tells the tile flags whether the tile holds water)
+                const bool alldry = DRY_SKIP ? cta_and<NTX>(fh == T(0) && y1h == T(0) && y2h == T(0))
+                                             : (cta_sync<NTX>(), false);
+                anywet |= !alldry;
+                if (!alldry && out_col && ro < P.ny) {
                     if (xlam) {
                         V4<T> L = buf[t - 1], R = buf[t + 1];
                         lx = kmax(lx, speed_key(cell_speed(L.x, fh, R.x, L.y, fu, R.y, frh, C.hdry, C.g)));
@@ -320,30 +372,35 @@ __device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, 
         ra = rb;
         rb = rc;
     }
-
-    // FP64 budget slots, fixed order
-    const int blk = by * gdx + bx;
-    const bool edge = (bx == 0 && P.bc[0] == SWOF_BC_OUTFLOW) || (bx == gdx - 1 && P.bc[1] == SWOF_BC_OUTFLOW) ||
-                      (by == 0 && P.bc[2] == SWOF_BC_OUTFLOW) || (by == gdy - 1 && P.bc[3] == SWOF_BC_OUTFLOW);
-    if (edge && !P.no_budget) {
-        double s = block_sum_t(outacc, s_red);
-        if (t == 0) F.outflow_slots[blk] += 0.5 * ctl->dt * s;
     }
-    if (STAGE == 2 && P.infiltration && !P.no_budget) {
+
+    // FP64 budget slots, fixed order (one Euler stage at first order, else
+    // each Heun stage counts half)
+    // (a tile left alone adds nothing anywhere: its sums and maxima are 0)
+    const bool edge = (bx == 0 && P.bc[0] != SWOF_BC_WALL) || (bx == gdx - 1 && P.bc[1] != SWOF_BC_WALL) ||
+                      (by == 0 && P.bc[2] != SWOF_BC_WALL) || (by == gdy - 1 && P.bc[3] != SWOF_BC_WALL);
+    if (edge && !P.no_budget && !dead) {
+        double s = block_sum_t(outacc, s_red);
+        if (t == 0) F.outflow_slots[blk] += (ORD1 ? 1.0 : 0.5) * ctl->dt * s;
+    }
+    if (STAGE == 2 && F.tile_act && t == 0 && !dead) F.tile_act[blk] = (unsigned char)anywet;
+    if (STAGE == 2 && P.infiltration && !P.no_budget && !dead) {
         double s = block_sum_t(infacc, s_red);
         if (t == 0) F.infil_slots[blk] += s;
     }
-    if (STAGE == 2 && P.fuse_lambda) {
+    if (STAGE == 2 && P.fuse_lambda && !dead) {
         lx = block_max(lx, S.redk[0]);
         ly = block_max(ly, S.redk[1]);
-        if (t == 0) {
-            atomicMax(&F.ctl->lam_bits[0], key64(lx));
-            atomicMax(&F.ctl->lam_bits[1], key64(ly));
+        if (t == 0) {      // (a zero maximum changes nothing)
+            if (lx) atomicMax(&F.ctl->lam_bits[0], key64(lx));
+            if (ly) atomicMax(&F.ctl->lam_bits[1], key64(ly));
         }
     }
     if (STAGE == 2 && P.check_cfl) {
-        k2x = block_max(k2x, S.redk[0]);
-        k2y = block_max(k2y, S.redk[1]);
+        if (!dead) {
+            k2x = block_max(k2x, S.redk[0]);
+            k2y = block_max(k2y, S.redk[1]);
+        }
         if (t == 0) {
             DevCtl *c = F.ctl;
             atomicMax(&c->lam2_bits[0], key64(k2x));
@@ -366,11 +423,11 @@ __device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, 
 // (No minimum-blocks hint: capping registers that way made the compiler
 // route work through the FP64 pipe, which on GB300 costs more than the
 // occupancy it buys.)
-template <typename T, int STAGE, int NTX, int H>
+template <typename T, int STAGE, int NTX, int H, bool ORD1 = false>
 __global__ void __launch_bounds__(NTX) k_sweep(Params P, Fields<T> F)
 {
     __shared__ SweepSmem<T, NTX> S;
-    sweep_tile<T, STAGE, NTX, H>(P, F, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y, S);
+    sweep_tile<T, STAGE, NTX, H, true, ORD1>(P, F, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y, S);
 }
 
 }  // namespace swof

@@ -18,7 +18,10 @@ Workloads follow the test cases the paper uses or points at:
     noise, a level pool behind a dam line;
   * hillslope  - rainfall runoff with Green-Ampt infiltration (Sec. 3.5) on a
     ridge-and-furrow plane slope with lognormal K_s;
-  * ensemble_specs - a seeded batch of valley scenarios of uneven sizes.
+  * ensemble_specs - a seeded batch of valley scenarios of uneven sizes;
+  * dem        - a float32 DEM for the D8 flow-direction stencil (Sec. 6's
+    eight-neighbour example): a tilted fractal surface, optionally
+    quantised so that many neighbours tie, with no-data holes.
 """
 from __future__ import annotations
 
@@ -29,6 +32,9 @@ import numpy as np
 # Boundary codes, in W, E, S, N order (x-min, x-max, y-min, y-max).
 BC_WALL = 0
 BC_OUTFLOW = 1
+BC_IMPOSED_H = 2
+BC_IMPOSED_Q = 3
+BC_IMPOSED_HQ = 4
 
 RAIN_MM_PER_H = 1.0e-3 / 3600.0  # m/s per mm/h
 
@@ -247,3 +253,25 @@ def ensemble_member(spec: Scenario, dx: float = 2.0) -> Workload:
     return valley(n=spec.side, dx=dx, seed=spec.seed, reservoir=spec.reservoir,
                   dam_row=max(1, spec.side // 8), manning_n=spec.manning_n,
                   rain_mm_h=spec.rain_mm_h, steps=1000)
+
+
+def dem(nx: int, ny: int, seed: int, quantum: float = 0.0, nodata_frac: float = 0.0,
+        nodata: float = -9999.0) -> np.ndarray:
+    """float32 DEM [ny][nx]: 0.002 (x + 2y) tilt (cell units) + fractal
+    noise (H = 0.8, peak 1.5); with quantum > 0 values are rounded to
+    multiples of it (ties between neighbours), nodata_frac of the cells set
+    to `nodata`."""
+    rng = np.random.default_rng(seed + 1000)
+    # grids beyond 4096 repeat a 4096-periodic noise field (the synthesis is
+    # periodic, so the copies join without seams)
+    fx, fy = min(nx, 4096), min(ny, 4096)
+    noise = fractal_noise(fx, fy, 0.8, seed, 1.5).astype(np.float32)
+    z = np.tile(noise, (-(-ny // fy), -(-nx // fx)))[:ny, :nx]
+    z += (np.float32(0.002) * np.arange(nx, dtype=np.float32))[None, :]
+    z += (np.float32(0.004) * np.arange(ny, dtype=np.float32))[:, None]
+    if quantum > 0:
+        z = (np.round(z / np.float32(quantum)) * np.float32(quantum)).astype(np.float32)
+    z = np.ascontiguousarray(z, dtype=np.float32)
+    if nodata_frac > 0:
+        z[rng.random((ny, nx)) < nodata_frac] = np.float32(nodata)
+    return z

@@ -52,9 +52,10 @@ def test_struct_layout_matches_header(tmp_path):
 #include <stdio.h>
 #include "swof.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(swof_params), offsetof(swof_params, bc),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(swof_params), offsetof(swof_params, bc),
          offsetof(swof_params, friction_map), offsetof(swof_params, ks_map),
-         offsetof(swof_params, dt_fixed), offsetof(swof_params, stream));
+         offsetof(swof_params, dt_fixed), offsetof(swof_params, stream), offsetof(swof_params, friction_coef),
+         offsetof(swof_params, order), offsetof(swof_params, bc_h), offsetof(swof_params, bc_q));
   printf("%zu %zu\\n", sizeof(swof_step_info), offsetof(swof_step_info, status));
   printf("%zu %zu %zu\\n", sizeof(swof_diag), offsetof(swof_diag, min_h), offsetof(swof_diag, cfl_viol));
   printf("%zu %zu %zu\\n", sizeof(swof_scenario), offsetof(swof_scenario, manning_n), offsetof(swof_scenario, bc));
@@ -67,7 +68,8 @@ int main(void) {
                                                                check=True).stdout.strip().splitlines()]
     P = sw.SwofParams
     assert vals[0] == [ctypes.sizeof(P), P.bc.offset, P.friction_map.offset, P.ks_map.offset,
-                       P.dt_fixed.offset, P.stream.offset]
+                       P.dt_fixed.offset, P.stream.offset, P.friction_coef.offset, P.order.offset,
+                       P.bc_h.offset, P.bc_q.offset]
     assert vals[1] == [ctypes.sizeof(sw.SwofStepInfo), sw.SwofStepInfo.status.offset]
     assert vals[2] == [ctypes.sizeof(sw.SwofDiag), sw.SwofDiag.min_h.offset, sw.SwofDiag.cfl_viol.offset]
     assert vals[3] == [ctypes.sizeof(sw.SwofScenario), sw.SwofScenario.manning_n.offset, sw.SwofScenario.bc.offset]
@@ -91,6 +93,15 @@ def test_create_rejects_bad_arguments_before_touching_a_device(lib):
     assert lib.swof_create(4, 4, -1.0, 1.0, zp, ctypes.byref(p), ctypes.byref(ctx)) == sw.EINVAL
     p.bc[2] = 7
     assert lib.swof_create(4, 4, 1.0, 1.0, zp, ctypes.byref(p), ctypes.byref(ctx)) == sw.EINVAL
+    p = sw.default_params(bc=(sw.BC_IMPOSED_Q, 0, 0, 0), bc_q=(-1.0, 0, 0, 0))     # inflow only
+    assert lib.swof_create(4, 4, 1.0, 1.0, zp, ctypes.byref(p), ctypes.byref(ctx)) == sw.EINVAL
+    p = sw.default_params(friction=sw.FRIC_CHEZY, friction_coef=0.0)              # C = 0
+    assert lib.swof_create(4, 4, 1.0, 1.0, zp, ctypes.byref(p), ctypes.byref(ctx)) == sw.EINVAL
+    p = sw.default_params(friction=5)
+    assert lib.swof_create(4, 4, 1.0, 1.0, zp, ctypes.byref(p), ctypes.byref(ctx)) == sw.EINVAL
+    p = sw.default_params(order=3)
+    assert lib.swof_create(4, 4, 1.0, 1.0, zp, ctypes.byref(p), ctypes.byref(ctx)) == sw.EINVAL
+    assert lib.swof_flow_directions(None, 4, 4, None, None, None) == sw.EINVAL
     p = sw.default_params(precision=3)
     assert lib.swof_create(4, 4, 1.0, 1.0, zp, ctypes.byref(p), ctypes.byref(ctx)) == sw.EINVAL
     zn = np.full((4, 4), np.nan)

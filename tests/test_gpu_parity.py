@@ -320,7 +320,7 @@ def test_fp32_valley_512_rel_l1():
         assert rel_l1(a, b) <= 1e-4, (name, rel_l1(a, b))
 
 
-@pytest.mark.parametrize("shape", range(4))
+@pytest.mark.parametrize("shape", range(5))
 def test_fp64_every_tile_shape_bitwise(shape):
     w = si.random_state(300, 150, seed=40 + shape, dry_frac=0.2)
     w.bc = (1, 0, 0, 1)
@@ -350,4 +350,6 @@ def test_autotune_leaves_state_time_and_budgets_alone(tmp_path):
     b.step(5)
     for x, y in zip(a.state(), b.state()):
         assert np.array_equal(x, y)
-    assert a.diagnostics()["outflow"] == b.diagnostics()["outflow"]
+    # the outflow budget is summed per stage tile: another tile shape groups
+    # the same FP64 terms differently, so only the last bits may differ
+    assert a.diagnostics()["outflow"] == pytest.approx(b.diagnostics()["outflow"], rel=1e-14)

@@ -358,7 +358,7 @@ def test_gauge_outside_grid_rejected_and_max_requires_tracking():
 
 # ---------------------------------------------------------------- D8 flow direction
 
-def _d8_brute(z, nodata=-np.inf):
+def _d8_brute(z, nodata=None):
     """Restatement by angles: neighbour (di, dj) has code 1 + (angle of
     (di, dj) from +x, counter-clockwise, in steps of 45 degrees)."""
     ny, nx = z.shape
@@ -370,7 +370,7 @@ def _d8_brute(z, nodata=-np.inf):
             best, code = z[j, i], 0
             for k, (di, dj) in enumerate(order):
                 a, b = i + di, j + dj
-                if 0 <= a < nx and 0 <= b < ny and z[b, a] > nodata and z[b, a] < best:
+                if 0 <= a < nx and 0 <= b < ny and (nodata is None or z[b, a] > nodata) and z[b, a] < best:
                     best, code = z[b, a], k + 1
             out[j, i] = code
     return out
@@ -383,6 +383,10 @@ def test_d8_matches_brute_force_with_ties_and_nodata(seed):
     z[rng.random(z.shape) < 0.1] = -9999.0                    # no-data cells
     assert np.array_equal(oracle.d8(z), _d8_brute(z))
     assert np.array_equal(oracle.d8(z, nodata=-9999.0), _d8_brute(z, -9999.0))
+    assert np.array_equal(oracle.d8(z, nodata=1.0), _d8_brute(z, 1.0))
+    zi = z.copy()
+    zi[0, 0], zi[3, 4] = -np.inf, np.nan                     # -inf is a candidate without no-data; NaN never
+    assert np.array_equal(oracle.d8(zi), _d8_brute(zi))
     zc = rng.standard_normal((13, 7)).astype(np.float32)
     assert np.array_equal(oracle.d8(zc), _d8_brute(zc))
 

@@ -55,8 +55,8 @@ MUTATIONS = {
     "first_order_outflow_halved": ("o->outflow += dt * b1;", "o->outflow += 0.5 * dt * b1;"),
     "first_order_z_from_h": ("o->xzm[c] = o->xzp[c] = o->yzm[c] = o->yzp[c] = z[c];",
                              "o->xzm[c] = o->xzp[c] = o->yzm[c] = o->yzp[c] = h[c];"),
-    "d8_tie_goes_last": ("if (v > nodata && v < best) {", "if (v > nodata && v <= best) {"),
-    "d8_nodata_ignored": ("if (v > nodata && v < best) {", "if (v < best) {"),
+    "d8_tie_goes_last": ("if ((!use_nodata || v > nodata) && v < best) {", "if ((!use_nodata || v > nodata) && v <= best) {"),
+    "d8_nodata_ignored": ("if ((!use_nodata || v > nodata) && v < best) {", "if (v < best) {"),
     "d8_ne_nw_swapped": ("static const int di[8] = {1, 1, 0, -1, -1, -1, 0, 1};",
                          "static const int di[8] = {1, -1, 0, 1, -1, -1, 0, 1};"),
     "gauge_qx_qy_swapped": ("r[2 + 3 * g] = o->qx[c];", "r[2 + 3 * g] = o->qy[c];"),
@@ -291,10 +291,11 @@ def pin_d8_brute_force(L):
     z = rng.integers(0, 4, size=(7, 9)).astype(np.float32)
     z[rng.random(z.shape) < 0.15] = -9999.0
     ok = True
-    for nodata in (-np.inf, -9999.0):
+    for nodata in (None, -9999.0):
         out = np.zeros(z.shape, np.uint8)
         L.oracle_d8(z.ctypes.data_as(oracle.ctypes.POINTER(oracle.ctypes.c_float)), z.shape[1], z.shape[0],
-                    float(nodata), out.ctypes.data_as(oracle.ctypes.POINTER(oracle.ctypes.c_uint8)))
+                    int(nodata is not None), float(nodata or 0.0),
+                    out.ctypes.data_as(oracle.ctypes.POINTER(oracle.ctypes.c_uint8)))
         ok &= bool(np.array_equal(out, _d8_brute(z, nodata)))
     return ok
 
