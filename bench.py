@@ -22,6 +22,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import signal
 import statistics
 import subprocess
@@ -112,7 +113,8 @@ def recorded_metric(kernel: str, precision: str, tile, name: str):
         return None
     vals = dict(line.split(":", 1) for line in open(f) if ":" in line)
     vals = {k.strip(): v.strip() for k, v in vals.items()}
-    if vals.get("kernel_source_sha256_16") != sha or f", {tile[0]}, {tile[1]}>" not in vals.get("kernel", ""):
+    if vals.get("kernel_source_sha256_16") != sha or not re.search(rf", {tile[0]}, {tile[1]}[,>]",
+                                                                    vals.get("kernel", "")):
         return None
     try:
         return float(vals[name])
@@ -146,7 +148,7 @@ def recorded_traffic(kernel: str, precision: str, tile):
             vals[k.strip()] = v.strip()
     if vals.get("kernel_source_sha256_16") != sha:
         return None
-    if f", {tile[0]}, {tile[1]}>" not in vals.get("kernel", ""):
+    if not re.search(rf", {tile[0]}, {tile[1]}[,>]", vals.get("kernel", "")):
         return None
     try:
         return float(vals["dram_bytes_per_launch"])

@@ -411,6 +411,8 @@ int swof_create(int nx, int ny, double dx, double dy, const double *z, const swo
     P.fg = (float)P.g;
     P.fh_dry = (float)P.h_dry;
     P.fcf = (float)P.cf;
+    P.fdx = (float)dx;
+    P.fdy = (float)dy;
     P.fpsi = (float)P.psi;
     P.fdtheta = (float)P.dtheta;
     P.fks = (float)P.ks;

@@ -53,6 +53,7 @@ struct Params {
     double area;               // unused by the arithmetic; dx*dy
     // FP32 copies of the scalars the FP32 kernels use (no FP64 on their path)
     float fg, fh_dry, fcf, fpsi, fdtheta, fks;
+    float fdx, fdy;            // cell sizes for the FP32 budget terms
     float fbc_h[4], fbc_q[4];
     int tile_cfg;              // stage-1 kernel shape, index into the sweep shapes
     int tile_cfg2;             // stage-2 kernel shape
