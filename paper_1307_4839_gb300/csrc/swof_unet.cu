@@ -431,9 +431,10 @@ int conv(ConvArgs A, cudaStream_t s)
         default: break;
         }
     }
+    // (16-column layers -- the 1x1 output convolution -- stay on the gather
+    // kernel: measured 35 us there against 54 us with TMA boxes at 256^2 x 8)
     if (tma_ok(A)) {
         switch (nt) {
-        case 16: return conv_tma_launch<16>(A, s);
         case 32: return conv_tma_launch<32>(A, s);
         case 64: return conv_tma_launch<64>(A, s);
         case 128: return conv_tma_launch<128>(A, s);
