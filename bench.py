@@ -706,6 +706,19 @@ def main():
                 "step_bytes_per_cell": STEP_BYTES[P],
                 "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS,
                 "timing": "per-kernel CUDA events around every launch of the timed region"}
+    # The FP32 stage kernels are bound by instruction issue, not bytes: the
+    # issue roofline is one warp instruction per cycle per SM sub-partition
+    # (4 per SM, 152 SMs) at the SM clock sampled during the timed region;
+    # the instruction count per launch comes from the committed ncu capture
+    # of this kernel (current source and tile shape only).
+    winst = recorded_metric(dom, P, diag["tile"].get(dom), "warp instructions executed") if dom != "lambda" else None
+    mhz = (clk or {}).get("sm_mhz") or 2070.0
+    if winst:
+        peak_gi = 152 * 4 * mhz * 1e-3                 # G warp instructions / s
+        ach_gi = winst / (avg[dom] * 1e-3) * 1e-9
+        roofline["issue"] = {"warp_instructions_per_launch": winst, "achieved_ginst_s": ach_gi,
+                             "peak_ginst_s": peak_gi, "frac": ach_gi / peak_gi, "sm_mhz": mhz,
+                             "issue_active_pct_ncu": recorded_metric(dom, P, diag["tile"].get(dom), "issue active %")}
     if roofline["traffic"]:
         roofline["traffic_gbs"] = roofline["traffic"] / (avg[dom] * 1e-3) * 1e-9
         roofline["traffic_frac"] = roofline["traffic_gbs"] / hbm
