@@ -2,12 +2,13 @@
 // -fmad=false (no contraction of a*b+c) and IEEE division / square root so
 // that every value matches the FP64 oracle's operation order bit for bit.
 #include "swof_kernels.cuh"
+#include "swof_ring_tiles.cuh"
 
 namespace swof {
 
 const Launch &launch_fp64()
 {
-    static const Launch L = {configure_t<double>, launch_ghosts_t<double>, launch_lambda_t<double>, launch_lambda_ring_t<double>,
+    static const Launch L = {configure_t<double>, launch_ghosts_t<double>, launch_lambda_t<double>, launch_ring_t<double>,
                              launch_stage_t<double, 1>, launch_stage_t<double, 2>,
                              launch_stage1_o1_t<double>, launch_commit_o1_t<double>, launch_gauges_t<double>, launch_hmax_t<double>,
                              launch_pack1_t<double>,
