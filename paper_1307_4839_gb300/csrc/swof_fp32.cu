@@ -1,7 +1,7 @@
 // swof_fp32.cu -- FP32 bulk instantiation of the stencil kernels (difference
 // form of z, FMA contraction allowed).  dt, time and budgets stay FP64.
 #include "swof_kernels.cuh"
-#include "swof_ring_tiles.cuh"
+#include "swof_skip.cuh"
 
 namespace swof {
 

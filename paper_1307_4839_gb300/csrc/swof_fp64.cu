@@ -2,7 +2,7 @@
 // -fmad=false (no contraction of a*b+c) and IEEE division / square root so
 // that every value matches the FP64 oracle's operation order bit for bit.
 #include "swof_kernels.cuh"
-#include "swof_ring_tiles.cuh"
+#include "swof_skip.cuh"
 
 namespace swof {
 

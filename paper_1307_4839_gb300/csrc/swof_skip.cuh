@@ -1,5 +1,7 @@
-// swof_ring_tiles.cuh -- the tile-edge wave speeds when dry tiles are
-// skipped (sm_103a).
+// swof_skip.cuh -- the tile-edge wave speeds when dry tiles are skipped
+// (sm_103a).  (The stage kernels keep one CTA per tile: a wave of CTAs
+// looping over tiles in a fixed stride was measured slower, because the
+// wet region, long in y, then lands several live tiles on one CTA in turn.)
 //
 // The fused wave-speed pass of stage 2 covers each tile's interior; the
 // speeds of every tile's first and last column (x) and first and last row
@@ -68,8 +70,10 @@ int launch_ring_t(const Params &P, void *f, void *stream)
     if (!F.tile_live || F.n_ring_cols + F.n_ring_rows == 0) return launch_lambda_ring_t<T>(P, f, stream);
     const int gy = (P.ny + F.ring_th - 1) / F.ring_th;
     const long long tiles = (long long)F.ring_tgx * gy;
+    // two blocks per SM: each warp loops over tiles (a skipped one costs a
+    // byte), and few blocks keep the completion-ticket atomics short
     long long b = (tiles + NT / 32 - 1) / (NT / 32);
-    int grid = (int)(b < 152 * 8 ? (b > 0 ? b : 1) : 152 * 8);
+    int grid = (int)(b < 152 * 2 ? (b > 0 ? b : 1) : 152 * 2);
     k_lambda_ring_tiles<T><<<grid, NT, 0, (cudaStream_t)stream>>>(P, F);
     return (int)cudaGetLastError();
 }
