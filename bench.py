@@ -288,6 +288,25 @@ def time_oracle(w, steps_cap: int, budget_s: float):
     return n, dt, oracle.threads()
 
 
+def time_oracle_single_thread(side: int, budget_s: float = 15.0):
+    """The oracle restricted to one OpenMP thread (a fresh process, so the
+    thread count is fixed before the library starts): full-grid steps of the
+    same valley until the budget is used.  Returns (cells per second, steps),
+    or None if the child fails."""
+    code = ("import sys, time, json; sys.path.insert(0, %r); import oracle, swof_inputs as si; "
+            "w = si.valley(%d); o = oracle.Oracle.from_workload(w); t0 = time.perf_counter(); n = 0\n"
+            "while True:\n    o.step(1); n += 1\n    if time.perf_counter() - t0 > %f: break\n"
+            "print(json.dumps({'n': n, 's': time.perf_counter() - t0, 'threads': oracle.threads()}))"
+            % (ROOT, side, budget_s))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+        return side * side * d["n"] / d["s"], d["n"], d["threads"]
+    except Exception:
+        return None
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -838,6 +857,10 @@ def main():
         n, el, cores = time_oracle(w, 8, 12.0)
         cpu = {"value": cells * n / el * 1e-9, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{n} full-grid FP64 steps of the same valley from its initial state"}
+        one = time_oracle_single_thread(args.side)
+        if one:
+            cpu["single_thread"] = {"value": one[0] * 1e-9, "unit": UNIT, "threads": one[2],
+                                    "sample": f"{one[1]} full-grid FP64 steps, one OpenMP thread"}
 
     launches = 3 * args.steps
     line = {

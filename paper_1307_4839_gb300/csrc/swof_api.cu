@@ -533,7 +533,7 @@ int swof_set_state(swof_ctx *c, const double *h, const double *hu, const double 
     if (flag & 1) return SWOF_ENONFINITE;
     if (flag & 2) return SWOF_ENEGATIVE;
     st = cuda_err((cudaError_t)c->L->unpack(c->P, c->fields(), s0, s1, s2, SWOF_FP64, c->stream));
-    if (!st) st = cuda_err((cudaError_t)c->L->ghosts(c->P, c->fields(), 0, c->stream));
+    if (!st) st = cuda_err((cudaError_t)c->L->ghosts(c->P, c->fields(), c->stream));
     if (!st) st = clear_status(c);
     if (!st) st = invalidate_lambda(c);
     if (!st) st = reset_activity(c);
@@ -564,7 +564,7 @@ int swof_set_state_device(swof_ctx *c, const void *h, const void *hu, const void
 {
     if (!c || !h || !hu || !hv || (dtype != SWOF_FP64 && dtype != SWOF_FP32)) return SWOF_EINVAL;
     int st = cuda_err((cudaError_t)c->L->unpack(c->P, c->fields(), h, hu, hv, dtype, c->stream));
-    if (!st) st = cuda_err((cudaError_t)c->L->ghosts(c->P, c->fields(), 0, c->stream));
+    if (!st) st = cuda_err((cudaError_t)c->L->ghosts(c->P, c->fields(), c->stream));
     if (!st) st = clear_status(c);
     if (!st) st = invalidate_lambda(c);
     if (!st) st = reset_activity(c);

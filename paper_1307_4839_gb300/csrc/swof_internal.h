@@ -114,7 +114,7 @@ struct Fields {
 // enqueue on `stream` and return cudaError_t as int.
 struct Launch {
     int (*configure)();              // per-device kernel attributes
-    int (*ghosts)(const Params &, void *fields, int which, void *stream);   // 0: U^n, 1: U*
+    int (*ghosts)(const Params &, void *fields, void *stream);
     int (*lambda)(const Params &, void *fields, void *stream);
     int (*lambda_ring)(const Params &, void *fields, void *stream);
     int (*stage1)(const Params &, void *fields, void *stream);

@@ -730,9 +730,9 @@ __device__ __forceinline__ void store_cell(const Params &P, T *h, T *qx, T *qy, 
 }
 
 // ---------------------------------------------------------------------------
-// Ghost cells of a state from its interior (after a state is set, and after
-// each stage when an edge is imposed): thread k < ny does the W/E ghosts of
-// row k, the next nx threads the S/N ghosts of one column each.
+// Ghost cells of U^n from its interior (after a state is set): thread k < ny
+// does the W/E ghosts of row k, the next nx threads the S/N ghosts of one
+// column each.
 template <typename T>
 __global__ void k_ghosts(Params P, Fields<T> F)
 {
@@ -972,16 +972,10 @@ __global__ void k_pack1(Params P, const T *src, double *dst)
 
 // ---------------------------------------------------------------------------
 // Launchers
-// which = 0: U^n (h, qx, qy); 1: U* (h1, qx1, qy1)
 template <typename T>
-int launch_ghosts_t(const Params &P, void *f, int which, void *stream)
+int launch_ghosts_t(const Params &P, void *f, void *stream)
 {
-    Fields<T> F = *static_cast<const Fields<T> *>(f);
-    if (which == 1) {
-        F.h = F.h1;
-        F.qx = F.qx1;
-        F.qy = F.qy1;
-    }
+    const Fields<T> &F = *static_cast<const Fields<T> *>(f);
     int n = P.nx + P.ny;
     k_ghosts<T><<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(P, F);
     return (int)cudaGetLastError();
@@ -1068,10 +1062,10 @@ template <typename T>
 int launch_commit_o1_t(const Params &P, void *f, void *stream)
 {
     const Fields<T> &F = *static_cast<const Fields<T> *>(f);
+    // one block per row (up to the number of budget slots): enough loads in
+    // flight to stream the 24 B per cell (FP32) of the step end
     long long b = P.ny;
-    long long cap = 152 * 8;
     long long slots = max_stage_blocks(P.nx, P.ny);
-    if (b > cap) b = cap;
     if (b > slots) b = slots;
     k_commit1<T><<<(int)b, NT, 0, (cudaStream_t)stream>>>(P, F);
     return (int)cudaGetLastError();

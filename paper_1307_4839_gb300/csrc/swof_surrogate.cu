@@ -262,7 +262,7 @@ int enqueue_fallback(swof_ctx *c, float *sb, int C, long long HW, int out_ch, do
     else
         k_member_in<float><<<g, 256, 0, c->stream>>>(c->P, c->f32, c->ctl, sb, HW, vinf, t);
     int st = cuerr(cudaGetLastError());
-    if (!st) st = cuerr((cudaError_t)c->L->ghosts(c->P, c->fields(), 0, c->stream));
+    if (!st) st = cuerr((cudaError_t)c->L->ghosts(c->P, c->fields(), c->stream));
     c->lam_valid = false;
     if (!st) st = swof_step(c, steps, nullptr);
     if (st) return st;
