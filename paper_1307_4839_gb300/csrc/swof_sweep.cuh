@@ -260,21 +260,30 @@ __device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, 
 
         // ---- y part: recon of row r-1, face between r-2 and r-1, update of r-2 ----
         if (k >= 2) {
-            Rec<T> qb;
-            if constexpr (ORD1)
-                qb = rec1<T>(rb.h, fp64 ? rb.zy : T(0), rb.v, rb.u);
-            else if constexpr (fp64)
-                qb = muscl<T>(ra.h, rb.h, rc.h, ra.zy, rb.zy, rc.zy, ra.v, rb.v, rc.v, ra.u, rb.u, rc.u,
-                              rb.rh, C.hdry);
-            else
-                qb = muscl<T>(ra.h, rb.h, rc.h, ra.zy, rb.zy, T(0), ra.v, rb.v, rc.v, ra.u, rb.u, rc.u,
-                              rb.rh, C.hdry);
-            if (STAGE == 2 && P.check_cfl && out_col && r - 1 >= j0 && r - 1 < j0 + H && r - 1 < P.ny)
-                k2y = kmax(k2y, speed_key(mx(ab(qb.unm) + sq(C.g * qb.hm), ab(qb.unp) + sq(C.g * qb.hp))));
+            // Three dry cells down the column (h = 0 exactly): a dry cell's
+            // reconstructed depths are 0 on both faces, so the face above it
+            // and the face below it are dry-dry and their fluxes are exact
+            // zeros whatever the reconstructed z; the centred term is 0 and
+            // the speeds are 0.  The thread skips the reconstruction and the
+            // face (no barrier involved; the result is the full path's).
+            Rec<T> qb{};
             V4<T> gn{};
-            if (k >= 3)
-                face_flux<T>(C.g, ypa.x, ypa.y, ypa.z, ypa.w, qb.hm, qb.zm, qb.unm, qb.utm,
-                             fp64 ? T(0) : ra.zy, gn.x, gn.y, gn.z, gn.w);
+            const bool ydry = DRY_SKIP && ra.h == T(0) && rb.h == T(0) && rc.h == T(0);
+            if (!ydry) {
+                if constexpr (ORD1)
+                    qb = rec1<T>(rb.h, fp64 ? rb.zy : T(0), rb.v, rb.u);
+                else if constexpr (fp64)
+                    qb = muscl<T>(ra.h, rb.h, rc.h, ra.zy, rb.zy, rc.zy, ra.v, rb.v, rc.v, ra.u, rb.u, rc.u,
+                                  rb.rh, C.hdry);
+                else
+                    qb = muscl<T>(ra.h, rb.h, rc.h, ra.zy, rb.zy, T(0), ra.v, rb.v, rc.v, ra.u, rb.u, rc.u,
+                                  rb.rh, C.hdry);
+                if (STAGE == 2 && P.check_cfl && out_col && r - 1 >= j0 && r - 1 < j0 + H && r - 1 < P.ny)
+                    k2y = kmax(k2y, speed_key(mx(ab(qb.unm) + sq(C.g * qb.hm), ab(qb.unp) + sq(C.g * qb.hp))));
+                if (k >= 3)
+                    face_flux<T>(C.g, ypa.x, ypa.y, ypa.z, ypa.w, qb.hm, qb.zm, qb.unm, qb.utm,
+                                 fp64 ? T(0) : ra.zy, gn.x, gn.y, gn.z, gn.w);
+            }
             const int ro = r - 2;                      // row updated now
             T fh = T(0), fu = T(0), fv = T(0), frh = T(0);
             if (k >= 4 && ro < P.ny && out_col) {
