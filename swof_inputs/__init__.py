@@ -117,7 +117,7 @@ def valley(n: int = 4096, dx: float = 2.0, seed: int = 1,
            manning_n: float = 0.033, side_slope: float = 0.15,
            long_slope: float = 0.003, noise_peak: float = 1.5,
            hurst: float = 0.8, rain_mm_h: float = 0.0,
-           steps: int = 2000) -> Workload:
+           steps: int = 2000, literal_pool: bool = False) -> Workload:
     """Synthetic dam-break valley flood (stand-in for the Malpasset case).
 
     z = side_slope |x - x_c| + long_slope (L_y - y) + fractal noise.
@@ -125,7 +125,9 @@ def valley(n: int = 4096, dx: float = 2.0, seed: int = 1,
     eta = long_slope (L_y - y_{dam_row-1}) + reservoir (the noise-free
     thalweg elevation of the last reservoir row plus the reservoir depth);
     h = max(0, eta - z) there, dry (h = 0) downstream.  Outflow at the
-    downstream edge (j = ny - 1), walls elsewhere.
+    downstream edge (j = ny - 1), walls elsewhere.  literal_pool: the
+    literal reading instead, h = reservoir in every cell upstream of the dam
+    row (water stands on the valley walls).
     """
     if dam_row is None:
         dam_row = 512 if n == 4096 else max(1, n // 8)
@@ -138,7 +140,7 @@ def valley(n: int = 4096, dx: float = 2.0, seed: int = 1,
          + fractal_noise(n, n, hurst, seed, noise_peak))
     eta = long_slope * (ly - y[dam_row - 1]) + reservoir
     h = np.zeros((n, n))
-    h[:dam_row, :] = np.maximum(0.0, eta - z[:dam_row, :])
+    h[:dam_row, :] = reservoir if literal_pool else np.maximum(0.0, eta - z[:dam_row, :])
     zero = np.zeros((n, n))
     return Workload(name=f"valley_{n}", nx=n, ny=n, dx=dx, dy=dx, z=z, h=h,
                     qx=zero.copy(), qy=zero.copy(),
