@@ -600,38 +600,36 @@ __global__ void __launch_bounds__(NT) k_lambda_ring(Params P, Fields<T> F)
     if (ctl->status) return;
     const Scal<T> C = scal<T>(P);
     K kx = 0, ky = 0;
-    const long long nxr = (long long)F.n_ring_cols * P.ny;
-    const long long total = nxr + (long long)F.n_ring_rows * P.nx;
-    for (long long k = blockIdx.x * (long long)NT + threadIdx.x; k < total; k += (long long)gridDim.x * NT) {
-        if (F.tile_live) {
-            // a tile left alone in the last step holds U^{n+1} = U^n = 0:
-            // every speed there is 0
-            int gi, gj;
-            if (k < nxr) {
-                gj = (int)(k / F.n_ring_cols);
-                gi = F.ring_cols[k % F.n_ring_cols];
-            } else {
-                gj = F.ring_rows[(k - nxr) / P.nx];
-                gi = (int)((k - nxr) % P.nx);
-            }
-            if (!F.tile_live[(gj / F.ring_th) * F.ring_tgx + gi / F.ring_tw]) continue;
-        }
-        if (k < nxr) {
-            int gj = (int)(k / F.n_ring_cols), gi = F.ring_cols[k % F.n_ring_cols];
-            V4<T> w = cell_rec(P, F, gi - 1, gj, C.hdry), m = cell_rec(P, F, gi, gj, C.hdry),
-                  e = cell_rec(P, F, gi + 1, gj, C.hdry);
-            kx = kmax(kx, speed_key(cell_speed(w.x, m.x, e.x, w.y, m.y, e.y, m.w, C.hdry, C.g)));
-            if (gi == 0 && P.bc[0] >= SWOF_BC_IMPOSED_H) kx = kmax(kx, speed_key(ab(w.y) + sq(C.g * w.x)));
-            if (gi == P.nx - 1 && P.bc[1] >= SWOF_BC_IMPOSED_H) kx = kmax(kx, speed_key(ab(e.y) + sq(C.g * e.x)));
-        } else {
-            long long q = k - nxr;
-            int gj = F.ring_rows[q / P.nx], gi = (int)(q % P.nx);
-            V4<T> s_ = cell_rec(P, F, gi, gj - 1, C.hdry), m = cell_rec(P, F, gi, gj, C.hdry),
-                  n = cell_rec(P, F, gi, gj + 1, C.hdry);
-            ky = kmax(ky, speed_key(cell_speed(s_.x, m.x, n.x, s_.z, m.z, n.z, m.w, C.hdry, C.g)));
-            if (gj == 0 && P.bc[2] >= SWOF_BC_IMPOSED_H) ky = kmax(ky, speed_key(ab(s_.z) + sq(C.g * s_.x)));
-            if (gj == P.ny - 1 && P.bc[3] >= SWOF_BC_IMPOSED_H) ky = kmax(ky, speed_key(ab(n.z) + sq(C.g * n.x)));
-        }
+    // x speeds on the ring columns of every row: each thread keeps one ring
+    // column and walks rows (no index division inside the loops)
+    const int nc = F.n_ring_cols;
+    if (nc > 0) {
+        const int rows_per = NT / nc > 0 ? NT / nc : 1;
+        const int tr = threadIdx.x / nc, c = threadIdx.x % nc;
+        if (tr < rows_per)
+            for (int gj = blockIdx.x * rows_per + tr; gj < P.ny; gj += gridDim.x * rows_per)
+                for (int cc = c; cc < nc; cc += NT) {
+                    const int gi = F.ring_cols[cc];
+                    V4<T> w = cell_rec(P, F, gi - 1, gj, C.hdry), m = cell_rec(P, F, gi, gj, C.hdry),
+                          e = cell_rec(P, F, gi + 1, gj, C.hdry);
+                    kx = kmax(kx, speed_key(cell_speed(w.x, m.x, e.x, w.y, m.y, e.y, m.w, C.hdry, C.g)));
+                    if (gi == 0 && P.bc[0] >= SWOF_BC_IMPOSED_H) kx = kmax(kx, speed_key(ab(w.y) + sq(C.g * w.x)));
+                    if (gi == P.nx - 1 && P.bc[1] >= SWOF_BC_IMPOSED_H)
+                        kx = kmax(kx, speed_key(ab(e.y) + sq(C.g * e.x)));
+                }
+    }
+    // y speeds on the ring rows: blocks over (ring row, NT-column chunk)
+    // items (one division per item, not per cell), threads along the chunk
+    const int chunks = (P.nx + NT - 1) / NT;
+    for (int it = blockIdx.x; it < F.n_ring_rows * chunks; it += gridDim.x) {
+        const int q = it / chunks, gi = (it - q * chunks) * NT + threadIdx.x;
+        if (gi >= P.nx) continue;
+        const int gj = F.ring_rows[q];
+        V4<T> s_ = cell_rec(P, F, gi, gj - 1, C.hdry), m = cell_rec(P, F, gi, gj, C.hdry),
+              n = cell_rec(P, F, gi, gj + 1, C.hdry);
+        ky = kmax(ky, speed_key(cell_speed(s_.x, m.x, n.x, s_.z, m.z, n.z, m.w, C.hdry, C.g)));
+        if (gj == 0 && P.bc[2] >= SWOF_BC_IMPOSED_H) ky = kmax(ky, speed_key(ab(s_.z) + sq(C.g * s_.x)));
+        if (gj == P.ny - 1 && P.bc[3] >= SWOF_BC_IMPOSED_H) ky = kmax(ky, speed_key(ab(n.z) + sq(C.g * n.x)));
     }
     kx = block_max(kx, red[0]);
     ky = block_max(ky, red[1]);

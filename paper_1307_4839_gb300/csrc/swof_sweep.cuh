@@ -58,6 +58,12 @@ __device__ __forceinline__ int cta_and(int p)
     }
 }
 
+// x == 0 of either sign; FP64 on the bit pattern, off GB300's narrow FP64
+// pipe (same answer as the comparison, NaN included).
+__device__ __forceinline__ bool is0(double x) { return (__double_as_longlong(x) << 1) == 0; }
+__device__ __forceinline__ bool is0(float x) { return x == 0.0f; }
+__device__ __forceinline__ unsigned long long bits(double x) { return (unsigned long long)__double_as_longlong(x); }
+
 template <typename T, int NTX>
 struct SweepSmem {
     using K = decltype(speed_key(T(0)));
@@ -220,7 +226,7 @@ __device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, 
             // A row with h = 0 in every column of the CTA has zero x fluxes
             // and a zero Fc (h_- + h_+ = 0): its x differences are +0, the
             // value a1..a3 already hold, so the CTA skips the x part.
-            if (!(DRY_SKIP ? cta_and<NTX>(rc.h == T(0)) : (cta_sync<NTX>(), 0))) {
+            if (!(DRY_SKIP ? cta_and<NTX>(is0(rc.h)) : (cta_sync<NTX>(), 0))) {
             Rec<T> q{};
             const bool rec = t >= 1 && t <= NTX - 2;
             if (rec) {
@@ -268,7 +274,7 @@ __device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, 
             // face (no barrier involved; the result is the full path's).
             Rec<T> qb{};
             V4<T> gn{};
-            const bool ydry = DRY_SKIP && ra.h == T(0) && rb.h == T(0) && rc.h == T(0);
+            const bool ydry = DRY_SKIP && is0(ra.h) && is0(rb.h) && is0(rc.h);
             if (!ydry) {
                 if constexpr (ORD1)
                     qb = rec1<T>(rb.h, fp64 ? rb.zy : T(0), rb.v, rb.u);
@@ -287,14 +293,28 @@ __device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, 
             const int ro = r - 2;                      // row updated now
             T fh = T(0), fu = T(0), fv = T(0), frh = T(0);
             if (k >= 4 && ro < P.ny && out_col) {
+                // FP64: a cell at h = +0 whose x and y flux differences and
+                // centred terms are all +0 ends the stage at (+0, 0, 0) -- what
+                // the update below gives (+0 - dt/dx (+0) - dt/dy (+0), then
+                // q := 0 below h_dry) -- so it skips the FP64 arithmetic; the
+                // test is one OR of the bit patterns.
+                bool quiet = false;
+                if constexpr (fp64)
+                    quiet = DRY_SKIP && (bits(ra.h) | bits(a1q[0]) | bits(a2q[0]) | bits(a3q[0]) | bits(gn.x) |
+                                         bits(gs.x) | bits(gn.y) | bits(gs.z) | bits(fcya) | bits(gn.w) |
+                                         bits(gs.w)) == 0ull;
+                T hs = T(0), qxs = T(0), qys = T(0);
+                if (!quiet) {
                 T b1 = gn.x - gs.x;
                 T b2 = (gn.y - gs.z) + fcya;
                 T b3 = gn.w - gs.w;
-                T hs = ra.h - dtdx * a1q[0] - dtdy * b1;
-                T qxs = ra.qx - dtdx * a2q[0] - dtdy * b3;
-                T qys = ra.qy - dtdx * a3q[0] - dtdy * b2;
+                hs = ra.h - dtdx * a1q[0] - dtdy * b1;
+                qxs = ra.qx - dtdx * a2q[0] - dtdy * b3;
+                qys = ra.qy - dtdx * a3q[0] - dtdy * b2;
+                }
                 size_t o = pidx(P, gi, ro);
-                if (hs > C.hdry) {
+                if (quiet) {
+                } else if (hs > C.hdry) {
                     if (P.friction != SWOF_FRIC_NONE) {
                         // q / (1 + dt g C_f |u^s| / h*^p), p = 4/3 (Manning,
                         // Strickler) or 1 (Darcy-Weisbach, Chezy), Sec. 2.1, 3.2
@@ -320,6 +340,11 @@ __device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, 
                 if (ro == P.ny - 1 && P.bc[3] != SWOF_BC_WALL) outacc += gn.x * cdx;
                 if (STAGE == 1) {
                     store_cell<T>(P, F.h1, F.qx1, F.qy1, gi, ro, hs, qxs, qys);
+                } else if (quiet && !rain && !P.infiltration && (bits(c_h) | bits(c_qx) | bits(c_qy)) == 0ull) {
+                    // ... and with U^n = (+0, +0, +0), no rain and no
+                    // infiltration U^{n+1} is (+0, +0, +0) (the Heun average
+                    // of zeros; below h_dry)
+                    store_cell<T>(P, F.h, F.qx, F.qy, gi, ro, T(0), T(0), T(0));
                 } else {
                     T hn = T(0.5) * (c_h + hs);
                     T qxn = T(0.5) * (c_qx + qxs);
@@ -360,7 +385,7 @@ __device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, 
                 buf[t] = {fh, fu, fv, frh};
                 // all three rows of U^{n+1} dry across the CTA: every speed is 0
                 // (the same vote tells the tile flags whether the tile holds water)
-                const bool alldry = DRY_SKIP ? cta_and<NTX>(fh == T(0) && y1h == T(0) && y2h == T(0))
+                const bool alldry = DRY_SKIP ? cta_and<NTX>(is0(fh) && is0(y1h) && is0(y2h))
                                              : (cta_sync<NTX>(), false);
                 anywet |= !alldry;
                 if (!alldry && out_col && ro < P.ny) {
