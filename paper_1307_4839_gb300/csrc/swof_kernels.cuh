@@ -8,15 +8,22 @@
 //   k_sweep<1>: U* = U^n + dt Phi(U^n) -- boundary values, MUSCL-minmod
 //               (Sec. 3.4), hydrostatic reconstruction + HLL + S_L/S_R/Fc
 //               (Sec. 3.1, 3.3), scheme Eq. (SW1Dscheme) in x and y,
-//               semi-implicit Manning friction (Sec. 3.2).  Writes U* and
-//               its ghost cells.
+//               semi-implicit friction (Sec. 3.2, the laws of Sec. 2.1).
+//               Writes U* and its ghost cells (imposed edges: the boundary
+//               state of Sec. 2.2).
 //   k_sweep<2>: the same on U*, then the Heun average with U^n (in place),
-//               rain, Green-Ampt (Sec. 3.5), the dry clean-up and ghosts.
+//               rain, Green-Ampt (Sec. 3.5), the dry clean-up and ghosts,
+//               and the wave speeds of U^{n+1} inside its tile; the next
+//               step's first launch (k_lambda_ring) adds the tile edges.
 // The stage kernels walk columns down the grid (swof_sweep.cuh): every cell
-// is reconstructed once per direction, every face flux computed once.
+// is reconstructed once per direction, every face flux computed once.  The
+// first-order step (Sec. 3.3) is the stage with face values = cell values
+// followed by k_commit1 (sources, ghosts, speeds).
 //
 // FP64 (T = double): every expression follows the oracle's operation order
-// and is compiled with -fmad=false, so results match it bit for bit.
+// and is compiled with -fmad=false, so results match it bit for bit; where a
+// dry cell's result is known exactly (+0 fluxes, +0 state) the arithmetic
+// that would produce it is skipped.
 // FP32 (T = float): bulk arithmetic in FP32; z enters only as per-face
 // differences dz (precomputed in FP64), the hydrostatic reconstruction in
 // difference form h_L = max(0, h_- - max(0, z_+ - z_-)), which is the
@@ -600,36 +607,40 @@ __global__ void __launch_bounds__(NT) k_lambda_ring(Params P, Fields<T> F)
     if (ctl->status) return;
     const Scal<T> C = scal<T>(P);
     K kx = 0, ky = 0;
-    // x speeds on the ring columns of every row: each thread keeps one ring
-    // column and walks rows (no index division inside the loops)
+    // Items: groups of rows for the x speeds on the ring columns (each thread
+    // keeps one ring column), then (ring row, NT-column chunk) pairs for the
+    // y speeds; blocks stride over both in one loop so the work is balanced.
+    // One division per item, none per cell.
     const int nc = F.n_ring_cols;
-    if (nc > 0) {
-        const int rows_per = NT / nc > 0 ? NT / nc : 1;
-        const int tr = threadIdx.x / nc, c = threadIdx.x % nc;
-        if (tr < rows_per)
-            for (int gj = blockIdx.x * rows_per + tr; gj < P.ny; gj += gridDim.x * rows_per)
-                for (int cc = c; cc < nc; cc += NT) {
-                    const int gi = F.ring_cols[cc];
-                    V4<T> w = cell_rec(P, F, gi - 1, gj, C.hdry), m = cell_rec(P, F, gi, gj, C.hdry),
-                          e = cell_rec(P, F, gi + 1, gj, C.hdry);
-                    kx = kmax(kx, speed_key(cell_speed(w.x, m.x, e.x, w.y, m.y, e.y, m.w, C.hdry, C.g)));
-                    if (gi == 0 && P.bc[0] >= SWOF_BC_IMPOSED_H) kx = kmax(kx, speed_key(ab(w.y) + sq(C.g * w.x)));
-                    if (gi == P.nx - 1 && P.bc[1] >= SWOF_BC_IMPOSED_H)
-                        kx = kmax(kx, speed_key(ab(e.y) + sq(C.g * e.x)));
-                }
-    }
-    // y speeds on the ring rows: blocks over (ring row, NT-column chunk)
-    // items (one division per item, not per cell), threads along the chunk
+    const int rows_per = nc > 0 ? (NT / nc > 0 ? NT / nc : 1) : 1;
+    const int tr = nc > 0 ? threadIdx.x / nc : 0, c = nc > 0 ? threadIdx.x % nc : 0;
+    const int items_x = nc > 0 ? (P.ny + rows_per - 1) / rows_per : 0;
     const int chunks = (P.nx + NT - 1) / NT;
-    for (int it = blockIdx.x; it < F.n_ring_rows * chunks; it += gridDim.x) {
-        const int q = it / chunks, gi = (it - q * chunks) * NT + threadIdx.x;
-        if (gi >= P.nx) continue;
-        const int gj = F.ring_rows[q];
-        V4<T> s_ = cell_rec(P, F, gi, gj - 1, C.hdry), m = cell_rec(P, F, gi, gj, C.hdry),
-              n = cell_rec(P, F, gi, gj + 1, C.hdry);
-        ky = kmax(ky, speed_key(cell_speed(s_.x, m.x, n.x, s_.z, m.z, n.z, m.w, C.hdry, C.g)));
-        if (gj == 0 && P.bc[2] >= SWOF_BC_IMPOSED_H) ky = kmax(ky, speed_key(ab(s_.z) + sq(C.g * s_.x)));
-        if (gj == P.ny - 1 && P.bc[3] >= SWOF_BC_IMPOSED_H) ky = kmax(ky, speed_key(ab(n.z) + sq(C.g * n.x)));
+    const int items = items_x + F.n_ring_rows * chunks;
+    for (int it = blockIdx.x; it < items; it += gridDim.x) {
+        if (it < items_x) {
+            const int gj = it * rows_per + tr;
+            if (tr >= rows_per || gj >= P.ny) continue;
+            for (int cc = c; cc < nc; cc += NT) {
+                const int gi = F.ring_cols[cc];
+                V4<T> w = cell_rec(P, F, gi - 1, gj, C.hdry), m = cell_rec(P, F, gi, gj, C.hdry),
+                      e = cell_rec(P, F, gi + 1, gj, C.hdry);
+                kx = kmax(kx, speed_key(cell_speed(w.x, m.x, e.x, w.y, m.y, e.y, m.w, C.hdry, C.g)));
+                if (gi == 0 && P.bc[0] >= SWOF_BC_IMPOSED_H) kx = kmax(kx, speed_key(ab(w.y) + sq(C.g * w.x)));
+                if (gi == P.nx - 1 && P.bc[1] >= SWOF_BC_IMPOSED_H)
+                    kx = kmax(kx, speed_key(ab(e.y) + sq(C.g * e.x)));
+            }
+        } else {
+            const int iy = it - items_x;
+            const int q = iy / chunks, gi = (iy - q * chunks) * NT + threadIdx.x;
+            if (gi >= P.nx) continue;
+            const int gj = F.ring_rows[q];
+            V4<T> s_ = cell_rec(P, F, gi, gj - 1, C.hdry), m = cell_rec(P, F, gi, gj, C.hdry),
+                  n = cell_rec(P, F, gi, gj + 1, C.hdry);
+            ky = kmax(ky, speed_key(cell_speed(s_.x, m.x, n.x, s_.z, m.z, n.z, m.w, C.hdry, C.g)));
+            if (gj == 0 && P.bc[2] >= SWOF_BC_IMPOSED_H) ky = kmax(ky, speed_key(ab(s_.z) + sq(C.g * s_.x)));
+            if (gj == P.ny - 1 && P.bc[3] >= SWOF_BC_IMPOSED_H) ky = kmax(ky, speed_key(ab(n.z) + sq(C.g * n.x)));
+        }
     }
     kx = block_max(kx, red[0]);
     ky = block_max(ky, red[1]);

@@ -15,7 +15,9 @@
 // Every input cell is read from HBM once (next row prefetched), every output
 // written once.  The per-cell arithmetic is exactly the one of the oracle
 // (same functions, same operation order), so the FP64 instantiation stays
-// bit-identical to it.
+// bit-identical to it; work whose result is known exactly is skipped: the x
+// part of a row dry across the CTA, the y part of a column window of three
+// dry cells, and (FP64) the update of a dry cell whose fluxes are all +0.
 #pragma once
 
 namespace swof {
