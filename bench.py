@@ -11,8 +11,11 @@ Our arm times the CUDA path (libswof through its C ABI) with CUDA events on
 the stream the kernels run on; the state of the valley flood evolves over
 the warm-up and timed steps.  The headline is the FP32 bulk path; the FP64
 path (bit-identical to the oracle) is timed on the same workload and
-reported under "variants".  --impl reference times the CPU oracle (the
-plain FP64 C implementation, all host cores) on the same workload.
+reported under "variants", beside the fully wet valley, dry-tile skipping
+(all cells still counted; its final state must equal the full step's), the
+first-order step, D8 flow directions on a 16384^2 DEM, the 256-member
+ensemble and the learned surrogate.  --impl reference times the CPU oracle
+(the plain FP64 C implementation, all host cores) on the same workload.
 With N > 1 (torchrun) every rank runs its own replica of the grid: the path
 is one grid per GPU, so N GPUs process N grids ("replicas only").
 """
