@@ -290,3 +290,46 @@ def test_d8_full_size_sampled_rows():
     for j in rows:
         a, b = max(j - 1, 0), min(j + 2, n)      # the row with all of its neighbour rows
         assert np.array_equal(d[j], oracle.d8(z[a:b])[j - a]), j
+
+
+# ------------------------------------------------------------------ the bench's size
+
+def test_fp64_full_size_first_order_with_imposed_edge_bitwise():
+    """The 4096^2 valley at first order (n_CFL 1) with an imposed inflow on
+    the west edge and an imposed depth on the east edge, against the oracle
+    over its first 3 steps (whole grid, bit for bit)."""
+    w = si.valley(4096)
+    over = dict(order=sw.ORDER_1, cfl=1.0, bc=(3, 2, 0, 1), bc_q=(0.5, 0, 0, 0), bc_h=(0, 0.2, 0, 0))
+    o, s, dts = pair(w, 3, **over)
+    assert_bitwise(o, s, dts)
+
+
+def test_fp32_full_size_first_order_against_oracle_dt():
+    """The first-order FP32 variant the benchmark times, on the oracle's dt:
+    relative L1 of h <= 1e-5 and of the down-valley discharge <= 1e-4."""
+    w = si.valley(4096)
+    o, s, _ = pair(w, 6, sw.FP32, order=sw.ORDER_1, cfl=1.0)
+    (h, qx, qy), (oh, oqx, oqy) = s.state(), o.state()
+    assert rel_l1(h, oh) <= 1e-5 and rel_l1(qy, oqy) <= 1e-4
+    assert h.min() >= 0.0
+
+
+def test_full_size_dry_tile_skip_equals_full_step():
+    """Dry-tile skipping on the benchmark's 4096^2 valley (FP32, the shape
+    skipping selects): 60 steps give the full step's state and dt sequence
+    bit for bit."""
+    w = si.valley(4096)
+    res = []
+    for skip in (False, True):
+        s = sw.Solver.from_workload(w, sw.FP32)
+        if skip:
+            s.set_dry_tile_skip(True)
+        for _ in range(3):
+            assert s.step(20).status == 0
+        res.append((s.state(), s.dt_history(), s.tile_activity() if skip else None))
+        s.close()
+    for a, b in zip(res[0][0], res[1][0]):
+        assert np.array_equal(a, b)
+    assert np.array_equal(res[0][1], res[1][1])
+    live, total = res[1][2]
+    assert 0 < live < 0.2 * total
