@@ -11,9 +11,10 @@ Our arm times the CUDA path (libswof through its C ABI) with CUDA events on
 the stream the kernels run on; the state of the valley flood evolves over
 the warm-up and timed steps.  The headline is the FP32 bulk path; the FP64
 path (bit-identical to the oracle) is timed on the same workload and
-reported under "variants", beside the fully wet valley, dry-tile skipping
-(all cells still counted; its final state must equal the full step's), the
-first-order step, D8 flow directions on a 16384^2 DEM, the 256-member
+reported under "variants", beside the fully wet valley in FP32 and FP64
+(with an ALU roofline: the operation census's arithmetic per cell-update
+over the lanes' operation rate), dry-tile skipping (all cells still
+counted; its final state must equal the full step's), the first-order step, D8 flow directions on a 16384^2 DEM, the 256-member
 ensemble and the learned surrogate.  --impl reference times the CPU oracle
 (the plain FP64 C implementation, all host cores) on the same workload.
 With N > 1 (torchrun) every rank runs its own replica of the grid: the path
@@ -123,6 +124,37 @@ def recorded_metric(kernel: str, precision: str, tile, name: str):
         return float(vals[name])
     except Exception:
         return None
+
+
+def census_per_update(case: str) -> dict | None:
+    """Operations per cell-update of one step of the scheme, by kind, from
+    the committed operation census of the 4096^2 valley (the oracle's
+    arithmetic with each value computed once), or None."""
+    f = os.path.join(ROOT, "profiles", "op_census_valley4096.txt")
+    try:
+        for line in open(f):
+            if line.startswith(case + ":"):
+                return {k: float(v) for k, v in (t.split("=") for t in line.split(":", 1)[1].split())}
+    except Exception:
+        return None
+    return None
+
+
+def alu_roofline(precision: str, gcells: float, mhz: float) -> dict | None:
+    """ALU roofline of a fully wet step: the census's arithmetic operations
+    (add, mul, div, sqrt, cube root; each counted once) per cell-update
+    times the measured rate, over the lanes' operation rate at the sampled
+    SM clock: FP32 152 SMs x 128 lanes; FP64 the nominal 1.25 TFLOP/s
+    (an FMA counted as 2) as 0.625 T lane operations per second at
+    2070 MHz, scaled to the clock."""
+    c = census_per_update("fully_wet")
+    if not c or not gcells:
+        return None
+    peak = 152 * 128 * mhz * 1e6 if precision == "fp32" else 1.25e12 / 2 * (mhz / 2070.0)
+    ach = c["flops"] * gcells * 1e9
+    return {"bound": "alu", "achieved": ach * 1e-12, "peak": peak * 1e-12, "unit": "T lane-ops/s",
+            "frac": ach / peak, "ops_per_cell_update": c["flops"], "all_ops_per_cell_update": c["all"],
+            "sm_mhz": mhz, "census": "profiles/op_census_valley4096.txt"}
 
 
 def bf16_peak() -> float:
@@ -779,8 +811,22 @@ def main():
             "value": vw, "unit": UNIT, "ms_per_step": msw / kw_, "steps": kw_,
             "kernel_ms": {kk: round(v, 5) for kk, v in avgw.items()},
             "stage2_hbm_frac": BYTES["fp32"]["stage2"] * cells / (avgw["stage2"] * 1e-3) * 1e-9 / hbm,
+            "alu": alu_roofline("fp32", vw, mhz),
             "what": "valley DEM with 0.5 m of water added to every cell"}
         del sw_
+        if not args.no_fp64:
+            # FP64 fully wet: every cell does the whole scheme, so the FP64
+            # pipe bounds it; fixed tile shape (the FP64 valley's default)
+            kw64 = 10
+            ms6, t6, _, _, s6 = measure(sw, torch, wet, "fp64", kw64, 3, ws, None, False, 0)
+            ms6 = max_over_ranks(ms6, ws)
+            v6 = ws * cells / (ms6 / kw64 * 1e-3) * 1e-9
+            variants["fp64_fully_wet"] = {
+                "value": v6, "unit": UNIT, "ms_per_step": ms6 / kw64, "steps": kw64,
+                "kernel_ms": {kk: round(t6[kk + "_ms"] / kw64, 4) for kk in ("lambda", "stage1", "stage2")},
+                "alu": alu_roofline("fp64", v6, mhz),
+                "what": "valley DEM with 0.5 m of water added to every cell"}
+            del s6
 
     if P == "fp32" and not args.no_skip:
         # the same workload with dry-tile skipping (all cells still counted):
