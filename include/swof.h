@@ -190,7 +190,9 @@ SWOF_API int swof_step(swof_ctx *ctx, int n, swof_step_info *info);
 
 /* Replay the given dt values (host, copied) for the next n steps instead of
  * Eq. (cfl), e.g. the oracle's sequence for parity.  n = 0 switches replay
- * off.  Running past the end latches SWOF_EDTSEQ. */
+ * off.  Running past the end latches SWOF_EDTSEQ.  Errors: SWOF_EINVAL,
+ * SWOF_ENONFINITE (a value is not finite), SWOF_ENOMEM, SWOF_ECUDA; a call
+ * that fails leaves the previous replay (or none) in place. */
 SWOF_API int swof_set_dt_sequence(swof_ctx *ctx, const double *dts, int n);
 
 /* dt of each step taken so far (up to max values, oldest first) into host
@@ -240,7 +242,8 @@ SWOF_API int swof_get_max_depth(swof_ctx *ctx, double *hmax);
  * steps are not recorded).  Replaces earlier gauges; n = 0 switches them
  * off.  swof_get_gauges copies up to max_records records of 1 + 3n doubles
  * (t, then h, hu, hv per gauge) to host out and the number recorded to
- * *count.  Synchronises.  Errors: SWOF_EINVAL (cell outside the grid). */
+ * *count.  Synchronises.  Errors: SWOF_EINVAL (cell outside the grid; the
+ * earlier gauges stay), SWOF_ENOMEM / SWOF_ECUDA (gauges end up off). */
 SWOF_API int swof_set_gauges(swof_ctx *ctx, const int *cells, int n, int capacity);
 SWOF_API int swof_get_gauges(swof_ctx *ctx, double *out, int max_records, int *count);
 

@@ -352,10 +352,11 @@ class Solver:
 
     def set_gauges(self, cells, capacity: int):
         ij = np.ascontiguousarray(np.asarray(cells, dtype=np.int32).reshape(-1, 2))
-        self._n_gauges = int(ij.shape[0])
-        self._gauge_cap = int(capacity)
+        n = int(ij.shape[0])
         _check(load().swof_set_gauges(self._ctx, ij.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
-                                      self._n_gauges, int(capacity)), "swof_set_gauges")
+                                      n, int(capacity)), "swof_set_gauges")
+        self._n_gauges = n                  # (a rejected call keeps the earlier gauges)
+        self._gauge_cap = int(capacity)
 
     def gauges(self) -> np.ndarray:
         """Records [n][1 + 3G]: t, then h, hu, hv at each gauge."""

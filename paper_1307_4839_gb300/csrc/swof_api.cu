@@ -497,13 +497,18 @@ __global__ void k_check_state(const double *s, long long n, int *flag)
 // first use, kept until destroy).
 static int ensure_staging(swof_ctx *c)
 {
-    if (c->staging) return SWOF_OK;
+    if (c->staging && c->d_flag) return SWOF_OK;
     const size_t n = (size_t)c->P.nx * c->P.ny;
-    if (cudaMalloc(&c->staging, 3 * n * sizeof(double)) != cudaSuccess) {
+    if (!c->staging && cudaMalloc(&c->staging, 3 * n * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
         c->staging = nullptr;
         return SWOF_ENOMEM;
     }
-    if (cudaMalloc(&c->d_flag, sizeof(int)) != cudaSuccess) return SWOF_ENOMEM;
+    if (!c->d_flag && cudaMalloc(&c->d_flag, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        c->d_flag = nullptr;
+        return SWOF_ENOMEM;
+    }
     return SWOF_OK;
 }
 
@@ -654,22 +659,33 @@ int swof_step(swof_ctx *c, int n, swof_step_info *info)
 int swof_set_dt_sequence(swof_ctx *c, const double *dts, int n)
 {
     if (!c || n < 0 || (n > 0 && !dts)) return SWOF_EINVAL;
+    if (n > 0 && !all_finite(dts, (size_t)n)) return SWOF_ENONFINITE;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SWOF_ECUDA;
-    if (c->dt_seq) cudaFree(c->dt_seq);
-    c->dt_seq = nullptr;
-    c->dt_seq_n = 0;
+    // the new sequence is complete on the device before the old one is
+    // released: a call that fails leaves the replay as it was
+    double *p = nullptr;
     if (n > 0) {
-        if (!all_finite(dts, (size_t)n)) return SWOF_ENONFINITE;
-        if (cudaMalloc(&c->dt_seq, (size_t)n * sizeof(double)) != cudaSuccess) return SWOF_ENOMEM;
-        if (cudaMemcpy(c->dt_seq, dts, (size_t)n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+        if (cudaMalloc(&p, (size_t)n * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return SWOF_ENOMEM;
+        }
+        if (cudaMemcpy(p, dts, (size_t)n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaFree(p);
             return SWOF_ECUDA;
-        c->dt_seq_n = n;
+        }
     }
     int v[2] = {0, n};
     cudaError_t e = cudaMemcpyAsync(&c->ctl->dt_seq_pos, v, sizeof v, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        if (p) cudaFree(p);
+        return SWOF_ECUDA;
+    }
+    if (c->dt_seq) cudaFree(c->dt_seq);
+    c->dt_seq = p;
+    c->dt_seq_n = n;
     set_hist(c);
-    return cuda_err(e);
+    return SWOF_OK;
 }
 
 int swof_get_dt_history(swof_ctx *c, double *out, int max, int *count)
@@ -847,23 +863,37 @@ int swof_set_gauges(swof_ctx *c, const int *cells, int n, int capacity)
         F.n_gauges = c->n_gauges;
         F.gauge_cap = c->gauge_cap;
     };
+    // any failure below leaves the gauges off (nothing allocated, no offsets
+    // for the kernel to read)
+    auto drop = [&]() {
+        if (c->d_gauge_off) cudaFree(c->d_gauge_off);
+        if (c->d_gauge_rec) cudaFree(c->d_gauge_rec);
+        c->d_gauge_off = nullptr;
+        c->d_gauge_rec = nullptr;
+    };
     cudaError_t e = cudaMemsetAsync(&c->ctl->gauge_n, 0, sizeof(long long), c->stream);
+    int st = SWOF_OK;
     if (n > 0 && e == cudaSuccess) {
         if (cudaMalloc(&c->d_gauge_off, (size_t)n * sizeof(long long)) != cudaSuccess ||
             cudaMalloc(&c->d_gauge_rec, (size_t)capacity * (1 + 3 * (size_t)n) * sizeof(double)) != cudaSuccess) {
-            wire(c->f64);
-            wire(c->f32);
-            return SWOF_ENOMEM;
+            cudaGetLastError();
+            drop();
+            st = SWOF_ENOMEM;
+        } else {
+            e = cudaMemcpyAsync(c->d_gauge_off, off.data(), (size_t)n * sizeof(long long), cudaMemcpyHostToDevice,
+                                c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (e == cudaSuccess) {
+                c->n_gauges = n;
+                c->gauge_cap = capacity;
+            } else {
+                drop();
+            }
         }
-        e = cudaMemcpyAsync(c->d_gauge_off, off.data(), (size_t)n * sizeof(long long), cudaMemcpyHostToDevice,
-                            c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        c->n_gauges = n;
-        c->gauge_cap = capacity;
     }
     wire(c->f64);
     wire(c->f32);
-    return cuda_err(e);
+    return st != SWOF_OK ? st : cuda_err(e);
 }
 
 int swof_get_gauges(swof_ctx *c, double *out, int max_records, int *count)
@@ -893,10 +923,18 @@ int swof_set_dry_tile_skip(swof_ctx *c, int on)
         c->f64.tile_live = c->f32.tile_live = nullptr;
         return SWOF_OK;
     }
-    if (!c->d_tile_act) {
-        if (cudaMalloc(&c->d_tile_act, (size_t)c->nslots) != cudaSuccess ||
-            cudaMalloc(&c->d_tile_live, (size_t)c->nslots) != cudaSuccess)
+    // both flag arrays or neither (a stage kernel reads both when skipping)
+    if (!c->d_tile_act || !c->d_tile_live) {
+        unsigned char *a = nullptr, *b = nullptr;
+        if (cudaMalloc(&a, (size_t)c->nslots) != cudaSuccess || cudaMalloc(&b, (size_t)c->nslots) != cudaSuccess) {
+            cudaGetLastError();
+            if (a) cudaFree(a);
             return SWOF_ENOMEM;
+        }
+        if (c->d_tile_act) cudaFree(c->d_tile_act);
+        if (c->d_tile_live) cudaFree(c->d_tile_live);
+        c->d_tile_act = a;
+        c->d_tile_live = b;
     }
     c->skip_dry = true;
     c->f64.tile_act = c->f32.tile_act = c->d_tile_act;

@@ -208,6 +208,43 @@ def test_fp32_gauges_follow_state():
     assert np.array_equal(s.max_depth(), hm)
 
 
+def test_rejected_gauges_keep_the_earlier_ones():
+    """A gauge set with a cell outside the grid is rejected before anything
+    changes: the earlier gauges go on recording."""
+    w = si.random_state(40, 30, seed=62, dry_frac=0.2)
+    s = sw.Solver.from_workload(w, sw.FP64)
+    s.set_gauges([(3, 4)], 10)
+    with pytest.raises(sw.SwofError) as e:
+        s.set_gauges([(3, 4), (40, 0)], 10)          # i = nx: outside
+    assert e.value.code == sw.EINVAL
+    for _ in range(3):
+        s.step(1)
+    g = s.gauges()
+    h, qx, qy = s.state()
+    assert g.shape == (3, 4)
+    assert g[-1][1] == h[4, 3] and g[-1][2] == qx[4, 3] and g[-1][3] == qy[4, 3]
+
+
+def test_rejected_dt_sequence_keeps_the_previous_replay():
+    """A replay rejected for a non-finite value changes nothing: the steps
+    that follow take the earlier sequence (the oracle's, so the state is
+    bit for bit the oracle's), and running past its end latches
+    SWOF_EDTSEQ."""
+    w = si.random_state(40, 30, seed=61, dry_frac=0.2)
+    o = oracle.Oracle.from_workload(w)
+    dts = o.step(4)
+    s = sw.Solver.from_workload(w, sw.FP64)
+    s.set_dt_sequence(dts)
+    with pytest.raises(sw.SwofError) as e:
+        s.set_dt_sequence([1e-3, float("nan")])
+    assert e.value.code == sw.ENONFINITE
+    assert s.step(4).status == 0
+    assert_bitwise(o, s, dts)
+    with pytest.raises(sw.SwofError) as e:
+        s.step(1)
+    assert e.value.code == sw.EDTSEQ
+
+
 # ------------------------------------------------------------------ dry-tile skipping
 
 @pytest.mark.parametrize("precision", [sw.FP64, sw.FP32])
