@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -222,22 +223,47 @@ __global__ void k_target(const float *in, int nin, const float *next, int nout, 
 inline int grid_for(long long n) { long long g = (n + 255) / 256; return (int)(g < 152 * 16 ? (g > 0 ? g : 1) : 152 * 16); }
 
 // ---------------------------------------------------------------------------
-// Launchers of the tensor-core kernels
+// Launchers of the tensor-core kernels.  Each keeps, per device, the
+// dynamic shared memory it has opted its kernel into and the resident CTAs
+// of the whole GPU (persistent grids); the first launch on a device sets
+// them, under one lock so that host threads may share the library.
+constexpr int MAX_DEVICES = 64;
+std::mutex g_launch_attr_lock;
+
+inline int current_device()
+{
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= MAX_DEVICES) d = 0;
+    return d;
+}
+
+// resident CTAs of kernel f on device dev at `threads` threads and `smem`
+// bytes of dynamic shared memory (at least one per SM)
+template <typename Kern>
+int resident_ctas(Kern f, int threads, size_t smem, int dev)
+{
+    int n = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, smem) != cudaSuccess || n < 1) n = 1;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return n * (sms > 0 ? sms : 152);
+}
+
 template <int NT>
 int conv_launch(const ConvArgs &A, cudaStream_t s)
 {
     size_t smem = ConvCfg<NT>::SMEM;
-    static int per_sm = 0;         // resident CTAs per SM (persistent grid)
-    if (!per_sm) {
-        if (cudaFuncSetAttribute(k_conv<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-            return SWOF_ECUDA;
-        int n = 0, dev = 0, sms = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_conv<NT>, ConvCfg<NT>::THREADS, smem) != cudaSuccess ||
-            n < 1)
-            n = 1;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        per_sm = n * (sms > 0 ? sms : 152);
+    static int per_dev[MAX_DEVICES] = {};   // resident CTAs of the GPU (persistent grid)
+    const int dev = current_device();
+    int per_sm;
+    {
+        std::lock_guard<std::mutex> g(g_launch_attr_lock);
+        if (!per_dev[dev]) {
+            if (cudaFuncSetAttribute(k_conv<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess)
+                return SWOF_ECUDA;
+            per_dev[dev] = resident_ctas(k_conv<NT>, ConvCfg<NT>::THREADS, smem, dev);
+        }
+        per_sm = per_dev[dev];
     }
     long long M = (long long)A.B * A.H * A.W;
     long long tiles = (M + 127) / 128;
@@ -257,17 +283,17 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
 
 EncodeTiledFn encode_tiled()
 {
-    static EncodeTiledFn fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
+    // looked up once per process (a function-local static is initialised
+    // once even with several host threads)
+    static const EncodeTiledFn fn = []() -> EncodeTiledFn {
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(p);
-    }
+            return reinterpret_cast<EncodeTiledFn>(p);
+        return nullptr;
+    }();
     return fn;
 }
 
@@ -289,23 +315,23 @@ int conv_halo_launch(const ConvArgs &A, cudaStream_t s)
     const int stages = Cfg::stages(A.Kp);
     if (stages < 2) return SWOF_EINVAL;
     const size_t smem = Cfg::smem(A.Kp, stages);
-    static int per_sm = 0;
-    static size_t smem_set = 0;
-    if (smem > smem_set) {
-        if (cudaFuncSetAttribute(k_conv_halo<NT, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-            return SWOF_ECUDA;
-        smem_set = smem;
-        per_sm = 0;
-    }
-    if (!per_sm) {
-        int n = 0, dev = 0, sms = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_conv_halo<NT, CB>, Cfg::THREADS, smem) != cudaSuccess ||
-            n < 1)
-            n = 1;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        per_sm = n * (sms > 0 ? sms : 152);
+    // the opt-in grows to the largest stage count asked for so far; the
+    // resident CTAs are those of the size set last
+    static int per_dev[MAX_DEVICES] = {};
+    static size_t smem_set[MAX_DEVICES] = {};
+    const int dev = current_device();
+    int per_sm;
+    {
+        std::lock_guard<std::mutex> g(g_launch_attr_lock);
+        if (smem > smem_set[dev]) {
+            if (cudaFuncSetAttribute(k_conv_halo<NT, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess)
+                return SWOF_ECUDA;
+            smem_set[dev] = smem;
+            per_dev[dev] = 0;
+        }
+        if (!per_dev[dev]) per_dev[dev] = resident_ctas(k_conv_halo<NT, CB>, Cfg::THREADS, smem, dev);
+        per_sm = per_dev[dev];
     }
     const long long tiles = (long long)A.B * A.H * A.W / 128;
     const long long gy = A.ntot / NT;
@@ -342,18 +368,18 @@ int conv_tma_launch(const ConvArgs &A, cudaStream_t s)
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
         CUDA_SUCCESS)
         return SWOF_ECUDA;
-    static int per_sm = 0;
-    if (!per_sm) {
-        if (cudaFuncSetAttribute(k_conv_tma<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM) !=
-            cudaSuccess)
-            return SWOF_ECUDA;
-        int n = 0, dev = 0, sms = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_conv_tma<NT>, Cfg::THREADS, Cfg::SMEM) != cudaSuccess ||
-            n < 1)
-            n = 1;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        per_sm = n * (sms > 0 ? sms : 152);
+    static int per_dev[MAX_DEVICES] = {};
+    const int dev = current_device();
+    int per_sm;
+    {
+        std::lock_guard<std::mutex> g(g_launch_attr_lock);
+        if (!per_dev[dev]) {
+            if (cudaFuncSetAttribute(k_conv_tma<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM) !=
+                cudaSuccess)
+                return SWOF_ECUDA;
+            per_dev[dev] = resident_ctas(k_conv_tma<NT>, Cfg::THREADS, Cfg::SMEM, dev);
+        }
+        per_sm = per_dev[dev];
     }
     const long long tiles = (long long)A.B * A.H * A.W / 128;
     const long long gy = A.ntot / NT;
