@@ -282,6 +282,30 @@ def test_fp32_full_size_valley_4096_against_oracle_dt():
     assert abs(d["volume"] + d["outflow"] - v0) <= 1e-6 * v0
 
 
+def test_fp32_valley_4096_at_its_end_time():
+    """The FP32 path over the whole valley run (2000 steps, t = 36 s) on the
+    FP64 path's dt sequence, against the FP64 path (bit for bit the
+    oracle's: test_fp64_full_size_valley_4096_first_steps_bitwise and the
+    ragged-grid tests; the oracle itself would take minutes here).  Relative
+    L1 at the end: h and the down-valley discharge hv within the 1e-5 FP32
+    target (measured 1.9e-6 and 8.0e-6); the cross-valley discharge hu,
+    ~0 in the exact solution, at FP32 roundoff over a near-zero total
+    (measured 1.95e-5, bounded at 3e-5).  Both paths are deterministic."""
+    w = si.valley(4096)
+    s64 = sw.Solver.from_workload(w, sw.FP64)
+    assert s64.step(2000).status == 0
+    dts = s64.dt_history(2000)
+    h64, qx64, qy64 = s64.state()
+    s64.close()
+    s32 = sw.Solver.from_workload(w, sw.FP32)
+    s32.set_dt_sequence(dts)
+    assert s32.step(2000).status == 0
+    h, qx, qy = s32.state()
+    s32.close()
+    assert rel_l1(h, h64) <= 1e-5 and rel_l1(qy, qy64) <= 1e-5 and rel_l1(qx, qx64) <= 3e-5
+    assert h.min() >= 0.0
+
+
 def test_fp32_dam_break_200_rel_l1():
     w = si.dam_break(200)
     o = oracle.Oracle.from_workload(w)
