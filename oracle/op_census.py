@@ -34,9 +34,15 @@ resulting state matches the oracle's bit for bit (ties of signed zeros
 aside), and the counts equal those of a scalar restatement whose number
 type counts its own operations (tests/test_op_census.py).
 
-Supported: order 2, wall and free-outflow edges, no friction or one of the
-four laws with a scalar coefficient, uniform rain on or off; no
-infiltration, no imposed edges.
+At first order (Sec. 3.3) the face values are the cell values (no
+reconstruction arithmetic), the wave speeds are taken on them, and one
+Euler stage replaces the two Heun stages.  Green-Ampt infiltration
+(Sec. 3.5) is counted per cell after the rain, with the step's
+infiltration sum.
+
+Supported: order 1 or 2, wall and free-outflow edges, no friction or one of
+the four laws with a scalar coefficient, uniform rain on or off,
+Green-Ampt with a scalar or per-cell K_s; no imposed edges.
 """
 from __future__ import annotations
 
@@ -237,9 +243,17 @@ class Census:
     """The state of one run and the counts of the steps taken so far."""
 
     def __init__(self, z, h, qx, qy, dx, dy, *, g=9.81, h_dry=1e-6, bc=(0, 0, 0, 0), friction=0,
-                 friction_coef=0.0, cfl=0.5, dt_max=0.1, rain_rate=0.0):
+                 friction_coef=0.0, cfl=0.5, dt_max=0.1, rain_rate=0.0, order=2, infiltration=False,
+                 ks=0.0, ks_map=None, psi=0.0, dtheta=0.0, vinf=None):
         if any(b not in (0, 1) for b in bc):
             raise ValueError("the census covers wall and outflow edges only")
+        if order not in (1, 2):
+            raise ValueError("order is 1 or 2")
+        self.order, self.infiltration = int(order), bool(infiltration)
+        self.ks = np.asarray(ks_map, dtype=np.float64) if ks_map is not None else float(ks)
+        self.psi, self.dtheta = float(psi), float(dtheta)
+        self.vinf = (np.array(vinf, dtype=np.float64) if vinf is not None
+                     else np.zeros(np.shape(z), dtype=np.float64))
         self.ny, self.nx = np.shape(z)
         self.dx, self.dy, self.g, self.hdry = float(dx), float(dy), float(g), float(h_dry)
         self.bc, self.friction = tuple(int(b) for b in bc), int(friction)
@@ -259,6 +273,21 @@ class Census:
     def state(self):
         ny, nx = self.ny, self.nx
         return tuple(a[2:ny + 2, 2:nx + 2].copy() for a in (self.h, self.qx, self.qy))
+
+    def _recon1(self, h, u, v):
+        """First order: the face values are the cell values (copies, no
+        arithmetic), over the same cells as the MUSCL reconstruction."""
+        ny, nx, z = self.ny, self.nx, self.z
+        out = []
+        for rows, cols, un, ut in ((slice(2, ny + 2), slice(1, nx + 3), u, v),
+                                   (slice(1, ny + 3), slice(2, nx + 2), v, u)):
+            r = _Rec()
+            r.hm = r.hp = h[rows, cols]
+            r.zm = r.zp = z[rows, cols]
+            r.unm = r.unp = un[rows, cols]
+            r.utm = r.utp = ut[rows, cols]
+            out.append(r)
+        return tuple(out)
 
     def _velocities(self, h, qx, qy):
         T = self.T
@@ -363,27 +392,46 @@ class Census:
         _ghosts(qx0, self.bc, -1.0, 1.0)
         _ghosts(qy0, self.bc, 1.0, -1.0)
         u, v = self._velocities(h0, qx0, qy0)
-        rec = self._recon(h0, u, v)
+        rec = self._recon(h0, u, v) if self.order == 2 else self._recon1(h0, u, v)
         lx, ly = self._lambda(*rec)
         den = lx / self.dx + ly / self.dy
         dt = self.cfl / den if den > 0.0 else self.dt_max
         dt = min(dt, self.dt_max)
         # stage 1 works from the same velocities and reconstruction of U^n
         h1, qx1, qy1 = self._stage(h0, qx0, qy0, dt, (u, v) + rec)
-        p1 = [_pad(a) for a in (h1, qx1, qy1)]
-        _ghosts(p1[0], self.bc, 1.0, 1.0)
-        _ghosts(p1[1], self.bc, -1.0, 1.0)
-        _ghosts(p1[2], self.bc, 1.0, -1.0)
-        h2, qx2, qy2 = self._stage(*p1, dt)
         al = np.ones((ny, nx), dtype=bool)
-        T.c("add", al, 3)
-        T.c("mul", al, 3)
-        hn = 0.5 * (h0[J, I] + h2)
-        qxn = 0.5 * (qx0[J, I] + qx2)
-        qyn = 0.5 * (qy0[J, I] + qy2)
+        if self.order == 1:
+            hn, qxn, qyn = h1, qx1, qy1                # one Euler stage
+        else:
+            p1 = [_pad(a) for a in (h1, qx1, qy1)]
+            _ghosts(p1[0], self.bc, 1.0, 1.0)
+            _ghosts(p1[1], self.bc, -1.0, 1.0)
+            _ghosts(p1[2], self.bc, 1.0, -1.0)
+            h2, qx2, qy2 = self._stage(*p1, dt)
+            T.c("add", al, 3)
+            T.c("mul", al, 3)
+            hn = 0.5 * (h0[J, I] + h2)
+            qxn = 0.5 * (qx0[J, I] + qx2)
+            qyn = 0.5 * (qy0[J, I] + qy2)
         if self.rain > 0.0:
             T.c("add", al)
             hn = hn + dt * self.rain
+        if self.infiltration:
+            # Sec. 3.5: capacity K_s (1 + (psi + h) dtheta / V_inf), all the
+            # water while V_inf = 0; then h, V_inf and the step's sum
+            vi = self.vinf
+            P = vi > 0.0
+            T.c("cmp", al)
+            T.c("add", P, 2)
+            T.c("mul", P, 3)
+            T.c("div", P)
+            T.c("minmax", P)
+            with np.errstate(divide="ignore", invalid="ignore"):
+                ic = self.ks * (1.0 + ((self.psi + hn) * self.dtheta) / np.where(P, vi, 1.0))
+            d = np.where(P, np.fmin(hn, dt * ic), hn)
+            T.c("add", al, 3)
+            hn = hn - d
+            self.vinf = vi + d
         T.c("cmp", al)
         dry = hn <= self.hdry
         qxn = np.where(dry, 0.0, qxn)
@@ -393,19 +441,24 @@ class Census:
         return dt
 
 
-def census(w, steps: int = 1, rain: bool | None = None) -> tuple[Census, list[float]]:
+def census(w, steps: int = 1, rain: bool | None = None, order: int = 2, cfl: float | None = None,
+           vinf=None) -> tuple[Census, list[float]]:
     """Run `steps` counted steps of a workload (an object with nx, ny, dx,
     dy, z, h, qx, qy, bc, friction, manning_n, cfl, dt_max, h_dry,
-    rain_rate); rain is taken as on for every step when rain_rate > 0."""
+    rain_rate, infiltration, ks, psi, dtheta); rain is taken as on for
+    every step when rain_rate > 0; vinf = the infiltrated depth at the
+    start (zero if None)."""
     c = Census(w.z, w.h, w.qx, w.qy, w.dx, w.dy, h_dry=w.h_dry, bc=w.bc, friction=w.friction,
-               friction_coef=w.manning_n, cfl=w.cfl, dt_max=w.dt_max,
-               rain_rate=w.rain_rate if (rain is None or rain) else 0.0)
+               friction_coef=w.manning_n, cfl=cfl if cfl is not None else w.cfl, dt_max=w.dt_max,
+               rain_rate=w.rain_rate if (rain is None or rain) else 0.0, order=order,
+               infiltration=bool(w.infiltration), ks_map=w.ks, psi=w.psi, dtheta=w.dtheta, vinf=vinf)
     dts = [c.step() for _ in range(steps)]
     return c, dts
 
 
 if __name__ == "__main__":
     import argparse
+    import copy
     import os
     import sys
 
@@ -413,22 +466,36 @@ if __name__ == "__main__":
     import swof_inputs as si
 
     ap = argparse.ArgumentParser(description="operation census of the scheme's step")
+    ap.add_argument("--case", default="valley", choices=["valley", "hillslope"])
     ap.add_argument("--side", type=int, default=4096)
     ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--t0", type=float, default=300.0, help="hillslope: start the census at this time")
     a = ap.parse_args()
-    w = si.valley(a.side)
-    cases = [("valley", w)]
-    import copy
-    wet = copy.copy(w)
-    wet.h = w.h + 0.5
-    cases.append(("valley + 0.5 m everywhere (fully wet)", wet))
-    cells = w.nx * w.ny
-    print(f"# operation census of the scheme's step on the {a.side}^2 valley: {a.steps} steps from t = 0,")
+    print(f"# operation census of the scheme's step: {a.case} {a.side}^2, {a.steps} steps")
     print("# operations per cell-update (oracle form, each value computed once; see oracle/op_census.py)")
-    print(f"# command: python -m oracle.op_census --side {a.side} --steps {a.steps}")
+    print(f"# command: python -m oracle.op_census --case {a.case} --side {a.side} --steps {a.steps}"
+          + (f" --t0 {a.t0:g}" if a.case == "hillslope" else ""))
     print("# flops = add + mul + div + sqrt + cbrt; all = every kind; wet = fraction of wet cells at the end")
-    for key, (name, wl) in zip(("valley", "fully_wet"), cases):
-        c, dts = census(wl, a.steps)
+    runs = []
+    if a.case == "valley":
+        w = si.valley(a.side)
+        wet = copy.copy(w)
+        wet.h = w.h + 0.5
+        runs = [("valley", "valley from t = 0", w, 2, None, None),
+                ("fully_wet", "valley + 0.5 m everywhere (fully wet)", wet, 2, None, None),
+                ("valley_order1", "valley from t = 0, first order (n_CFL = 1)", w, 1, 1.0, None)]
+    else:
+        import oracle as orc
+        w = si.hillslope(a.side)
+        o = orc.Oracle.from_workload(w)
+        o.run_to(a.t0)
+        w = copy.copy(w)
+        w.h, w.qx, w.qy = o.state()
+        runs = [("hillslope", f"hillslope with rain and Green-Ampt from the oracle's state at t = {a.t0:g} s",
+                 w, 2, None, o.vinf())]
+    cells = w.nx * w.ny
+    for key, name, wl, order, cfl, vinf in runs:
+        c, dts = census(wl, a.steps, order=order, cfl=cfl, vinf=vinf)
         per = c.T.per(cells * a.steps)
         wetf = float(np.count_nonzero(c.state()[0] > wl.h_dry)) / cells
         print(f"# {name}: dt = " + ", ".join(f"{d:.6g}" for d in dts))

@@ -2,8 +2,9 @@
 
 1. The census's state after each step equals the oracle's bit for bit
    (signed zeros aside) on random wet/dry grids with walls, outflow, each
-   friction law and rain, and its dt sequence equals the oracle's: the
-   census performs the oracle's arithmetic.
+   friction law, rain, Green-Ampt on a K_s map (V_inf too) and at both
+   orders, and its dt sequence equals the oracle's: the census performs
+   the oracle's arithmetic.
 2. Its counts equal, kind by kind, those of a scalar restatement written
    here whose number type counts every operation it executes, the branches
    taken as Python takes them: the census's masks select the right cells.
@@ -122,7 +123,13 @@ class Scalar:
     once (the velocities and reconstruction of U^n shared by the wave
     speeds and stage 1)."""
 
-    def __init__(self, w, friction, coef, rain):
+    def __init__(self, w, friction, coef, rain, order=2, vinf=None):
+        self.order, self.inf = order, bool(w.infiltration)
+        self.ks = w.ks
+        self.psi, self.dtheta = w.psi, w.dtheta
+        self.vinf = [[CF(float(vinf[j][i])) if vinf is not None else Z for i in range(w.nx)]
+                     for j in range(w.ny)]
+        self.infsum = 0.0
         self.nx, self.ny, self.dx, self.dy = w.nx, w.ny, w.dx, w.dy
         self.g, self.hd, self.bc = 9.81, w.h_dry, w.bc
         self.fr = friction
@@ -189,7 +196,23 @@ class Scalar:
             return hmv, hpv, zmv, zpv, unc - a * hu, unc + b * hu, utc - a * ht, utc + b * ht
         return hmv, hpv, zmv, zpv, unc, unc, utc, utc
 
+    def _recon1(self, h, u, v):
+        """first order: face values = cell values (no arithmetic)"""
+        nx, ny, z = self.nx, self.ny, self.z
+        X, Y = {}, {}
+        for j in range(ny):
+            for i in range(-1, nx + 1):
+                c = (j + 2, i + 2)
+                X[i, j] = (h[c[0]][c[1]],) * 2 + (z[c[0]][c[1]],) * 2 + (u[c[0]][c[1]],) * 2 + (v[c[0]][c[1]],) * 2
+        for j in range(-1, ny + 1):
+            for i in range(nx):
+                c = (j + 2, i + 2)
+                Y[i, j] = (h[c[0]][c[1]],) * 2 + (z[c[0]][c[1]],) * 2 + (v[c[0]][c[1]],) * 2 + (u[c[0]][c[1]],) * 2
+        return X, Y
+
     def _recon(self, h, u, v):
+        if self.order == 1:
+            return self._recon1(h, u, v)
         nx, ny = self.nx, self.ny
         X, Y = {}, {}
         for j in range(ny):
@@ -279,21 +302,36 @@ class Scalar:
         den = lx / self.dx + ly / self.dy
         dt = min(self.cfl / den if den > 0.0 else self.dtmax, self.dtmax)
         s1 = self._stage(h, qx, qy, dt, u, v, X, Y)
-        p1 = [self._pad(np.array(a, dtype=object)) for a in s1]
-        self._ghosts(p1[0], 1, 1)
-        self._ghosts(p1[1], -1, 1)
-        self._ghosts(p1[2], 1, -1)
-        u1, v1 = self._vel(*p1)
-        X1, Y1 = self._recon(p1[0], u1, v1)
-        s2 = self._stage(*p1, dt, u1, v1, X1, Y1)
+        if self.order == 2:
+            p1 = [self._pad(np.array(a, dtype=object)) for a in s1]
+            self._ghosts(p1[0], 1, 1)
+            self._ghosts(p1[1], -1, 1)
+            self._ghosts(p1[2], 1, -1)
+            u1, v1 = self._vel(*p1)
+            X1, Y1 = self._recon(p1[0], u1, v1)
+            s2 = self._stage(*p1, dt, u1, v1, X1, Y1)
         for j in range(ny):
             for i in range(nx):
                 c = (j + 2, i + 2)
-                hn = 0.5 * (h[c[0]][c[1]] + s2[0][j][i])
-                qxn = 0.5 * (qx[c[0]][c[1]] + s2[1][j][i])
-                qyn = 0.5 * (qy[c[0]][c[1]] + s2[2][j][i])
+                if self.order == 1:
+                    hn, qxn, qyn = s1[0][j][i], s1[1][j][i], s1[2][j][i]
+                else:
+                    hn = 0.5 * (h[c[0]][c[1]] + s2[0][j][i])
+                    qxn = 0.5 * (qx[c[0]][c[1]] + s2[1][j][i])
+                    qyn = 0.5 * (qy[c[0]][c[1]] + s2[2][j][i])
                 if self.rain > 0.0:
                     hn = hn + dt * self.rain
+                if self.inf:
+                    vi = self.vinf[j][i]
+                    ks = float(self.ks[j][i]) if self.ks is not None else 0.0
+                    if vi > 0.0:
+                        ic = ks * (1.0 + ((self.psi + hn) * self.dtheta) / vi)
+                        d = fmin(hn, dt * ic)
+                    else:
+                        d = hn
+                    hn = hn - d
+                    self.vinf[j][i] = vi + d
+                    self.infsum = self.infsum + d
                 if hn <= self.hd:
                     qxn = qyn = Z
                 h[c[0]][c[1]], qx[c[0]][c[1]], qy[c[0]][c[1]] = hn, qxn, qyn
@@ -306,13 +344,21 @@ class Scalar:
 
 # ---------------------------------------------------------------------------
 
-def _case(seed, nx, ny, dry_frac, bc, friction, rain):
+def _case(seed, nx, ny, dry_frac, bc, friction, rain, order=2, ga=False):
+    """A random wet/dry workload; with ga, Green-Ampt on a K_s map and a
+    starting infiltrated depth that is zero in some cells."""
     w = si.random_state(nx, ny, seed, dry_frac=dry_frac)
     w.bc = bc
     w.friction = friction
     w.manning_n = {1: 0.03, 2: 30.0, 3: 0.05, 4: 40.0}.get(friction, 0.0)
     w.rain_rate = rain
-    return w
+    vinf = None
+    if ga:
+        rng = np.random.default_rng(seed + 100)
+        w.infiltration, w.psi, w.dtheta = 1, 0.1, 0.3
+        w.ks = 1e-4 * np.exp(0.5 * rng.standard_normal((ny, nx)))
+        vinf = 0.01 * rng.random((ny, nx)) * (rng.random((ny, nx)) < 0.7)
+    return w, order, vinf
 
 
 CASES = [
@@ -321,29 +367,41 @@ CASES = [
     (3, 11, 6, 0.0, (0, 0, 0, 0), 2, 1e-3),
     (4, 7, 7, 0.8, (1, 1, 1, 1), 4, 0.0),
     (5, 10, 9, 0.2, (0, 1, 1, 0), 0, 2e-4),
+    (6, 9, 8, 0.3, (0, 1, 0, 1), 1, 0.0, 1),
+    (7, 10, 7, 0.2, (1, 0, 0, 1), 3, 5e-4, 1, True),
+    (8, 8, 9, 0.3, (0, 0, 1, 1), 1, 5e-4, 2, True),
 ]
+
+
+def _census(w, order, vinf):
+    return oc.Census(w.z, w.h, w.qx, w.qy, w.dx, w.dy, h_dry=w.h_dry, bc=w.bc, friction=w.friction,
+                     friction_coef=w.manning_n, cfl=w.cfl, dt_max=w.dt_max, rain_rate=w.rain_rate,
+                     order=order, infiltration=bool(w.infiltration), ks_map=w.ks, psi=w.psi,
+                     dtheta=w.dtheta, vinf=vinf)
 
 
 @pytest.mark.parametrize("case", CASES)
 def test_census_matches_oracle_bitwise(case):
-    w = _case(*case)
-    o = oracle.Oracle.from_workload(w, friction_coef=w.manning_n, rain_t_on=0.0, rain_t_off=1e9)
-    c = oc.Census(w.z, w.h, w.qx, w.qy, w.dx, w.dy, h_dry=w.h_dry, bc=w.bc, friction=w.friction,
-                  friction_coef=w.manning_n, cfl=w.cfl, dt_max=w.dt_max, rain_rate=w.rain_rate)
+    w, order, vinf = _case(*case)
+    o = oracle.Oracle.from_workload(w, friction_coef=w.manning_n, rain_t_on=0.0, rain_t_off=1e9, order=order)
+    if vinf is not None:
+        o.set_vinf(vinf)
+    c = _census(w, order, vinf)
     for _ in range(3):
         dto = o.step(1)[0]
         dtc = c.step()
         assert dtc == dto
         for a, b in zip(c.state(), o.state()):
             assert np.array_equal(a, b)
+        if vinf is not None:
+            assert np.array_equal(c.vinf, o.vinf())
 
 
 @pytest.mark.parametrize("case", CASES)
 def test_census_counts_equal_scalar_count(case):
-    w = _case(*case)
-    c = oc.Census(w.z, w.h, w.qx, w.qy, w.dx, w.dy, h_dry=w.h_dry, bc=w.bc, friction=w.friction,
-                  friction_coef=w.manning_n, cfl=w.cfl, dt_max=w.dt_max, rain_rate=w.rain_rate)
-    s = Scalar(w, w.friction, w.manning_n, w.rain_rate)
+    w, order, vinf = _case(*case)
+    c = _census(w, order, vinf)
+    s = Scalar(w, w.friction, w.manning_n, w.rain_rate, order, vinf)
     for _ in range(2):
         assert c.step() == s.step()
         for a, b in zip(c.state(), s.state()):
