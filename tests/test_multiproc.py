@@ -55,3 +55,24 @@ def test_reference_arm_under_torchrun_prints_once():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_reference_arm_caps_its_timed_region(monkeypatch, capsys):
+    """A --steps too large for the CPU oracle ends at the wall-time cap: the
+    line reports the rate over the full-grid steps actually taken and says
+    so in its sample."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    oracle.build()
+    monkeypatch.setattr(bench, "REFERENCE_BUDGET_S", 0.05)
+
+    class A:
+        side, warmup, steps, gpus = 64, 3, 10 ** 6, 1
+    bench.run_reference(A, 1, 0)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["steps"] == 10 ** 6 and line["warmup"] == 3
+    assert "capped" in line["cpu_baseline"]["sample"]
+    done = int(line["cpu_baseline"]["sample"].split()[0])
+    assert 1 <= done < 10 ** 6
+    assert line["value"] > 0 and line["value"] == line["cpu_baseline"]["value"] == line["e2e"]["value"]
