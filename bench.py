@@ -442,7 +442,7 @@ def measure(sw, torch, w, precision: str, steps: int, warmup: int, ws: int, cloc
 
 
 def measure_d8(sw, torch, n: int, reps: int = 20):
-    """D8 flow directions (Sec. 6) of an n x n float32 DEM: 4 B read and 1 B
+    """D8 flow directions (Sec. 5.2) of an n x n float32 DEM: 4 B read and 1 B
     written per cell; the DEM (n^2 x 4 B) is larger than L2."""
     import swof_inputs as si
     z = torch.from_numpy(si.dem(n, n, seed=7, quantum=0.01)).cuda()

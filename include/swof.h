@@ -262,7 +262,7 @@ SWOF_API int swof_get_gauges(swof_ctx *ctx, double *out, int max_records, int *c
 SWOF_API int swof_set_dry_tile_skip(swof_ctx *ctx, int on);
 SWOF_API int swof_get_tile_activity(swof_ctx *ctx, long long *live_tiles, long long *tiles);
 
-/* D8 flow direction of a DEM (Sec. 6, the eight-neighbour example): for
+/* D8 flow direction of a DEM (Sec. 5.2, the eight-neighbour example): for
  * each cell the neighbour of smallest elevation among those strictly below
  * it, as code 1..8 = E, NE, N, NW, W, SW, S, SE (counter-clockwise from +x,
  * row j + 1 north of row j), 0 when none is lower; ties go to the first

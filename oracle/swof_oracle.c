@@ -30,7 +30,7 @@
  *     or q, for a fluvial boundary; both for a torrential inflow).
  *   - Sec. 3.3: the first-order variant (no reconstruction, n_CFL = 1 is
  *     the caller's choice) advanced by one explicit Euler stage.
- *   - Sec. 6 (SkelGIS example): the D8 flow direction of a DEM.
+ *   - Sec. 5.2 (SkelGIS example): the D8 flow direction of a DEM.
  *
  * Readings where the paper is silent (each also listed in the design notes):
  *   2-D: F = (hu, hu^2 + g h^2/2, huv), G = (hv, huv, hv^2 + g h^2/2); the
@@ -837,7 +837,7 @@ int oracle_get_gauges(const oracle_t *o, double *out, int max)
     return n;
 }
 
-/* D8 flow direction (Sec. 6, the SkelGIS example): for each cell, the
+/* D8 flow direction (Sec. 5.2, the SkelGIS example): for each cell, the
  * neighbour of smallest elevation among those strictly below the cell;
  * code k = 1..8 for the neighbours E, NE, N, NW, W, SW, S, SE (counter-
  * clockwise from +x, rows growing northwards), 0 when no neighbour is

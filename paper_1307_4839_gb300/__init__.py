@@ -456,7 +456,7 @@ class Solver:
 def flow_directions(z, out=None, nodata: float | None = None, stream=None):
     """D8 flow-direction codes (uint8 torch tensor [ny][nx], 0 = no lower
     neighbour, 1..8 = E, NE, N, NW, W, SW, S, SE) of a float32 CUDA DEM
-    tensor [ny][nx] (Sec. 6's eight-neighbour example), in one kernel;
+    tensor [ny][nx] (Sec. 5.2's eight-neighbour example), in one kernel;
     neighbours at z <= nodata are no candidates (None: no no-data value)."""
     import torch
     if z.dtype != torch.float32 or not z.is_cuda or z.dim() != 2 or not z.is_contiguous():

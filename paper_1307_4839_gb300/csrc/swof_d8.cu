@@ -1,5 +1,5 @@
 // swof_d8.cu -- D8 flow directions of a DEM (sm_103a), the eight-neighbour
-// example of arXiv 1307.4839 Sec. 6: for every cell, the neighbour of
+// example of arXiv 1307.4839 Sec. 5.2: for every cell, the neighbour of
 // smallest elevation among those strictly below it (code 1..8 = E, NE, N,
 // NW, W, SW, S, SE; 0 when none is lower; ties to the first code;
 // neighbours outside the grid, or at z <= nodata when a no-data value is

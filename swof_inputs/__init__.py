@@ -19,7 +19,7 @@ Workloads follow the test cases the paper uses or points at:
   * hillslope  - rainfall runoff with Green-Ampt infiltration (Sec. 3.5) on a
     ridge-and-furrow plane slope with lognormal K_s;
   * ensemble_specs - a seeded batch of valley scenarios of uneven sizes;
-  * dem        - a float32 DEM for the D8 flow-direction stencil (Sec. 6's
+  * dem        - a float32 DEM for the D8 flow-direction stencil (Sec. 5.2's
     eight-neighbour example): a tilted fractal surface, optionally
     quantised so that many neighbours tie, with no-data holes.
 """

@@ -1,7 +1,7 @@
 """CUDA path vs the FP64 oracle for the extensions (needs a GPU), through the
 C ABI: the friction laws of Sec. 2.1, the imposed (Riemann-invariant)
 edges of Sec. 2.2, the first-order variant of Sec. 3.3, gauges and the
-maximum depth, dry-tile skipping, and the D8 flow direction of Sec. 6.
+maximum depth, dry-tile skipping, and the D8 flow direction of Sec. 5.2.
 
 FP64 states, dt sequences, gauge records and maximum depths must agree with
 the oracle bit for bit; FP32 by relative L1 (<= 1e-5 on depths); D8 codes

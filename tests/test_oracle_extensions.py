@@ -14,7 +14,7 @@ fix (no GPU):
   form with first-order convergence, and the CFL speed of the cell values,
 * gauges and the running maximum depth against brute force over single
   steps,
-* the D8 flow direction (Sec. 6) against a brute-force restatement on small
+* the D8 flow direction (Sec. 5.2) against a brute-force restatement on small
   DEMs with ties, a cone and a tilted plane.
 """
 import math
