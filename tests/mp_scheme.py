@@ -7,7 +7,11 @@ to within FP64 rounding.  The code is written cell-by-cell from the paper's
 formulas (Sec. 3.1 scheme + hydrostatic reconstruction + S_L/S_R/Fc, Sec. 3.3
 HLL, Sec. 3.4 MUSCL-minmod with modified velocities, Sec. 3.2 friction and
 Heun, Sec. 3.5 Green-Ampt) and the same readings of the paper's silent points
-as the oracle, without sharing any of its code.
+as the oracle, without sharing any of its code.  It also takes the other
+friction laws of Sec. 2.1 (C_f = 1/K^2, f/(8g), 1/C^2 with h^p, p = 4/3 or
+1), the first-order step of Sec. 3.3 (face values = cell values, one Euler
+stage) and the Riemann-invariant edges of Sec. 2.2, whose imposed-discharge
+celerity comes from the exact roots of its cubic here.
 """
 from __future__ import annotations
 
@@ -27,13 +31,33 @@ def _minmod(a, b):
 class MPScheme:
     def __init__(self, nx, ny, dx, dy, z, h, qx, qy, *, g=9.81, h_dry=1e-6,
                  bc=(0, 0, 0, 0), manning_n=0.0, rain_rate=0.0, ks=0.0,
-                 psi=0.0, dtheta=0.0, infiltration=False):
+                 psi=0.0, dtheta=0.0, infiltration=False, friction=None, friction_coef=None,
+                 order=2, bc_h=(0.0,) * 4, bc_q=(0.0,) * 4):
+        """friction: 1 Manning (n), 2 Strickler (K), 3 Darcy-Weisbach (f),
+        4 Chezy (C), coefficient in friction_coef; by default Manning with
+        manning_n.  bc: 0 wall, 1 outflow, 2 imposed depth (bc_h), 3
+        imposed inflow discharge (bc_q), 4 both; sides W, E, S, N."""
         M = mp.mpf
         self.nx, self.ny = nx, ny
         self.dx, self.dy = M(dx), M(dy)
         self.g, self.h_dry = M(g), M(h_dry)
         self.bc = bc
-        self.n2 = M(manning_n) ** 2
+        self.order = order
+        self.bc_h = [M(v) for v in bc_h]
+        self.bc_q = [M(v) for v in bc_q]
+        law = 1 if friction is None else friction
+        coef = M(manning_n if friction_coef is None else friction_coef)
+        # C_f of the law and the power p of h in S_f = C_f |u| u / h^p
+        if law == 1:
+            self.n2, self.p = coef ** 2, M(4) / 3
+        elif law == 2:
+            self.n2, self.p = 1 / coef ** 2, M(4) / 3
+        elif law == 3:
+            self.n2, self.p = coef / (8 * self.g), M(1)
+        elif law == 4:
+            self.n2, self.p = 1 / coef ** 2, M(1)
+        else:
+            self.n2, self.p = M(0), M(4) / 3
         self.R = M(rain_rate)
         self.ks, self.psi, self.dtheta = M(ks), M(psi), M(dtheta)
         self.infiltration = infiltration
@@ -44,9 +68,48 @@ class MPScheme:
         self.vinf = [[M(0) for _ in range(nx)] for _ in range(ny)]
 
     # --- ghost values: map an out-of-range index onto the interior -------
+    def _imposed(self, side, h1, qn1, qt1):
+        """Boundary state (h, inward normal discharge, tangential discharge)
+        of an imposed edge from its edge cell (Sec. 2.2): the outgoing
+        invariant R = w1 - 2 sqrt(g h1) is kept, the imposed variable
+        replaces the incoming one."""
+        g, typ = self.g, self.bc[side]
+        w1 = qn1 / h1 if h1 > self.h_dry else mp.mpf(0)
+        t1 = qt1 / h1 if h1 > self.h_dry else mp.mpf(0)
+        R = w1 - 2 * mp.sqrt(g * h1)
+        hb, qb = self.bc_h[side], self.bc_q[side]
+        if typ == 4:
+            return hb, qb, mp.mpf(0)
+        if typ == 2:
+            w = R + 2 * mp.sqrt(g * hb)
+            return hb, hb * w, hb * t1
+        # q imposed: c = sqrt(g h) with q g / c^2 - 2c = R, the positive
+        # root of 2 c^3 + R c^2 - q g (q = 0: c = max(-R/2, 0))
+        Q = qb * g
+        if Q > 0:
+            roots = mp.polyroots([2, R, 0, -Q], maxsteps=200, extraprec=200)
+            c = max(mp.re(r) for r in roots if abs(mp.im(r)) < mp.mpf(10) ** -30 and mp.re(r) > 0)
+        else:
+            c = max(-R / 2, mp.mpf(0))
+        hh = c * c / g
+        return hh, qb, hh * t1
+
     def _cell(self, arrs, i, j):
         """(h, qx, qy, z) at (i, j), ghosts from the boundary conditions."""
         h, qx, qy = arrs
+        # imposed edges: both ghost layers hold the edge cell's boundary
+        # state; the bed extends the edge cell
+        for side, out, ei, ej, sgn, normal_x in ((0, i < 0, 0, j, 1, True),
+                                                  (1, i >= self.nx, self.nx - 1, j, -1, True),
+                                                  (2, j < 0, i, 0, 1, False),
+                                                  (3, j >= self.ny, i, self.ny - 1, -1, False)):
+            if out and self.bc[side] >= 2:
+                h1, qx1, qy1 = h[ej][ei], qx[ej][ei], qy[ej][ei]
+                qn1, qt1 = (sgn * qx1, qy1) if normal_x else (sgn * qy1, qx1)
+                b = self._imposed(side, h1, qn1, qt1)
+                if normal_x:
+                    return b[0], sgn * b[1], b[2], self.z[ej][ei]
+                return b[0], b[2], sgn * b[1], self.z[ej][ei]
         sx = sy = 1
         if i < 0:
             if self.bc[0] == 0:
@@ -74,8 +137,14 @@ class MPScheme:
         return q / h if h > self.h_dry else mp.mpf(0)
 
     def _recon(self, arrs, i, j, axis):
-        """MUSCL values of cell (i, j) along axis: (h-,h+,z-,z+,un-,un+,ut-,ut+)."""
+        """MUSCL values of cell (i, j) along axis: (h-,h+,z-,z+,un-,un+,ut-,ut+);
+        at first order the cell values themselves."""
         di, dj = (1, 0) if axis == 0 else (0, 1)
+        if self.order == 1:
+            c = self._cell(arrs, i, j)
+            un = self._vel(c[0], c[1 + axis])
+            ut = self._vel(c[0], c[2 - axis])
+            return c[0], c[0], c[3], c[3], un, un, ut, ut
         cells = [self._cell(arrs, i + k * di, j + k * dj) for k in (-1, 0, 1)]
         hs = [c[0] for c in cells]
         es = [c[0] + c[3] for c in cells]
@@ -134,6 +203,22 @@ class MPScheme:
                 b = self._recon(arrs, i, j, 1)
                 lx = max(lx, abs(a[4]) + mp.sqrt(self.g * a[0]), abs(a[5]) + mp.sqrt(self.g * a[1]))
                 ly = max(ly, abs(b[4]) + mp.sqrt(self.g * b[0]), abs(b[5]) + mp.sqrt(self.g * b[1]))
+        # an imposed edge's boundary state feeds the edge fluxes, so the
+        # face value of the ghost cell facing the domain counts too
+        for j in range(self.ny):
+            if self.bc[0] >= 2:
+                a = self._recon(arrs, -1, j, 0)
+                lx = max(lx, abs(a[5]) + mp.sqrt(self.g * a[1]))
+            if self.bc[1] >= 2:
+                a = self._recon(arrs, self.nx, j, 0)
+                lx = max(lx, abs(a[4]) + mp.sqrt(self.g * a[0]))
+        for i in range(self.nx):
+            if self.bc[2] >= 2:
+                b = self._recon(arrs, i, -1, 1)
+                ly = max(ly, abs(b[5]) + mp.sqrt(self.g * b[1]))
+            if self.bc[3] >= 2:
+                b = self._recon(arrs, i, self.ny, 1)
+                ly = max(ly, abs(b[4]) + mp.sqrt(self.g * b[0]))
         return lx, ly
 
     def _stage(self, arrs, dt):
@@ -160,7 +245,7 @@ class MPScheme:
                 if hs > self.h_dry:
                     u = self._vel(h[j][i], qx[j][i])
                     v = self._vel(h[j][i], qy[j][i])
-                    den = 1 + dt * g * self.n2 * mp.sqrt(u * u + v * v) / hs ** (mp.mpf(4) / 3)
+                    den = 1 + dt * g * self.n2 * mp.sqrt(u * u + v * v) / hs ** self.p
                     qxs, qys = qxs / den, qys / den
                 else:
                     qxs = qys = mp.mpf(0)
@@ -171,12 +256,15 @@ class MPScheme:
         dt = mp.mpf(dt)
         U0 = (self.h, self.qx, self.qy)
         U1 = self._stage(U0, dt)
-        U2 = self._stage(U1, dt)
+        U2 = self._stage(U1, dt) if self.order == 2 else None
         for j in range(self.ny):
             for i in range(self.nx):
-                h = (U0[0][j][i] + U2[0][j][i]) / 2
-                qx = (U0[1][j][i] + U2[1][j][i]) / 2
-                qy = (U0[2][j][i] + U2[2][j][i]) / 2
+                if self.order == 1:                     # one Euler stage
+                    h, qx, qy = U1[0][j][i], U1[1][j][i], U1[2][j][i]
+                else:
+                    h = (U0[0][j][i] + U2[0][j][i]) / 2
+                    qx = (U0[1][j][i] + U2[1][j][i]) / 2
+                    qy = (U0[2][j][i] + U2[2][j][i]) / 2
                 h = h + dt * self.R
                 if self.infiltration:
                     V = self.vinf[j][i]

@@ -24,6 +24,7 @@ import pytest
 
 import oracle
 import swof_inputs as si
+from mp_scheme import MPScheme
 from swe_closed_forms import dam_break_profile
 
 G = 9.81
@@ -406,3 +407,47 @@ def test_d8_cone_and_plane():
     plane = (x + 2.0 * y).astype(np.float32)                # lowest neighbour: south-west
     d = oracle.d8(plane)
     assert np.all(d[1:, 1:] == 6) and np.all(d[0, 1:] == 5) and np.all(d[1:, 0] == 7) and d[0, 0] == 0
+
+
+# ------------------------------------------------ 50-digit second implementation
+
+# (name, order, friction law, coefficient, bc W E S N, bc_h, bc_q)
+MP_CASES = [
+    ("first_order", 1, 1, 0.04, (0, 1, 1, 0), (0, 0, 0, 0), (0, 0, 0, 0)),
+    ("strickler", 2, 2, 25.0, (0, 1, 1, 0), (0, 0, 0, 0), (0, 0, 0, 0)),
+    ("darcy_weisbach", 2, 3, 0.3, (1, 0, 0, 1), (0, 0, 0, 0), (0, 0, 0, 0)),
+    ("chezy", 2, 4, 15.0, (0, 0, 1, 1), (0, 0, 0, 0), (0, 0, 0, 0)),
+    ("imposed_q_west_h_east", 2, 1, 0.03, (3, 2, 0, 1), (0, 1.3, 0, 0), (0.6, 0, 0, 0)),
+    ("imposed_hq_south_first_order", 1, 0, 0.0, (0, 1, 4, 2), (0, 0, 0.8, 1.1), (0, 0, 2.5, 0)),
+]
+
+
+@pytest.mark.parametrize("case", MP_CASES, ids=[c[0] for c in MP_CASES])
+def test_extensions_match_50_digit_second_implementation(case):
+    """The first-order step, the Strickler / Darcy-Weisbach / Chezy laws and
+    the imposed edges against the 50-digit restatement (tests/mp_scheme.py:
+    exact powers h^p, the imposed-discharge celerity from the exact roots of
+    its cubic): wave speeds to 1e-14 and two steps to 1e-13 relative on a
+    rough 5 x 4 grid."""
+    name, order, law, coef, bc, bc_h, bc_q = case
+    rng = np.random.default_rng(sum(map(ord, name)))
+    nx, ny, dx, dy = 5, 4, 0.3, 0.25
+    z = 0.2 * rng.standard_normal((ny, nx))
+    h = 0.5 + rng.random((ny, nx))
+    h[rng.random((ny, nx)) < 0.2] = 0.0
+    qx = h * 0.4 * rng.standard_normal((ny, nx))
+    qy = h * 0.4 * rng.standard_normal((ny, nx))
+    o = oracle.Oracle(nx, ny, dx, dy, z, friction=law, friction_coef=coef, bc=bc, bc_h=bc_h, bc_q=bc_q,
+                      order=order)
+    o.set_state(h, qx, qy)
+    m = MPScheme(nx, ny, dx, dy, z, h, qx, qy, bc=bc, friction=law, friction_coef=coef if law else 0.0,
+                 order=order, bc_h=bc_h, bc_q=bc_q)
+    lx, ly = o.lam()
+    mlx, mly = m.lam()
+    assert math.isclose(lx, float(mlx), rel_tol=1e-14) and math.isclose(ly, float(mly), rel_tol=1e-14)
+    for _ in range(2):
+        dt = o.step(1)[0]
+        m.step(dt)
+    for a, b in zip(o.state(), m.state()):
+        scale = max(np.max(np.abs(b)), 1e-300)
+        assert np.max(np.abs(a - b)) / scale <= 1e-13
