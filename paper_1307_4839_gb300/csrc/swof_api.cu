@@ -628,9 +628,11 @@ int swof_step(swof_ctx *c, int n, swof_step_info *info)
                     if (g) cudaGraphDestroy(g);
                     return SWOF_ECUDA;
                 }
-                e = cudaGraphInstantiate(&c->gexec, g, 0);
+                cudaGraphExec_t ge = nullptr;      // kept only once it is valid
+                e = cudaGraphInstantiate(&ge, g, 0);
                 cudaGraphDestroy(g);
                 if (e != cudaSuccess) return SWOF_ECUDA;
+                c->gexec = ge;
                 c->graph_n = n;
                 c->graph_gen = c->gen;
             }

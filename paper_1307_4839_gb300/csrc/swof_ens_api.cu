@@ -310,9 +310,11 @@ int swof_ensemble_step(swof_ens *e, int n, int *status)
                 if (g) cudaGraphDestroy(g);
                 return SWOF_ECUDA;
             }
-            ce = cudaGraphInstantiate(&e->gexec, g, 0);
+            cudaGraphExec_t ge = nullptr;          // kept only once it is valid
+            ce = cudaGraphInstantiate(&ge, g, 0);
             cudaGraphDestroy(g);
             if (ce != cudaSuccess) return SWOF_ECUDA;
+            e->gexec = ge;
             e->graph_n = n;
             e->graph_key = e->key;
             if (cudaGraphLaunch(e->gexec, e->stream) != cudaSuccess) return SWOF_ECUDA;
