@@ -19,6 +19,8 @@ fix (no GPU):
 """
 import math
 
+import mpmath as mp
+
 import numpy as np
 import pytest
 
@@ -411,7 +413,7 @@ def test_d8_cone_and_plane():
 
 # ------------------------------------------------ 50-digit second implementation
 
-# (name, order, friction law, coefficient, bc W E S N, bc_h, bc_q)
+# (name, order, friction law, coefficient, bc W E S N, bc_h, bc_q[, Green-Ampt])
 MP_CASES = [
     ("first_order", 1, 1, 0.04, (0, 1, 1, 0), (0, 0, 0, 0), (0, 0, 0, 0)),
     ("strickler", 2, 2, 25.0, (0, 1, 1, 0), (0, 0, 0, 0), (0, 0, 0, 0)),
@@ -419,17 +421,17 @@ MP_CASES = [
     ("chezy", 2, 4, 15.0, (0, 0, 1, 1), (0, 0, 0, 0), (0, 0, 0, 0)),
     ("imposed_q_west_h_east", 2, 1, 0.03, (3, 2, 0, 1), (0, 1.3, 0, 0), (0.6, 0, 0, 0)),
     ("imposed_hq_south_first_order", 1, 0, 0.0, (0, 1, 4, 2), (0, 0, 0.8, 1.1), (0, 0, 2.5, 0)),
+    # where V_inf = 0 Green-Ampt takes all the water: the clean-up must zero q
+    ("green_ampt_dry_out", 2, 1, 0.04, (0, 1, 1, 0), (0, 0, 0, 0), (0, 0, 0, 0), True),
 ]
 
 
-@pytest.mark.parametrize("case", MP_CASES, ids=[c[0] for c in MP_CASES])
-def test_extensions_match_50_digit_second_implementation(case):
-    """The first-order step, the Strickler / Darcy-Weisbach / Chezy laws and
-    the imposed edges against the 50-digit restatement (tests/mp_scheme.py:
-    exact powers h^p, the imposed-discharge celerity from the exact roots of
-    its cubic): wave speeds to 1e-14 and two steps to 1e-13 relative on a
-    rough 5 x 4 grid."""
-    name, order, law, coef, bc, bc_h, bc_q = case
+def mp_case_errors(case, library=None):
+    """(wave speeds agree to 1e-14, largest relative state difference after
+    two steps) between the oracle (or a library built from it) and the
+    50-digit restatement for one of MP_CASES."""
+    name, order, law, coef, bc, bc_h, bc_q = case[:7]
+    ga = len(case) > 7 and case[7]
     rng = np.random.default_rng(sum(map(ord, name)))
     nx, ny, dx, dy = 5, 4, 0.3, 0.25
     z = 0.2 * rng.standard_normal((ny, nx))
@@ -437,17 +439,33 @@ def test_extensions_match_50_digit_second_implementation(case):
     h[rng.random((ny, nx)) < 0.2] = 0.0
     qx = h * 0.4 * rng.standard_normal((ny, nx))
     qy = h * 0.4 * rng.standard_normal((ny, nx))
+    R, ks, psi, dth = (1e-3, 1e-4, 0.1, 0.3) if ga else (0.0, 0.0, 0.0, 0.0)
     o = oracle.Oracle(nx, ny, dx, dy, z, friction=law, friction_coef=coef, bc=bc, bc_h=bc_h, bc_q=bc_q,
-                      order=order)
+                      order=order, rain_rate=R, rain_t_off=1e9 if ga else 0.0, infiltration=int(ga), ks=ks,
+                      psi=psi, dtheta=dth, library=library)
     o.set_state(h, qx, qy)
     m = MPScheme(nx, ny, dx, dy, z, h, qx, qy, bc=bc, friction=law, friction_coef=coef if law else 0.0,
-                 order=order, bc_h=bc_h, bc_q=bc_q)
+                 order=order, bc_h=bc_h, bc_q=bc_q, rain_rate=R, ks=ks, psi=psi, dtheta=dth,
+                 infiltration=ga)
+    if ga:
+        v0 = 0.01 * (rng.random((ny, nx)) < 0.5)
+        o.set_vinf(v0)
+        m.vinf = [[mp.mpf(float(v0[j, i])) for i in range(nx)] for j in range(ny)]
     lx, ly = o.lam()
     mlx, mly = m.lam()
-    assert math.isclose(lx, float(mlx), rel_tol=1e-14) and math.isclose(ly, float(mly), rel_tol=1e-14)
+    lam_ok = math.isclose(lx, float(mlx), rel_tol=1e-14) and math.isclose(ly, float(mly), rel_tol=1e-14)
     for _ in range(2):
-        dt = o.step(1)[0]
-        m.step(dt)
-    for a, b in zip(o.state(), m.state()):
-        scale = max(np.max(np.abs(b)), 1e-300)
-        assert np.max(np.abs(a - b)) / scale <= 1e-13
+        m.step(o.step(1)[0])
+    err = max(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300) for a, b in zip(o.state(), m.state()))
+    return lam_ok, err
+
+
+@pytest.mark.parametrize("case", MP_CASES, ids=[c[0] for c in MP_CASES])
+def test_extensions_match_50_digit_second_implementation(case):
+    """The first-order step, the Strickler / Darcy-Weisbach / Chezy laws,
+    the imposed edges and Green-Ampt emptying cells against the 50-digit
+    restatement (tests/mp_scheme.py: exact powers h^p, the imposed-discharge
+    celerity from the exact roots of its cubic): wave speeds to 1e-14 and
+    two steps to 1e-13 relative on a rough 5 x 4 grid."""
+    lam_ok, err = mp_case_errors(case)
+    assert lam_ok and err <= 1e-13, err

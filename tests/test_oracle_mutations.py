@@ -18,7 +18,7 @@ import oracle
 import swof_inputs as si
 from mp_scheme import MPScheme
 from swe_closed_forms import dam_break_profile
-from test_oracle_extensions import _d8_brute, _textbook_hll_step
+from test_oracle_extensions import MP_CASES, _d8_brute, _textbook_hll_step, mp_case_errors
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "swof_oracle.c")
 
@@ -68,6 +68,16 @@ MUTATIONS = {
     "cfl_uses_cell_not_face": ("fabs(o->xup[c]) + sqrt(g * o->xhp[c]));", "fabs(o->xum[c]) + sqrt(g * o->xhm[c]));"),
     "rain_before_dt_scale": ("double rdt = dt * o->p.rain_rate;", "double rdt = o->p.rain_rate;"),
     "icbrt_one_newton_step": ("for (int it = 0; it < 4; ++it) {", "for (int it = 0; it < 1; ++it) {"),
+    "imposed_hq_tangent_kept": ("out[0] = hset; out[1] = qset; out[2] = 0.0;",
+                                "out[0] = hset; out[1] = qset; out[2] = hset * t1;"),
+    "no_dry_cleanup": ("if (h <= hdry) { qx = 0.0; qy = 0.0; }", ""),
+    "cfl_min_mode_max": ("double m = fmin(a, b);", "double m = fmax(a, b);"),
+    "event_clamp_keeps_dt": ("if (ev[k] > t && ev[k] < t + dt) { dt = ev[k] - t; tn = ev[k]; }",
+                             "if (ev[k] > t && ev[k] < t + dt) { tn = ev[k]; }"),
+    "cfl_viol_inverted": ("if (dt * (lx / o->dx + ly / o->dy) > o->p.cfl) o->cfl_viol++;",
+                          "if (dt * (lx / o->dx + ly / o->dy) <= o->p.cfl) o->cfl_viol++;"),
+    "rain_before_t_on": ("int rain = o->p.rain_rate > 0.0 && o->t >= o->p.rain_t_on && o->t < o->p.rain_t_off;",
+                         "int rain = o->p.rain_rate > 0.0 && o->t < o->p.rain_t_off;"),
 }
 
 
@@ -316,11 +326,62 @@ def pin_gauges_and_max(L):
     return bool(np.array_equal(o.gauges(), np.array(recs)) and np.array_equal(o.max_depth(), hmax))
 
 
+def pin_mp_imposed_hq_and_dry_out(L):
+    """50-digit restatement: depth and discharge both imposed (tangential
+    discharge 0, Sec. 2.2) at first order, and Green-Ampt emptying the cells
+    with V_inf = 0 (the clean-up then zeroes their discharge)."""
+    cases = [c for c in MP_CASES if c[0] in ("imposed_hq_south_first_order", "green_ampt_dry_out")]
+    return all(lam_ok and err <= 1e-13 for lam_ok, err in (mp_case_errors(c, L) for c in cases))
+
+
+def pin_cfl_min_mode(L):
+    """The per-direction form of Eq. (cfl) in 2-D (SWOF_CFL_MIN): on a
+    uniform flow dt = n_CFL min(dx / (|u| + c), dy / (|v| + c))."""
+    h, u, v, dx, dy, n = 0.7, -0.9, 0.35, 0.4, 0.25, 6
+    o = oracle.Oracle(n, n, dx, dy, np.zeros((n, n)), bc=(1, 1, 1, 1), dt_max=10.0, cfl_mode=1, library=L)
+    o.set_state(np.full((n, n), h), np.full((n, n), h * u), np.full((n, n), h * v))
+    c = math.sqrt(9.81 * h)
+    return math.isclose(o.step(1)[0], 0.5 * min(dx / (abs(u) + c), dy / (abs(v) + c)), rel_tol=1e-14)
+
+
+def pin_event_clamps_and_rain_window(L):
+    """Steps land on the rain on/off times and on t_end, and rain falls only
+    on steps that start in [t_on, t_off): a lake at rest under rain from
+    0.3 to 0.7 s with dt capped at 0.08 s (so both event times and t_end
+    fall inside steps)."""
+    n, R, dx = 4, 1e-3, 10.0
+    o = oracle.Oracle(n, n, dx, dx, np.zeros((n, n)), dt_max=0.08, t_end=1.0, rain_rate=R,
+                      rain_t_on=0.3, rain_t_off=0.7, library=L)
+    o.set_state(np.ones((n, n)), np.zeros((n, n)), np.zeros((n, n)))
+    dts = o.run_to(1.0)
+    d = o.diag()
+    return (d["t"] == 1.0 and abs(float(np.sum(dts)) - 1.0) <= 1e-12
+            and math.isclose(d["rain_in"], R * 0.4 * n * n * dx * dx, rel_tol=1e-12))
+
+
+def pin_cfl_violation_counter(L):
+    """The CFL check at U* (counted, not corrected): a replayed dt of a
+    quarter of the bound counts nothing over 3 steps, three times the
+    bound counts its step."""
+    w = si.random_state(12, 10, seed=4, dry_frac=0.0, vel=0.3)
+    counts = []
+    for factor, steps in ((0.25, 3), (3.0, 1)):
+        o = oracle.Oracle(w.nx, w.ny, w.dx, w.dy, w.z, check_cfl=1, library=L)
+        o.set_state(w.h, w.qx, w.qy)
+        lx, ly = o.lam()
+        o.set_dt_sequence(np.full(steps, factor * 0.5 / (lx / w.dx + ly / w.dy)))
+        o.step(steps)
+        counts.append(o.diag()["cfl_viol"])
+    return counts == [0.0, 1.0]
+
+
 BATTERY = [pin_mp_second_implementation, pin_lake_at_rest, pin_mass_and_positivity,
            pin_stoker, pin_symmetry, pin_cfl_uniform, pin_cfl_muscl_faces,
            pin_friction_uniform, pin_ponding_time, pin_friction_laws_ode,
            pin_imposed_uniform_channels, pin_torrential_fill, pin_first_order_textbook,
-           pin_first_order_lake_and_budget, pin_d8_brute_force, pin_gauges_and_max]
+           pin_first_order_lake_and_budget, pin_d8_brute_force, pin_gauges_and_max,
+           pin_mp_imposed_hq_and_dry_out, pin_cfl_min_mode, pin_event_clamps_and_rain_window,
+           pin_cfl_violation_counter]
 
 
 def _run_battery(L):
