@@ -78,6 +78,10 @@ MUTATIONS = {
                           "if (dt * (lx / o->dx + ly / o->dy) <= o->p.cfl) o->cfl_viol++;"),
     "rain_before_t_on": ("int rain = o->p.rain_rate > 0.0 && o->t >= o->p.rain_t_on && o->t < o->p.rain_t_off;",
                          "int rain = o->p.rain_rate > 0.0 && o->t < o->p.rain_t_off;"),
+    "dt_max_cap_dropped": ("if (dt > o->p.dt_max) dt = o->p.dt_max;", ""),
+    "ks_map_ignored": ("double ks = o->ksmap ? o->ksmap[ci] : o->p.ks;", "double ks = o->p.ks;"),
+    "friction_map_ignored": ("double cf = o->cf ? o->cf[(size_t)j * nx + i] : o->p_cf;", "double cf = o->p_cf;"),
+    "infiltration_budget_without_area": ("o->infiltrated += infil * o->dx * o->dy;", "o->infiltrated += infil;"),
 }
 
 
@@ -326,11 +330,13 @@ def pin_gauges_and_max(L):
     return bool(np.array_equal(o.gauges(), np.array(recs)) and np.array_equal(o.max_depth(), hmax))
 
 
-def pin_mp_imposed_hq_and_dry_out(L):
+def pin_mp_extension_cases(L):
     """50-digit restatement: depth and discharge both imposed (tangential
-    discharge 0, Sec. 2.2) at first order, and Green-Ampt emptying the cells
-    with V_inf = 0 (the clean-up then zeroes their discharge)."""
-    cases = [c for c in MP_CASES if c[0] in ("imposed_hq_south_first_order", "green_ampt_dry_out")]
+    discharge 0, Sec. 2.2) at first order; Green-Ampt emptying the cells
+    with V_inf = 0 (the clean-up then zeroes their discharge); Darcy-
+    Weisbach friction between outflow edges on the west and north."""
+    cases = [c for c in MP_CASES if c[0] in ("imposed_hq_south_first_order", "green_ampt_dry_out",
+                                              "darcy_weisbach")]
     return all(lam_ok and err <= 1e-13 for lam_ok, err in (mp_case_errors(c, L) for c in cases))
 
 
@@ -355,8 +361,44 @@ def pin_event_clamps_and_rain_window(L):
     o.set_state(np.ones((n, n)), np.zeros((n, n)), np.zeros((n, n)))
     dts = o.run_to(1.0)
     d = o.diag()
-    return (d["t"] == 1.0 and abs(float(np.sum(dts)) - 1.0) <= 1e-12
+    return (d["t"] == 1.0 and abs(float(np.sum(dts)) - 1.0) <= 1e-12 and float(np.max(dts)) <= 0.08
             and math.isclose(d["rain_in"], R * 0.4 * n * n * dx * dx, rel_tol=1e-12))
+
+
+def pin_maps_and_infiltration_budget(L):
+    """Per-cell maps and the infiltration budget over one step of a uniform
+    flow on a flat bed between outflow edges: away from the column where the
+    Manning map changes (3 cells, the reach of one step) each cell's
+    discharge follows the friction recurrence with its own n (Sec. 3.2);
+    where the flow stays uniform the infiltrated depth scales with the
+    cell's own K_s (Sec. 3.5); the volume falls by the infiltrated volume
+    plus the net outflow (cells of 0.5 x 0.25 m)."""
+    nx, ny, dx, dy, h0, q0 = 16, 6, 0.5, 0.25, 0.6, 0.3
+    col = np.arange(nx)[None, :] * np.ones((ny, 1), dtype=int)
+    nmap = np.where(col < nx // 2, 0.02, 0.07)
+    ksmap = np.where(np.arange(ny)[:, None] < ny // 2, 2e-5, 5e-5) * np.ones((ny, nx))
+    o = oracle.Oracle(nx, ny, dx, dy, np.zeros((ny, nx)), bc=(1, 1, 1, 1), friction=1, n_map=nmap,
+                      infiltration=1, ks_map=ksmap, psi=0.1, dtheta=0.3, dt_max=0.05, library=L)
+    o.set_state(np.full((ny, nx), h0), np.full((ny, nx), q0), np.zeros((ny, nx)))
+    v0 = 0.01
+    o.set_vinf(np.full((ny, nx), v0))
+    vol0 = o.diag()["volume"]
+    dt = o.step(1)[0]
+    _, qx, _ = o.state()
+    far = np.abs(col - (nx // 2 - 0.5)) >= 3.5
+    ok = True
+    for nm in (0.02, 0.07):
+        k = dt * 9.81 * nm * nm / h0 ** (7.0 / 3.0)
+        q1 = q0 / (1.0 + k * abs(q0))
+        qe = 0.5 * (q0 + q1 / (1.0 + k * abs(q1)))
+        sel = far & (nmap == nm)
+        ok &= bool(np.allclose(qx[sel], qe, rtol=1e-14, atol=0))
+    dv = o.vinf()[:, 0] - v0                      # column 0: uniform flow all step
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ok &= bool(np.allclose(dv[ny // 2:] / dv[: ny // 2], 2.5, rtol=1e-12))
+    d = o.diag()
+    ok &= math.isclose(vol0 - d["volume"], d["infiltrated"] + d["outflow"], rel_tol=1e-9)
+    return ok and d["infiltrated"] > 0
 
 
 def pin_cfl_violation_counter(L):
@@ -380,8 +422,8 @@ BATTERY = [pin_mp_second_implementation, pin_lake_at_rest, pin_mass_and_positivi
            pin_friction_uniform, pin_ponding_time, pin_friction_laws_ode,
            pin_imposed_uniform_channels, pin_torrential_fill, pin_first_order_textbook,
            pin_first_order_lake_and_budget, pin_d8_brute_force, pin_gauges_and_max,
-           pin_mp_imposed_hq_and_dry_out, pin_cfl_min_mode, pin_event_clamps_and_rain_window,
-           pin_cfl_violation_counter]
+           pin_mp_extension_cases, pin_cfl_min_mode, pin_event_clamps_and_rain_window,
+           pin_cfl_violation_counter, pin_maps_and_infiltration_budget]
 
 
 def _run_battery(L):
