@@ -82,6 +82,12 @@ MUTATIONS = {
     "ks_map_ignored": ("double ks = o->ksmap ? o->ksmap[ci] : o->p.ks;", "double ks = o->p.ks;"),
     "friction_map_ignored": ("double cf = o->cf ? o->cf[(size_t)j * nx + i] : o->p_cf;", "double cf = o->p_cf;"),
     "infiltration_budget_without_area": ("o->infiltrated += infil * o->dx * o->dy;", "o->infiltrated += infil;"),
+    "cfl_ignores_east_boundary_state": (
+        "if (o->p.bc[1] >= 2) ax = fmax(ax, fabs(o->xum[e]) + sqrt(g * o->xhm[e]));", ""),
+    "cfl_ignores_south_boundary_state": (
+        "if (o->p.bc[2] >= 2) ay = fmax(ay, fabs(o->yvp[s]) + sqrt(g * o->yhp[s]));", ""),
+    "cfl_ignores_north_boundary_state": (
+        "if (o->p.bc[3] >= 2) ay = fmax(ay, fabs(o->yvm[n]) + sqrt(g * o->yhm[n]));", ""),
 }
 
 
@@ -417,13 +423,33 @@ def pin_cfl_violation_counter(L):
     return counts == [0.0, 1.0]
 
 
+def pin_cfl_sees_every_imposed_edge(L):
+    """The CFL maximum covers an imposed edge's boundary state (it feeds
+    the edge fluxes): a fast inflow, depth 0.5 m and discharge 3 m^2/s both
+    imposed, beside a lake at rest 1 m deep, on each side in turn -- the
+    wave speed along that side's axis is the ghost's 6 + sqrt(0.5 g), the
+    other axis keeps the lake's sqrt(g)."""
+    n, g, hb, qb = 6, 9.81, 0.5, 3.0
+    ok = True
+    for side in range(4):
+        bc, bh, bq = [0] * 4, [0.0] * 4, [0.0] * 4
+        bc[side], bh[side], bq[side] = 4, hb, qb
+        o = oracle.Oracle(n, n, 1.0, 1.0, np.zeros((n, n)), bc=bc, bc_h=bh, bc_q=bq, library=L)
+        o.set_state(np.ones((n, n)), np.zeros((n, n)), np.zeros((n, n)))
+        lam = o.lam()
+        fast, still = (lam[0], lam[1]) if side < 2 else (lam[1], lam[0])
+        ok &= math.isclose(fast, qb / hb + math.sqrt(g * hb), rel_tol=1e-14)
+        ok &= math.isclose(still, math.sqrt(g), rel_tol=1e-14)
+    return ok
+
+
 BATTERY = [pin_mp_second_implementation, pin_lake_at_rest, pin_mass_and_positivity,
            pin_stoker, pin_symmetry, pin_cfl_uniform, pin_cfl_muscl_faces,
            pin_friction_uniform, pin_ponding_time, pin_friction_laws_ode,
            pin_imposed_uniform_channels, pin_torrential_fill, pin_first_order_textbook,
            pin_first_order_lake_and_budget, pin_d8_brute_force, pin_gauges_and_max,
            pin_mp_extension_cases, pin_cfl_min_mode, pin_event_clamps_and_rain_window,
-           pin_cfl_violation_counter, pin_maps_and_infiltration_budget]
+           pin_cfl_violation_counter, pin_maps_and_infiltration_budget, pin_cfl_sees_every_imposed_edge]
 
 
 def _run_battery(L):
