@@ -46,3 +46,85 @@ def test_backward_matches_finite_differences():
         lm = UNetRef(C, 4, 3, pp, use_bf16=False).loss_and_grads(x, tgt)[0]
         fd = (lp - lm) / (2 * eps) / (P * 3)      # the gradient is of the mean
         assert abs(fd - g[i]) <= 1e-6 + 1e-4 * abs(fd), (i, fd, g[i])
+
+
+def _torch_unet_loss(p, spec, x, tgt, in_ch, out_ch):
+    """The same network restated with PyTorch's own CPU operators (conv2d,
+    conv_transpose2d, avg_pool2d, exact-erf gelu) in float64, its weights
+    read from the flat parameter vector p ([columns][Kp] rows, column K =
+    tap * cin_padded + c, taps row-major over the 3 x 3 window; transposed
+    2 x 2 convolutions with column sub * cout + o, sub = 2 dy + dx)."""
+    import torch
+    import torch.nn.functional as F
+
+    def wb(l):
+        d = spec[l]
+        return p[d["woff"]: d["woff"] + d["ncols"] * d["Kp"]].view(d["ncols"], d["Kp"]), \
+            p[d["boff"]: d["boff"] + d["cout"]]
+
+    def conv(l, x):
+        d = spec[l]
+        Wm, b = wb(l)
+        cin = x.shape[1]
+        if d["kind"] == 2:                                   # 2x2 stride-2 transposed
+            w = Wm[:, :cin].reshape(4, d["cout"], cin).permute(2, 1, 0).reshape(cin, d["cout"], 2, 2)
+            return F.conv_transpose2d(x, w, b, stride=2)
+        if d["kind"] == 1:                                   # 1x1
+            return F.conv2d(x, Wm[:, :cin].reshape(d["cout"], cin, 1, 1), b)
+        w = torch.stack([Wm[:, t * d["cin_p"]: t * d["cin_p"] + cin] for t in range(9)], dim=-1)
+        return F.conv2d(x, w.reshape(d["cout"], cin, 3, 3), b, padding=1)
+
+    h = torch.from_numpy(x[..., :in_ch]).permute(0, 3, 1, 2)
+    skips, inp = [], h
+    for l in range(4):
+        if l > 0:
+            inp = F.avg_pool2d(skips[l - 1], 2)
+        bo = F.gelu(conv(2 * l + 1, F.gelu(conv(2 * l, inp))))
+        if l < 3:
+            skips.append(bo)
+        else:
+            below = bo
+    for l in (2, 1, 0):
+        base = 8 + 3 * (2 - l)
+        cat = torch.cat([skips[l], conv(base, below)], dim=1)
+        below = F.gelu(conv(base + 2, F.gelu(conv(base + 1, cat))))
+    out = conv(17, below).permute(0, 2, 3, 1)
+    d = out[..., :out_ch] - torch.from_numpy(tgt)
+    return out, (d * d).sum()
+
+
+def test_forward_loss_and_gradient_match_torch_restatement():
+    """The numpy reference (exact arithmetic) against an independent
+    restatement with PyTorch's convolution, transposed convolution, pooling
+    and GELU operators and its autograd: output, loss and the whole flat
+    gradient (of the mean squared error) agree to FP64 rounding.  This pins
+    the forward itself -- padding, tap order, pooling, the up-convolution's
+    sub-pixel layout, the skip concatenation order -- which the
+    finite-difference pin (backward against the reference's own forward)
+    cannot."""
+    import torch
+    rng = np.random.default_rng(5)
+    C, H, B, in_ch, out_ch = 8, 16, 2, 4, 3
+    spec, n = layers_spec(C, in_ch, out_ch)
+    p = np.zeros(n)
+    for d in spec:
+        taps = 9 if d["kind"] == 0 else 1
+        W = p[d["woff"]: d["woff"] + d["ncols"] * d["Kp"]].reshape(d["ncols"], d["Kp"])
+        for t in range(taps):
+            W[:, t * d["cin_p"]: t * d["cin_p"] + d["cin"]] = \
+                np.sqrt(2.0 / (taps * d["cin"])) * rng.standard_normal((d["ncols"], d["cin"]))
+        p[d["boff"]: d["boff"] + d["cout"]] = 0.1 * rng.standard_normal(d["cout"])
+    x = np.zeros((B, H, H, 16))
+    x[..., :in_ch] = rng.standard_normal((B, H, H, in_ch))
+    tgt = rng.standard_normal((B, H, H, out_ch))
+    net = UNetRef(C, in_ch, out_ch, p, use_bf16=False)
+    out, _ = net.forward(x)
+    loss, g = net.loss_and_grads(x, tgt)
+    pt = torch.tensor(p, dtype=torch.float64, requires_grad=True)
+    tout, tloss = _torch_unet_loss(pt, spec, x, tgt, in_ch, out_ch)
+    (tloss / (B * H * H * out_ch)).backward()
+    tout = tout.detach().numpy()
+    assert np.max(np.abs(out - tout)) <= 1e-12 * np.max(np.abs(tout))
+    assert abs(loss - tloss.item()) <= 1e-12 * loss
+    tg = pt.grad.numpy()
+    assert np.max(np.abs(g - tg)) <= 1e-10 * np.max(np.abs(tg))
