@@ -128,3 +128,26 @@ def test_forward_loss_and_gradient_match_torch_restatement():
     assert abs(loss - tloss.item()) <= 1e-12 * loss
     tg = pt.grad.numpy()
     assert np.max(np.abs(g - tg)) <= 1e-10 * np.max(np.abs(tg))
+
+
+def test_bf16_rounding_is_round_to_nearest_even():
+    """The reference's bfloat16 rounding (the points where the GPU stores
+    bf16) equals PyTorch's float32 -> bfloat16 conversion bit for bit,
+    including exact ties (which go to the even mantissa), signed zeros,
+    overflow to infinity and subnormals; values given as float64 are first
+    rounded to float32, as the GPU's float accumulators are."""
+    import torch
+    from oracle.unet_ref import bf16
+    rng = np.random.default_rng(11)
+    f = np.concatenate([
+        rng.standard_normal(20000).astype(np.float32) * np.float32(10.0) ** rng.integers(-30, 30, 20000),
+        # exact ties: bf16 mantissa with the dropped half exactly 0x8000, both parities
+        (np.arange(1, 4001, dtype=np.uint32) << 16 | 0x8000).view(np.float32),
+        np.array([0.0, -0.0, 3.4e38, -3.4e38, 1e-40, -1e-40, 1.0, -1.0], dtype=np.float32),
+    ])
+    ours = bf16(f)
+    ref = torch.from_numpy(f).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(ours, ref, equal_nan=True)
+    assert np.array_equal(np.signbit(ours), np.signbit(ref))
+    x64 = rng.standard_normal(1000) * 1e3
+    assert np.array_equal(bf16(x64), torch.from_numpy(x64.astype(np.float32)).to(torch.bfloat16).double().numpy())
