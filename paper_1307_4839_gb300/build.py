@@ -22,6 +22,7 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
 PER_FILE = {
     "swof_fp64.cu": ["-fmad=false", "-prec-div=true", "-prec-sqrt=true"],
     "swof_fp32.cu": [],
+    "swof_fp64_reg.cu": ["-fmad=false", "-prec-div=true", "-prec-sqrt=true"],
     # the ensemble kernel reads, within one launch, data other CTAs wrote:
     # global loads bypass the (non-coherent) L1
     "swof_ens_fp64.cu": ["-fmad=false", "-prec-div=true", "-prec-sqrt=true", "-Xptxas", "-dlcm=cg"],

@@ -114,6 +114,39 @@ double friction_cf(int law, double g, double coef)
     }
 }
 
+// Tensor maps of the padded fields for the stage kernels' TMA ring: one
+// 2-D map per field and tile width, the whole padded array (pitch x ny + 4
+// elements) with a box of NTX columns x RING_ROWS rows; boxes reaching past
+// the array are zero-filled.
+template <typename T>
+int make_sweep_maps(swof_ctx *c, Fields<T> &F)
+{
+    swof::EncodeTiledFn enc = swof::encode_tiled();
+    if (!enc) return SWOF_ECUDA;
+    const Params &P = c->P;
+    T *fld[8] = {F.h, F.qx, F.qy, F.h1, F.qx1, F.qy1, c->prec == SWOF_FP64 ? F.z : F.dzx,
+                 c->prec == SWOF_FP64 ? nullptr : F.dzy};
+    const int widths[swof::N_MAP_WIDTHS] = {64, 128, 256};
+    const CUtensorMapDataType dt =
+        sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    cuuint64_t dims[2] = {(cuuint64_t)P.pitch, (cuuint64_t)(P.ny + 4)};
+    cuuint64_t strides[1] = {(cuuint64_t)P.pitch * sizeof(T)};
+    cuuint32_t es[2] = {1, 1};
+    for (int w = 0; w < swof::N_MAP_WIDTHS; ++w) {
+        std::memset(&c->tmaps[w], 0, sizeof c->tmaps[w]);
+        cuuint32_t box[2] = {(cuuint32_t)widths[w], (cuuint32_t)swof::RING_ROWS};
+        for (int f = 0; f < 8; ++f) {
+            if (!fld[f]) continue;
+            if (enc(&c->tmaps[w].m[f], dt, 2, (void *)fld[f], dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return SWOF_ECUDA;
+        }
+    }
+    F.tmaps = c->tmaps;
+    return SWOF_OK;
+}
+
 template <typename T>
 int alloc_fields(swof_ctx *c, Fields<T> &F, const double *z, const swof_params *p)
 {
@@ -165,6 +198,7 @@ int alloc_fields(swof_ctx *c, Fields<T> &F, const double *z, const swof_params *
     F.dt_seq = nullptr;
     F.dt_hist = nullptr;
     F.dt_hist_cap = 0;
+    if (!st) st = make_sweep_maps<T>(c, F);
     return st;
 }
 
@@ -376,14 +410,14 @@ int swof_create(int nx, int ny, double dx, double dy, const double *z, const swo
     Params &P = c->P;
     P.nx = nx;
     P.ny = ny;
-    P.lpad = c->prec == SWOF_FP64 ? 2 : 4;
+    P.lpad = 2;
     int align = 128 / (int)c->esize;
     P.pitch = ((P.lpad + nx + 2) + align - 1) / align * align;
     P.dx = dx;
     P.dy = dy;
     P.g = p->g;
     P.cfl = p->cfl;
-    P.h_dry = p->h_dry;
+    P.h_dry = p->h_dry == 0.0 ? 0.0 : p->h_dry;   // (-0 -> +0: the dry tests compare bit patterns)
     P.dt_max = p->dt_max;
     P.dt_min = p->dt_min;
     P.t_end = p->t_end;

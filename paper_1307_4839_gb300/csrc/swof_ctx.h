@@ -55,6 +55,8 @@ struct swof_ctx {
     long long gauge_cap = 0;
     unsigned char *d_tile_act = nullptr, *d_tile_live = nullptr;
     bool skip_dry = false;
+    // tensor maps of the padded fields for the stage kernels, per tile width
+    swof::SweepMaps tmaps[swof::N_MAP_WIDTHS]{};
 
     void *fields() { return prec == SWOF_FP64 ? (void *)&f64 : (void *)&f32; }
 };

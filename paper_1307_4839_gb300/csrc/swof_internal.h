@@ -5,10 +5,14 @@
 //   (ny + 4) rows of `pitch` elements; row r holds grid row j = r - 2
 //   (2 ghost rows below and above, Sec. 6.1: two layers at second order).
 //   Within a row, element lpad + i is cell i, i in [-2, nx + 1]; lpad is 2
-//   for FP64 and 4 for FP32 so the first interior cell sits on a 16-byte
-//   boundary (double2 / float4 aligned).  pitch is a multiple of 128 bytes.
+//   in both precisions, so the first ghost cell (i = -2) and the first
+//   column of every stage tile (tile widths NTX - 4 are multiples of 4) sit
+//   on a 16-byte boundary, as the stage kernels' tensor copies need.  pitch
+//   is a multiple of 128 bytes; the columns past nx + 1 stay zero.
 //   Corner ghosts are never read and stay zero.
 #pragma once
+#include <cuda.h>
+
 #include <cstddef>
 #include <cstdint>
 
@@ -62,13 +66,17 @@ struct Params {
     int lam_partial;           // 1: the wave-speed kernel only reduces (no dt control)
 };
 
-// Stage-kernel shapes (threads per CTA along x, rows per CTA); the last two
-// fields bound the number of per-block budget slots any shape can need.
+// Stage-kernel shapes: threads per CTA along x, rows per CTA, and how the
+// input rows arrive (ring = 1: the TMA ring with the dry fast path; 0: the
+// one-row register prefetch).  Shapes 5..9 are the register forms of 0..4.
 struct TileShape {
-    int ntx, h;
+    int ntx, h, ring;
 };
-constexpr int N_TILE_SHAPES = 5;
-constexpr TileShape TILE_SHAPES[N_TILE_SHAPES] = {{128, 32}, {128, 64}, {256, 32}, {64, 64}, {64, 16}};
+constexpr int N_TILE_SHAPES = 10;
+constexpr int N_RING_SHAPES = 5;
+constexpr TileShape TILE_SHAPES[N_TILE_SHAPES] = {{128, 32, 1}, {128, 64, 1}, {256, 32, 1}, {64, 64, 1},
+                                                  {64, 16, 1},  {128, 32, 0}, {128, 64, 0}, {256, 32, 0},
+                                                  {64, 64, 0},  {64, 16, 0}};
 constexpr int SHALLOW_SHAPE = 4;      // dry-tile skipping: short column walks
 inline int max_stage_blocks(int nx, int ny)
 {
@@ -80,6 +88,22 @@ inline int max_stage_blocks(int nx, int ny)
     }
     return m;
 }
+
+// TMA tensor maps of a context's padded fields for one stage-tile width
+// (box NTX columns x RING_ROWS rows): h, qx, qy, h1, qx1, qy1, then z (FP64)
+// or dz_x, dz_y (FP32).  Passed to the stage kernels by value.
+struct SweepMaps {
+    CUtensorMap m[8];
+};
+constexpr int N_MAP_WIDTHS = 3;                 // tile widths NTX = 64, 128, 256
+constexpr int RING_ROWS = 4;                    // rows per tensor copy of the stage ring
+inline int map_width_index(int ntx) { return ntx == 64 ? 0 : (ntx == 128 ? 1 : 2); }
+
+// cuTensorMapEncodeTiled, looked up from the driver at run time
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled();
 
 // Device pointers of one context.  T = double (FP64) or float (FP32).
 template <typename T>
@@ -108,6 +132,7 @@ struct Fields {
     double *gauge_rec;         // [gauge_cap][1 + 3 n_gauges]
     unsigned char *tile_act;   // dry-tile skipping: tile holds water after the step
     unsigned char *tile_live;  //   tile processed in the current step (nullptr: off)
+    const SweepMaps *tmaps;    // host memory: the stage kernels' tensor maps per tile width
 };
 
 // Launchers, one set per precision (swof_fp64.cu, swof_fp32.cu).  All

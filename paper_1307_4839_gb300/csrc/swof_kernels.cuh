@@ -36,6 +36,7 @@
 #include <type_traits>
 
 #include "swof_internal.h"
+#include "tc05.cuh"
 
 namespace swof {
 
@@ -92,6 +93,29 @@ __device__ __forceinline__ Scal<T> scal(const Params &P)
     else
         return {P.fg, P.fh_dry, P.fcf, P.fpsi, P.fdtheta, P.fks};
 }
+
+// x == 0 of either sign; FP64 on the bit pattern, off GB300's narrow FP64
+// pipe (same answer as the comparison, NaN included).
+__device__ __forceinline__ bool is0(double x) { return (__double_as_longlong(x) << 1) == 0; }
+__device__ __forceinline__ bool is0(float x) { return x == 0.0f; }
+
+// x > c and x <= c for a threshold c >= +0 (the dry depth): FP64 on the
+// bit patterns, which order like the values for non-negative doubles, with
+// negative x (sign bit set) below c and NaN on neither side -- the same
+// answer as the comparison for every x.
+__device__ __forceinline__ bool gt_pos(double x, double c)
+{
+    const long long b = __double_as_longlong(x);
+    return b > __double_as_longlong(c) && b <= 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool le_pos(double x, double c)
+{
+    const long long b = __double_as_longlong(x);
+    const bool nan = (b & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
+    return !nan && b <= __double_as_longlong(c);
+}
+__device__ __forceinline__ bool gt_pos(float x, float c) { return x > c; }
+__device__ __forceinline__ bool le_pos(float x, float c) { return x <= c; }
 
 // minmod limiter (Sec. 3.4): the value of smaller magnitude when a and b
 // have the same sign, else 0.
@@ -278,7 +302,7 @@ __device__ __forceinline__ Rec<T> muscl(T h0, T h1, T h2, T z0, T z1, T z2,
         r.zm = -off;
         r.zp = off;
     }
-    if (h1 > hdry) {
+    if (gt_pos(h1, hdry)) {
         T dun = minmod(un1 - un0, un2 - un1);
         T dut = minmod(ut1 - ut0, ut2 - ut1);
         r.unm = un1 - (r.hp * rh1) * (T(0.5) * dun);
@@ -303,7 +327,7 @@ __device__ __forceinline__ T cell_speed(T h0, T h1, T h2, T un0, T un1, T un2, T
     T hm = h1 - T(0.5) * dh;
     T hp = h1 + T(0.5) * dh;
     T unm = un1, unp = un1;
-    if (h1 > hdry) {
+    if (gt_pos(h1, hdry)) {
         T dun = minmod(un1 - un0, un2 - un1);
         unm = un1 - (hp * rh1) * (T(0.5) * dun);
         unp = un1 + (hm * rh1) * (T(0.5) * dun);
@@ -353,7 +377,7 @@ __device__ __forceinline__ void face_flux(T g, T hpa, T zpa, T unpa, T utpa,
         hR = fmaxf(0.0f, hmb - fmaxf(0.0f, zpa - zb));
     }
     T F0, F1, F2;
-    if (hL == T(0) && hR == T(0)) {
+    if (is0(hL) && is0(hR)) {
         // both face depths zero: every HLL branch gives exactly zero
         F0 = T(0);
         F1 = T(0);
@@ -533,7 +557,7 @@ __global__ void __launch_bounds__(NT) k_lambda(Params P, Fields<T> F)
                 qy = F.qy[o];
             }
             V4<T> e = {h, T(0), T(0), T(0)};
-            if (h > C.hdry) {
+            if (gt_pos(h, C.hdry)) {
                 e.w = rcp(h);
                 e.y = qx * e.w;
                 e.z = qy * e.w;
@@ -590,7 +614,7 @@ __device__ __forceinline__ V4<T> cell_rec(const Params &P, const Fields<T> &F, i
     size_t o = pidx(P, gi, gj);
     T h = F.h[o];
     V4<T> e = {h, T(0), T(0), T(0)};
-    if (h > hdry) {
+    if (gt_pos(h, hdry)) {
         e.w = rcp(h);
         e.y = F.qx[o] * e.w;
         e.z = F.qy[o] * e.w;
@@ -625,7 +649,8 @@ __global__ void __launch_bounds__(NT) k_lambda_ring(Params P, Fields<T> F)
                 const int gi = F.ring_cols[cc];
                 V4<T> w = cell_rec(P, F, gi - 1, gj, C.hdry), m = cell_rec(P, F, gi, gj, C.hdry),
                       e = cell_rec(P, F, gi + 1, gj, C.hdry);
-                kx = kmax(kx, speed_key(cell_speed(w.x, m.x, e.x, w.y, m.y, e.y, m.w, C.hdry, C.g)));
+                if (!(is0(w.x) && is0(m.x) && is0(e.x)))   // three dry cells: speed 0
+                    kx = kmax(kx, speed_key(cell_speed(w.x, m.x, e.x, w.y, m.y, e.y, m.w, C.hdry, C.g)));
                 if (gi == 0 && P.bc[0] >= SWOF_BC_IMPOSED_H) kx = kmax(kx, speed_key(ab(w.y) + sq(C.g * w.x)));
                 if (gi == P.nx - 1 && P.bc[1] >= SWOF_BC_IMPOSED_H)
                     kx = kmax(kx, speed_key(ab(e.y) + sq(C.g * e.x)));
@@ -637,7 +662,8 @@ __global__ void __launch_bounds__(NT) k_lambda_ring(Params P, Fields<T> F)
             const int gj = F.ring_rows[q];
             V4<T> s_ = cell_rec(P, F, gi, gj - 1, C.hdry), m = cell_rec(P, F, gi, gj, C.hdry),
                   n = cell_rec(P, F, gi, gj + 1, C.hdry);
-            ky = kmax(ky, speed_key(cell_speed(s_.x, m.x, n.x, s_.z, m.z, n.z, m.w, C.hdry, C.g)));
+            if (!(is0(s_.x) && is0(m.x) && is0(n.x)))
+                ky = kmax(ky, speed_key(cell_speed(s_.x, m.x, n.x, s_.z, m.z, n.z, m.w, C.hdry, C.g)));
             if (gj == 0 && P.bc[2] >= SWOF_BC_IMPOSED_H) ky = kmax(ky, speed_key(ab(s_.z) + sq(C.g * s_.x)));
             if (gj == P.ny - 1 && P.bc[3] >= SWOF_BC_IMPOSED_H) ky = kmax(ky, speed_key(ab(n.z) + sq(C.g * n.x)));
         }
@@ -1016,26 +1042,64 @@ int launch_lambda_ring_t(const Params &P, void *f, void *stream)
     return (int)cudaGetLastError();
 }
 
+// Per-device attributes: every stage kernel's input ring sits in dynamic
+// shared memory beyond the default 48 KB window, so each instantiation is
+// opted in on the current device.
+template <typename T, int STAGE, int NTX, int H, bool ORD1 = false>
+cudaError_t sweep_opt_in()
+{
+    return cudaFuncSetAttribute(k_sweep<T, STAGE, NTX, H, ORD1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)ring_bytes<T, STAGE, NTX>());
+}
+
+template <typename T, int NTX, int H>
+cudaError_t sweep_opt_in_shape()
+{
+    cudaError_t e = sweep_opt_in<T, 1, NTX, H>();
+    if (e == cudaSuccess) e = sweep_opt_in<T, 2, NTX, H>();
+    if (e == cudaSuccess) e = sweep_opt_in<T, 1, NTX, H, true>();
+    return e;
+}
+
 template <typename T>
 int configure_t()
 {
-    return (int)cudaSuccess;
+    cudaError_t e = sweep_opt_in_shape<T, 128, 32>();
+    if (e == cudaSuccess) e = sweep_opt_in_shape<T, 128, 64>();
+    if (e == cudaSuccess) e = sweep_opt_in_shape<T, 256, 32>();
+    if (e == cudaSuccess) e = sweep_opt_in_shape<T, 64, 64>();
+    if (e == cudaSuccess) e = sweep_opt_in_shape<T, 64, 16>();
+    return (int)e;
 }
 
 template <typename T, int STAGE, int NTX, int H>
 int launch_sweep(const Params &P, const Fields<T> &F, cudaStream_t s)
 {
     dim3 grid((P.nx + NTX - 5) / (NTX - 4), (P.ny + H - 1) / H);
-    k_sweep<T, STAGE, NTX, H><<<grid, NTX, 0, s>>>(P, F);
+    k_sweep<T, STAGE, NTX, H><<<grid, NTX, ring_bytes<T, STAGE, NTX>(), s>>>(P, F, F.tmaps[map_width_index(NTX)]);
     return (int)cudaGetLastError();
 }
+
+// The register-prefetch forms (shapes N_RING_SHAPES..), compiled in their
+// own translation units (swof_fp32_reg.cu, swof_fp64_reg.cu).
+template <typename T, int STAGE, int NTX, int H, bool ORD1>
+int launch_sweep_reg(const Params &P, const Fields<T> &F, cudaStream_t s)
+{
+    dim3 grid((P.nx + NTX - 5) / (NTX - 4), (P.ny + H - 1) / H);
+    k_sweep_reg<T, STAGE, NTX, H, ORD1><<<grid, NTX, 0, s>>>(P, F);
+    return (int)cudaGetLastError();
+}
+template <typename T, int STAGE, bool ORD1>
+int launch_stage_reg(int cfg, const Params &P, const Fields<T> &F, cudaStream_t s);
 
 template <typename T, int STAGE>
 int launch_stage_t(const Params &P, void *f, void *stream)
 {
     const Fields<T> &F = *static_cast<const Fields<T> *>(f);
     cudaStream_t s = (cudaStream_t)stream;
-    switch (STAGE == 1 ? P.tile_cfg : P.tile_cfg2) {
+    const int cfg = STAGE == 1 ? P.tile_cfg : P.tile_cfg2;
+    if (cfg >= N_RING_SHAPES) return launch_stage_reg<T, STAGE, false>(cfg, P, F, s);
+    switch (cfg) {
     case 1: return launch_sweep<T, STAGE, 128, 64>(P, F, s);
     case 2: return launch_sweep<T, STAGE, 256, 32>(P, F, s);
     case 3: return launch_sweep<T, STAGE, 64, 64>(P, F, s);
@@ -1048,7 +1112,7 @@ template <typename T, int NTX, int H>
 int launch_sweep_o1(const Params &P, const Fields<T> &F, cudaStream_t s)
 {
     dim3 grid((P.nx + NTX - 5) / (NTX - 4), (P.ny + H - 1) / H);
-    k_sweep<T, 1, NTX, H, true><<<grid, NTX, 0, s>>>(P, F);
+    k_sweep<T, 1, NTX, H, true><<<grid, NTX, ring_bytes<T, 1, NTX>(), s>>>(P, F, F.tmaps[map_width_index(NTX)]);
     return (int)cudaGetLastError();
 }
 
@@ -1057,6 +1121,7 @@ int launch_stage1_o1_t(const Params &P, void *f, void *stream)
 {
     const Fields<T> &F = *static_cast<const Fields<T> *>(f);
     cudaStream_t s = (cudaStream_t)stream;
+    if (P.tile_cfg >= N_RING_SHAPES) return launch_stage_reg<T, 1, true>(P.tile_cfg, P, F, s);
     switch (P.tile_cfg) {
     case 1: return launch_sweep_o1<T, 128, 64>(P, F, s);
     case 2: return launch_sweep_o1<T, 256, 32>(P, F, s);

@@ -36,7 +36,8 @@ __global__ void __launch_bounds__(256) k_lambda_ring_tiles(Params P, Fields<T> F
             const int gj = j0 + (r >> 1), gi = (r & 1) ? i1 : i0;
             V4<T> w = cell_rec(P, F, gi - 1, gj, C.hdry), m = cell_rec(P, F, gi, gj, C.hdry),
                   e = cell_rec(P, F, gi + 1, gj, C.hdry);
-            kx = kmax(kx, speed_key(cell_speed(w.x, m.x, e.x, w.y, m.y, e.y, m.w, C.hdry, C.g)));
+            if (!(is0(w.x) && is0(m.x) && is0(e.x)))   // three dry cells: speed 0
+                    kx = kmax(kx, speed_key(cell_speed(w.x, m.x, e.x, w.y, m.y, e.y, m.w, C.hdry, C.g)));
             if (gi == 0 && P.bc[0] >= SWOF_BC_IMPOSED_H) kx = kmax(kx, speed_key(ab(w.y) + sq(C.g * w.x)));
             if (gi == P.nx - 1 && P.bc[1] >= SWOF_BC_IMPOSED_H) kx = kmax(kx, speed_key(ab(e.y) + sq(C.g * e.x)));
         }
@@ -45,7 +46,8 @@ __global__ void __launch_bounds__(256) k_lambda_ring_tiles(Params P, Fields<T> F
             const int gi = i0 + (c >> 1), gj = (c & 1) ? j1 : j0;
             V4<T> s_ = cell_rec(P, F, gi, gj - 1, C.hdry), m = cell_rec(P, F, gi, gj, C.hdry),
                   n = cell_rec(P, F, gi, gj + 1, C.hdry);
-            ky = kmax(ky, speed_key(cell_speed(s_.x, m.x, n.x, s_.z, m.z, n.z, m.w, C.hdry, C.g)));
+            if (!(is0(s_.x) && is0(m.x) && is0(n.x)))
+                ky = kmax(ky, speed_key(cell_speed(s_.x, m.x, n.x, s_.z, m.z, n.z, m.w, C.hdry, C.g)));
             if (gj == 0 && P.bc[2] >= SWOF_BC_IMPOSED_H) ky = kmax(ky, speed_key(ab(s_.z) + sq(C.g * s_.x)));
             if (gj == P.ny - 1 && P.bc[3] >= SWOF_BC_IMPOSED_H) ky = kmax(ky, speed_key(ab(n.z) + sq(C.g * n.x)));
         }
