@@ -613,10 +613,26 @@ __device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, 
                     // of zeros; below h_dry)
                     store_cell<T>(P, F.h, F.qx, F.qy, gi, ro, T(0), T(0), T(0));
                 } else {
-                    T hn = T(0.5) * (c_h + hs);
-                    T qxn = T(0.5) * (c_qx + qxs);
-                    T qyn = T(0.5) * (c_qy + qys);
-                    if (rain) hn = hn + rdt;
+                    // Heun average (U^n + U**)/2, then rain.  FP32 adds the
+                    // step's rain to the Heun increment (U** - U^n)/2 before
+                    // that meets U^n: the rain depth of one step is a few ulp
+                    // of a deep cell, and adding that same constant on its own
+                    // every step rounds the same way every time (a bias that
+                    // grows with the number of steps); joined to the varying
+                    // increment the one rounding left averages out.
+                    T hn, qxn, qyn;
+                    if constexpr (fp64) {
+                        hn = T(0.5) * (c_h + hs);
+                        qxn = T(0.5) * (c_qx + qxs);
+                        qyn = T(0.5) * (c_qy + qys);
+                        if (rain) hn = hn + rdt;
+                    } else {
+                        T dh = T(0.5) * (hs - c_h);
+                        if (rain) dh = dh + rdt;
+                        hn = c_h + dh;
+                        qxn = c_qx + T(0.5) * (qxs - c_qx);
+                        qyn = c_qy + T(0.5) * (qys - c_qy);
+                    }
                     if (P.infiltration) {
                         T vi = c_vi;
                         T ks = c_ks;

@@ -109,7 +109,8 @@ def test_ensemble_bounded_wait_reports_timeout():
 
 def test_fp32_ensemble_members_against_fp64_oracle():
     """FP32 bulk members with the oracle's dt replayed: relative L1 of
-    (h, hu, hv) per member after 60 steps (reported; bound 1e-5 on h)."""
+    (h, hu, hv) per member after 60 steps within 1e-5 (the discharges also
+    printed against the discharge vector's L1 norm)."""
     ws = members(seed=21, sides=[64, 96, 130, 48])
     ens = sw.Ensemble(ws, precision=sw.FP32)
     refs = []
@@ -122,6 +123,8 @@ def test_fp32_ensemble_members_against_fp64_oracle():
     for k in range(len(ws)):
         got = ens.member(k).state()
         errs = [np.sum(np.abs(a - b)) / max(np.sum(np.abs(b)), 1e-30) for a, b in zip(got, refs[k])]
-        print(f"member {k} ({ws[k].nx}^2): rel L1 h {errs[0]:.2e} hu {errs[1]:.2e} hv {errs[2]:.2e}")
-        assert errs[0] <= 1e-5, errs
-        assert errs[1] <= 1e-4 and errs[2] <= 1e-4, errs
+        qn = max(np.sum(np.hypot(refs[k][1], refs[k][2])), 1e-30)
+        eq = [np.sum(np.abs(a - b)) / qn for a, b in zip(got[1:], refs[k][1:])]
+        print(f"member {k} ({ws[k].nx}^2): rel L1 h {errs[0]:.2e} hu {errs[1]:.2e} hv {errs[2]:.2e}; "
+              f"vs |q| {eq[0]:.2e} {eq[1]:.2e}")
+        assert max(errs) <= 1e-5, errs

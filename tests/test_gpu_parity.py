@@ -256,17 +256,27 @@ def test_fp64_all_dry_domain_and_two_cell_grid():
 
 
 # ---------------------------------------------------------------- FP32 ----
+# The FP32 bar: relative L1 <= 1e-5 against FP64 at the end time of each
+# workload, per field.  Where a discharge component is ~0 in the FP64
+# solution (the hillslope's cross-slope hu: 1e-4 of the downslope hv), its
+# relative error is FP32 roundoff over a near-zero total; the tests then also
+# state it against the L1 norm of the discharge vector |(hu, hv)|, the
+# reading the design notes record for such components.
+
+def rel_l1_vec(a, b, bx, by):
+    """sum |a - b| over the L1 norm of the FP64 discharge vector (bx, by)."""
+    return float(np.sum(np.abs(a - b)) / max(np.sum(np.hypot(bx, by)), 1e-300))
+
 
 def test_fp32_full_size_valley_4096_against_oracle_dt():
     """The FP32 path at the benchmark's size, on the oracle's first 8 dt
-    values, against the oracle: relative L1 of h <= 1e-5 and of the
-    down-valley discharge hv <= 1e-4 (measured 1.7e-5: this early in the
-    dam break hv is still small and FP32 rounding of the ~8e3 m^3/s^2
-    pressure terms is a visible part of it).  The cross-valley discharge hu
-    of the FP64 solution is ~0 in the 40 m pool (lake at rest, exact in
-    FP64), so its relative error is FP32 roundoff over a near-zero total:
-    bounded at 1e-2 (measured 1.6e-3).  h >= 0 and the FP64 budget closes
-    (walls and an outflow edge, no rain)."""
+    values, against the oracle (an early check, not the end-time bar): h
+    within 1e-5 relative L1 (measured 2.3e-8).  Eight steps into the dam
+    break the discharges are nonzero only near the dam, while the FP32
+    roundoff of the 40 m reservoir's surface (see the end-time test) stirs
+    discharges of ~1e-5 m^2/s over the whole pool: measured 1.7e-5 against
+    the discharge vector's L1 norm, bounded at 2e-5.  h >= 0 and the FP64
+    budget closes (walls and an outflow edge, no rain)."""
     w = si.valley(4096)
     o = oracle.Oracle.from_workload(w)
     dts = o.step(8)
@@ -276,7 +286,10 @@ def test_fp32_full_size_valley_4096_against_oracle_dt():
     s.step(8)
     h, qx, qy = s.state()
     oh, oqx, oqy = o.state()
-    assert rel_l1(h, oh) <= 1e-5 and rel_l1(qy, oqy) <= 1e-4 and rel_l1(qx, oqx) <= 1e-2
+    eq = (rel_l1_vec(qx, oqx, oqx, oqy), rel_l1_vec(qy, oqy, oqx, oqy))
+    print(f"valley 8 steps: h {rel_l1(h, oh):.2e}, hu {rel_l1(qx, oqx):.2e}, hv {rel_l1(qy, oqy):.2e}, "
+          f"vs |q|: {eq[0]:.2e} {eq[1]:.2e}")
+    assert rel_l1(h, oh) <= 1e-5 and max(eq) <= 2e-5
     assert h.min() >= 0.0
     d = s.diagnostics()
     assert abs(d["volume"] + d["outflow"] - v0) <= 1e-6 * v0
@@ -286,11 +299,15 @@ def test_fp32_valley_4096_at_its_end_time():
     """The FP32 path over the whole valley run (2000 steps, t = 36 s) on the
     FP64 path's dt sequence, against the FP64 path (bit for bit the
     oracle's: test_fp64_full_size_valley_4096_first_steps_bitwise and the
-    ragged-grid tests; the oracle itself would take minutes here).  Relative
-    L1 at the end: h and the down-valley discharge hv within the 1e-5 FP32
-    target (measured 1.9e-6 and 8.0e-6); the cross-valley discharge hu,
-    ~0 in the exact solution, at FP32 roundoff over a near-zero total
-    (measured 1.95e-5, bounded at 3e-5).  Both paths are deterministic."""
+    ragged-grid tests; the oracle itself would take minutes here).  h and the
+    down-valley discharge hv within 1e-5 relative L1 (measured 0.9e-6 and
+    3.8e-6).  The cross-valley discharge hu misses the 1e-5 bar: measured
+    1.3e-5, bounded at 2e-5.  72 % of its error sits in the 40 m reservoir,
+    a lake at rest in FP64: in FP32 each cell's depth is rounded on its own
+    over the rough bed, so the stored surface h + z is not flat to the last
+    bit (~2e-6 m) and the deep water feels that as a pressure gradient.
+    Against the discharge vector's L1 norm it is 1.6e-6 (bounded at 1e-5).
+    Both paths are deterministic."""
     w = si.valley(4096)
     s64 = sw.Solver.from_workload(w, sw.FP64)
     assert s64.step(2000).status == 0
@@ -302,8 +319,44 @@ def test_fp32_valley_4096_at_its_end_time():
     assert s32.step(2000).status == 0
     h, qx, qy = s32.state()
     s32.close()
-    assert rel_l1(h, h64) <= 1e-5 and rel_l1(qy, qy64) <= 1e-5 and rel_l1(qx, qx64) <= 3e-5
+    print(f"valley 2000 steps: h {rel_l1(h, h64):.2e}, hu {rel_l1(qx, qx64):.2e}, hv {rel_l1(qy, qy64):.2e}, "
+          f"hu vs |q| {rel_l1_vec(qx, qx64, qx64, qy64):.2e}")
+    assert rel_l1(h, h64) <= 1e-5 and rel_l1(qy, qy64) <= 1e-5
+    assert rel_l1(qx, qx64) <= 2e-5 and rel_l1_vec(qx, qx64, qx64, qy64) <= 1e-5
     assert h.min() >= 0.0
+
+
+def test_fp32_rainfall_hillslope_2048_at_its_end_time():
+    """The rainfall-runoff workload (2048^2 hillslope, 50 mm/h for 600 s,
+    Green-Ampt with the lognormal K_s map, Manning 0.05, outflow downslope)
+    run to its end time t = 1200 s by the FP64 path, then by the FP32 path
+    on the same dt sequence: h, the downslope discharge hv and the
+    infiltrated depth V_inf within 1e-5 relative L1.  The cross-slope
+    discharge hu is ~0 in the FP64 solution (sum |hu| ~ 1e-4 sum |hv|: the
+    furrows run downslope), so it is held to 1e-5 against the discharge
+    vector's L1 norm."""
+    w = si.hillslope(2048)
+    s64 = sw.Solver.from_workload(w, sw.FP64)
+    info = s64.step(1)
+    while info.t < w.t_end:             # the last step is clamped onto t_end
+        info = s64.step(1)
+        assert info.status == 0
+    steps = info.steps
+    assert info.t == w.t_end
+    dts = s64.dt_history(steps)
+    a = s64.state() + (s64.infiltrated(),)
+    s64.close()
+    s32 = sw.Solver.from_workload(w, sw.FP32)
+    s32.set_dt_sequence(dts)
+    assert s32.step(steps).status == 0
+    b = s32.state() + (s32.infiltrated(),)
+    s32.close()
+    r = {f: rel_l1(y, x) for f, x, y in zip(("h", "hu", "hv", "V_inf"), a, b)}
+    r["hu_vs_q"] = rel_l1_vec(b[1], a[1], a[1], a[2])
+    print(f"rainfall 2048 to t = {w.t_end} s ({steps} steps):", {k: f"{v:.2e}" for k, v in r.items()})
+    assert r["h"] <= 1e-5 and r["hv"] <= 1e-5 and r["V_inf"] <= 1e-5 and r["hu_vs_q"] <= 1e-5
+    assert np.sum(np.abs(a[1])) <= 1e-3 * np.sum(np.abs(a[2]))      # hu ~0 indeed
+    assert b[0].min() >= 0.0
 
 
 def test_fp32_dam_break_200_rel_l1():
@@ -334,24 +387,32 @@ def test_fp32_lake_at_rest_drift_small():
 
 
 def test_fp32_valley_512_rel_l1():
+    """A 512^2 valley (30 m pool) for 200 steps on the oracle's dt: h and
+    the down-valley discharge within 1e-5 relative L1; the cross-valley
+    discharge, small this early, within 1e-5 of the discharge vector's L1."""
     w = si.valley(n=512, dx=2.0, seed=6, reservoir=30.0)
     o = oracle.Oracle.from_workload(w)
     dts = o.step(200)
     s = sw.Solver.from_workload(w, sw.FP32)
     s.set_dt_sequence(dts)
     s.step(200)
-    for a, b, name in zip(s.state(), o.state(), ("h", "qx", "qy")):
-        assert rel_l1(a, b) <= 1e-4, (name, rel_l1(a, b))
+    (h, qx, qy), (oh, oqx, oqy) = s.state(), o.state()
+    print(f"valley 512: h {rel_l1(h, oh):.2e} hu {rel_l1(qx, oqx):.2e} hv {rel_l1(qy, oqy):.2e} "
+          f"hu vs |q| {rel_l1_vec(qx, oqx, oqx, oqy):.2e}")
+    assert rel_l1(h, oh) <= 1e-5 and rel_l1(qy, oqy) <= 1e-5
+    assert rel_l1_vec(qx, oqx, oqx, oqy) <= 1e-5
 
 
-@pytest.mark.parametrize("shape", range(5))
+@pytest.mark.parametrize("shape", range(10))
 def test_fp64_every_tile_shape_bitwise(shape):
+    """Every stage-kernel shape, TMA-ring (0..4) and register-prefetch
+    (5..9) forms, stage 1 and stage 2 on different shapes and forms."""
     w = si.random_state(300, 150, seed=40 + shape, dry_frac=0.2)
     w.bc = (1, 0, 0, 1)
     o = oracle.Oracle.from_workload(w)
     dts = o.step(12)
     s = sw.Solver.from_workload(w, sw.FP64)
-    s.set_tile_shape(shape, (shape + 1) % 4)
+    s.set_tile_shape(shape, (shape + 3) % 10)
     s.step(12)
     assert np.array_equal(s.dt_history(), dts)
     assert_state_equal(s, o)
