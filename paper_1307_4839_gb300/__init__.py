@@ -423,10 +423,13 @@ class Solver:
     def autotune(self, reps: int = 5, cache: str | None = None, key: str | None = None) -> dict:
         """Pick the fastest stage-kernel tile shape for this grid and
         precision.  With `cache`, a JSON file maps "<gpu>|<nx>x<ny>|<prec>"
-        to the chosen shape so later runs skip the timing."""
+        to the chosen shape so later runs skip the timing (and the number of
+        shapes the library has: a cache written by a build with another
+        shape table is not used)."""
         import json
         if key is None:
             key = f"{_gpu_name()}|{self.nx}x{self.ny}|{'fp64' if self.precision == FP64 else 'fp32'}"
+        key = f"{key}|{len(tile_shapes())} shapes"
         data = {}
         if cache and os.path.exists(cache):
             try:
