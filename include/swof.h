@@ -53,6 +53,7 @@ extern "C" {
 #define SWOF_ETIMEOUT     -8   /* a bounded device wait ran out */
 #define SWOF_EDTUNDERFLOW -9   /* CFL dt below params.dt_min */
 #define SWOF_ESTATE      -10   /* call not valid in the context's state */
+#define SWOF_EBOUNDS     -11   /* debug build: a kernel index check failed (the access was clamped) */
 
 /* ---- enums ---- */
 #define SWOF_FP64 0            /* all arithmetic in FP64 (parity path) */
@@ -206,24 +207,28 @@ SWOF_API int swof_get_diagnostics(swof_ctx *ctx, swof_diag *d);
 /* Water volume sum(h) dx dy and minimum depth of a caller-owned depth
  * field, computed without allocating any device memory.  The paper has no
  * counterpart: this is a service for callers that may not call cudaMalloc
- * (code recording into a CUDA graph it captures itself, hosts whose device
- * memory all belongs to their own pool allocator, real-time loops where an
- * allocation could synchronise the device).
+ * (hosts whose device memory all belongs to their own pool allocator, where
+ * an allocation behind the pool's back could fail or fragment it; real-time
+ * loops where an allocation is not allowed because it can synchronise the
+ * device).
  *   h      : device pointer, dense row-major [ny][nx] of dtype (SWOF_FP64
  *            double or SWOF_FP32 float) on the current device; caller-owned.
  *   out    : device pointer to 2 doubles, caller-owned: out[0] = volume
- *            [m^3], out[1] = min h.
+ *            [m^3], out[1] = min h (NaN if h holds a NaN).
  *   stream : cudaStream_t to enqueue on (NULL = the default stream); the
  *            call is asynchronous and returns once the kernels are queued.
  * Scratch is one fixed file-scope device array of 2 * SWOF_NOALLOC_MAX_ROWS
  * doubles (1 MiB), held by every GPU that loads the library until the
  * process exits; ny > SWOF_NOALLOC_MAX_ROWS is rejected with SWOF_EINVAL.
- * The first call on a device looks up that array's device address (once per
- * device), so make the first call on each device before any stream capture.
+ * The first call on a device looks up that array's device address and loads
+ * this entry point's kernels (once per device), so make the first call on
+ * each device before any stream capture.
  * All calls share the array: calls that overlap on the GPU race and must be
  * serialised by the caller.  The sum is a fixed-order reduction (per row,
  * then over rows), so repeated calls on the same data agree bit for bit.
- * Errors: SWOF_EINVAL (NULL, size, dtype), SWOF_ECUDA. */
+ * Errors: SWOF_EINVAL (NULL, size, dtype), SWOF_ECUDA (a launch failed; or
+ * a CUDA error was already pending on the calling thread: then nothing is
+ * launched and that error is left for the caller to read). */
 #define SWOF_NOALLOC_MAX_ROWS 65536
 SWOF_API int swof_volume_noalloc(const void *h, int nx, int ny, int dtype, double dx, double dy,
                                  double *out, void *stream);
@@ -476,6 +481,23 @@ SWOF_API const char *swof_strerror(int code);
 
 /* Library build information (static storage). */
 SWOF_API const char *swof_version(void);
+
+/* Debug build (libswof_debug.so, compiled with SWOF_BOUNDS_CHECK): every
+ * padded-array index the stencil kernels form, every ring slot the stage
+ * kernels read and every tensor-copy origin is checked on the device; a
+ * failed check clamps the index to element 0 (no access leaves the arrays)
+ * and latches SWOF_EBOUNDS in the context's status word, which swof_step
+ * (with info), swof_get_diagnostics and every later launch see.  Not in the
+ * paper: a checking aid.
+ * swof_debug_build returns 1 in the debug build, 0 otherwise.
+ * swof_debug_probe_index runs one thread that forms the padded index of
+ * cell (i, j) of ctx's grid (i, j may lie outside [-2, nx+1] x [-2, ny+1])
+ * through the checked path and reads the element there, so a test can see a
+ * failed check latch SWOF_EBOUNDS without any out-of-range access.
+ * Synchronises; returns the latched status (SWOF_OK when the index was in
+ * range), or SWOF_ESTATE in the release build. */
+SWOF_API int swof_debug_build(void);
+SWOF_API int swof_debug_probe_index(swof_ctx *ctx, int i, int j);
 
 #ifdef __cplusplus
 }

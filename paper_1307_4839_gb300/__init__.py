@@ -14,16 +14,20 @@ import threading
 
 import numpy as np
 
-from .build import LIB as _LIB_PATH
+from .build import LIB as _LIB_RELEASE
+from .build import LIB_DEBUG as _LIB_DEBUG
 from .build import build
+
+# SWOF_LIB_VARIANT=debug selects the index-checking build (build(debug=True))
+_LIB_PATH = _LIB_DEBUG if os.environ.get("SWOF_LIB_VARIANT", "") == "debug" else _LIB_RELEASE
 
 __all__ = ["build", "load", "Solver", "SwofError", "SwofParams", "SwofDiag", "SwofStepInfo",
            "FP64", "FP32", "BC_WALL", "BC_OUTFLOW", "BC_IMPOSED_H", "BC_IMPOSED_Q", "BC_IMPOSED_HQ",
            "FRIC_NONE", "FRIC_MANNING", "FRIC_STRICKLER", "FRIC_DARCY", "FRIC_CHEZY", "ORDER_1",
            "ORDER_2", "flow_directions"]
 
-OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ENEGATIVE, ECFL, EDTSEQ, ETIMEOUT, EDTUNDERFLOW, ESTATE = (
-    0, -1, -2, -3, -4, -5, -6, -7, -8, -9, -10)
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ENEGATIVE, ECFL, EDTSEQ, ETIMEOUT, EDTUNDERFLOW, ESTATE, EBOUNDS = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8, -9, -10, -11)
 FP64, FP32 = 0, 1
 CFL_SUM, CFL_MIN = 0, 1
 BC_WALL, BC_OUTFLOW, BC_IMPOSED_H, BC_IMPOSED_Q, BC_IMPOSED_HQ = 0, 1, 2, 3, 4
@@ -153,6 +157,8 @@ _SIGS = {
                                             ctypes.POINTER(ctypes.c_float), ctypes.c_void_p, ctypes.c_void_p]),
     "swof_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "swof_version": (ctypes.c_char_p, []),
+    "swof_debug_build": (ctypes.c_int, []),
+    "swof_debug_probe_index": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
 }
 
 
@@ -389,6 +395,11 @@ class Solver:
         _check(load().swof_get_dt_history(self._ctx, _ptr(out), int(n), ctypes.byref(cnt)),
                "swof_get_dt_history")
         return out[:cnt.value]
+
+    def debug_probe_index(self, i: int, j: int) -> int:
+        """Debug build only: form the padded index of cell (i, j) through the
+        checked path (swof_debug_probe_index); returns the status code."""
+        return int(load().swof_debug_probe_index(self._ctx, int(i), int(j)))
 
     def diagnostics(self) -> dict:
         d = SwofDiag()

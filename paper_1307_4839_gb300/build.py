@@ -2,7 +2,9 @@
 
 Each .cu file under csrc/ is compiled separately (in parallel); the FP64
 unit gets -fmad=false so no multiply-add is contracted.  The result lands in
-paper_1307_4839_gb300/_build/libswof.so (git-ignored).
+paper_1307_4839_gb300/_build/libswof.so (git-ignored).  build(debug=True)
+builds the index-checking variant (-DSWOF_BOUNDS_CHECK=1) into
+_build/debug/libswof_debug.so.
 """
 from __future__ import annotations
 
@@ -16,6 +18,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libswof.so")
+BUILD_DEBUG = os.path.join(BUILD, "debug")
+LIB_DEBUG = os.path.join(BUILD_DEBUG, "libswof_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
           "--expt-relaxed-constexpr"]
@@ -50,19 +54,22 @@ def _stale(obj: str, src: str) -> bool:
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False, debug: bool = False) -> str:
+    out_dir = BUILD_DEBUG if debug else BUILD
+    lib = LIB_DEBUG if debug else LIB
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = _nvcc()
     jobs = []
     for f in sources():
         src = os.path.join(CSRC, f)
-        obj = os.path.join(BUILD, f.replace(".cu", ".o"))
+        obj = os.path.join(out_dir, f.replace(".cu", ".o"))
         if force or _stale(obj, src):
-            cmd = [nvcc, *ARCH, *COMMON, *PER_FILE.get(f, []), "-c", src, "-o", obj]
+            cmd = [nvcc, *ARCH, *COMMON, *PER_FILE.get(f, []), *(["-DSWOF_BOUNDS_CHECK=1"] if debug else []),
+                   "-c", src, "-o", obj]
             if ptxas_v:
                 cmd.insert(1, "-Xptxas=-v")
             jobs.append((f, cmd))
-    objs = [os.path.join(BUILD, f.replace(".cu", ".o")) for f in sources()]
+    objs = [os.path.join(out_dir, f.replace(".cu", ".o")) for f in sources()]
 
     def run(job):
         name, cmd = job
@@ -78,15 +85,15 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             list(ex.map(run, jobs))
-    if jobs or not os.path.exists(LIB):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if jobs or not os.path.exists(lib):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-fPIC"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True, ptxas_v="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_v="-v" in sys.argv, debug="--debug" in sys.argv))

@@ -3,6 +3,7 @@
 // kernels (swof_kernels.cuh); this file only lays out memory, converts
 // host arrays and enqueues launches.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cmath>
 #include <cstdio>
@@ -301,6 +302,7 @@ int enqueue_steps(swof_ctx *c, int n)
     auto s1 = [&]() { return o1 ? c->L->stage1_o1(c->P, f, c->stream) : c->L->stage1(c->P, f, c->stream); };
     auto s2 = [&]() { return o1 ? c->L->commit_o1(c->P, f, c->stream) : c->L->stage2(c->P, f, c->stream); };
     for (int s = 0; s < n && !r; ++s) {
+        nvtxRangePushA("step");
         if (c->timing) {
             while ((int)c->ev.size() < c->ev_used + 4) {
                 cudaEvent_t e;
@@ -308,17 +310,29 @@ int enqueue_steps(swof_ctx *c, int n)
                 c->ev.push_back(e);
             }
             cudaEventRecord(c->ev[c->ev_used + 0], c->stream);
+            nvtxRangePushA("wave speeds + dt");
             r = first();
+            nvtxRangePop();
             cudaEventRecord(c->ev[c->ev_used + 1], c->stream);
+            nvtxRangePushA("stage 1");
             if (!r) r = s1();
+            nvtxRangePop();
             cudaEventRecord(c->ev[c->ev_used + 2], c->stream);
+            nvtxRangePushA("stage 2");
             if (!r) r = s2();
+            nvtxRangePop();
             cudaEventRecord(c->ev[c->ev_used + 3], c->stream);
             c->ev_used += 4;
         } else {
+            nvtxRangePushA("wave speeds + dt");
             r = first();
+            nvtxRangePop();
+            nvtxRangePushA("stage 1");
             if (!r) r = s1();
+            nvtxRangePop();
+            nvtxRangePushA("stage 2");
             if (!r) r = s2();
+            nvtxRangePop();
         }
         if (!r && c->hmax) {
             r = c->L->hmax(c->P, f, c->stream);
@@ -330,6 +344,7 @@ int enqueue_steps(swof_ctx *c, int n)
         }
         c->lam_valid = o1 || c->P.fuse_lambda != 0;
         c->launches_last += 3;
+        nvtxRangePop();
     }
     return r ? SWOF_ECUDA : SWOF_OK;
 }
@@ -451,6 +466,7 @@ int swof_create(int nx, int ny, double dx, double dy, const double *z, const swo
     P.fdtheta = (float)P.dtheta;
     P.fks = (float)P.ks;
     P.fuse_lambda = 1;
+    P.status = nullptr;           // set once the control block exists
 
     if (p->stream) {
         c->stream = (cudaStream_t)p->stream;
@@ -464,6 +480,7 @@ int swof_create(int nx, int ny, double dx, double dy, const double *z, const swo
     int st = cuda_err((cudaError_t)c->L->configure());
     if (!st) {
         c->ctl = dalloc<DevCtl>(c, 1, &st);
+        if (!st) c->P.status = &c->ctl->status;
         c->d_red = dalloc<double>(c, 4 * 240, &st);
     }
     if (!st) st = c->prec == SWOF_FP64 ? alloc_fields<double>(c, c->f64, z, p) : alloc_fields<float>(c, c->f32, z, p);
@@ -641,8 +658,15 @@ int swof_set_time(swof_ctx *c, double t)
     return cuda_err(cudaGetLastError());
 }
 
+// NVTX range over a scope (no-op unless a profiler is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 int swof_step(swof_ctx *c, int n, swof_step_info *info)
 {
+    NvtxRange range("swof_step");
     if (!c || n < 0) return SWOF_EINVAL;
     int st = ensure_hist(c, n);
     if (st) return st;
@@ -1102,10 +1126,27 @@ const char *swof_strerror(int code)
     case SWOF_ETIMEOUT: return "bounded device wait timed out";
     case SWOF_EDTUNDERFLOW: return "time step below dt_min";
     case SWOF_ESTATE: return "call not valid in this state";
+    case SWOF_EBOUNDS: return "a kernel index check failed (debug build)";
     default: return "unknown status";
     }
 }
 
-const char *swof_version(void) { return "libswof 0.1 (sm_103a; FP64 exact-order + FP32 bulk)"; }
+const char *swof_version(void)
+{
+    return SWOF_BOUNDS_CHECK ? "libswof 0.2 debug (sm_103a; FP64 exact-order + FP32 bulk; index checks)"
+                             : "libswof 0.2 (sm_103a; FP64 exact-order + FP32 bulk)";
+}
+
+int swof_debug_build(void) { return SWOF_BOUNDS_CHECK ? 1 : 0; }
+
+int swof_debug_probe_index(swof_ctx *c, int i, int j)
+{
+    if (!c) return SWOF_EINVAL;
+    if (!SWOF_BOUNDS_CHECK) return SWOF_ESTATE;
+    if (c->L->probe(c->P, c->fields(), i, j, c->stream)) return SWOF_ECUDA;
+    DevCtl d;
+    int st = read_ctl(c, &d);
+    return st ? st : d.status;
+}
 
 }  // extern "C"

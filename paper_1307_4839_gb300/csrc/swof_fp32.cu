@@ -12,7 +12,7 @@ const Launch &launch_fp32()
                              launch_stage1_o1_t<float>, launch_commit_o1_t<float>, launch_gauges_t<float>, launch_hmax_t<float>,
                              launch_pack1_t<float>,
                              launch_reduce_t<float>, stage_slots, launch_unpack_t<float>,
-                             launch_pack_t<float>};
+                             launch_pack_t<float>, launch_probe_t<float>};
     return L;
 }
 

@@ -13,7 +13,7 @@ const Launch &launch_fp64()
                              launch_stage1_o1_t<double>, launch_commit_o1_t<double>, launch_gauges_t<double>, launch_hmax_t<double>,
                              launch_pack1_t<double>,
                              launch_reduce_t<double>, stage_slots, launch_unpack_t<double>,
-                             launch_pack_t<double>};
+                             launch_pack_t<double>, launch_probe_t<double>};
     return L;
 }
 

@@ -18,6 +18,11 @@
 
 #include "../../include/swof.h"
 
+// Debug build: device-side index checks (libswof_debug.so; see swof.h).
+#ifndef SWOF_BOUNDS_CHECK
+#define SWOF_BOUNDS_CHECK 0
+#endif
+
 namespace swof {
 
 // Per-context control block in device memory: the CFL reduction words, the
@@ -64,6 +69,7 @@ struct Params {
     int no_budget;             // 1: stage kernels leave the budget slots alone (timing runs)
     int fuse_lambda;           // 1: stage 2 adds the wave speeds of U^{n+1} of its tile interiors
     int lam_partial;           // 1: the wave-speed kernel only reduces (no dt control)
+    int *status;               // the context's latched status word (debug build: failed index checks)
 };
 
 // Stage-kernel shapes: threads per CTA along x, rows per CTA, and how the
@@ -155,6 +161,8 @@ struct Launch {
     int (*unpack)(const Params &, void *fields, const void *h, const void *qx, const void *qy,
                   int dtype, void *stream);
     int (*pack)(const Params &, void *fields, void *h, void *qx, void *qy, int dtype, void *stream);
+    // debug build: form the padded index of cell (i, j) through the checked path
+    int (*probe)(const Params &, void *fields, int i, int j, void *stream);
 };
 
 const Launch &launch_fp64();

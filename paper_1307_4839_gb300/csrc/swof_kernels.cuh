@@ -412,8 +412,27 @@ __device__ __forceinline__ void face_flux(T g, T hpa, T zpa, T unpa, T utpa,
     f3 = F2;
 }
 
+// Index checks of the debug build (SWOF_BOUNDS_CHECK): a failed check
+// latches SWOF_EBOUNDS in the context's status word and the caller uses a
+// safe value instead.  Compiled out otherwise.
+__device__ __forceinline__ bool bounds_ok(const Params &P, bool ok)
+{
+    if constexpr (SWOF_BOUNDS_CHECK) {
+        if (!ok && P.status) atomicCAS(P.status, 0, SWOF_EBOUNDS);
+        return ok;
+    } else {
+        (void)P;
+        return true;
+    }
+}
+
+// Element of cell (gi, gj), gi in [-2, nx + 1 + padding], gj in [-2, ny + 1],
+// of a padded field.
 __device__ __forceinline__ size_t pidx(const Params &P, int gi, int gj)
 {
+    if constexpr (SWOF_BOUNDS_CHECK) {
+        if (!bounds_ok(P, gj >= -2 && gj <= P.ny + 1 && gi + P.lpad >= 0 && gi + P.lpad < P.pitch)) return 0;
+    }
     return (size_t)(gj + 2) * (size_t)P.pitch + (size_t)(gi + P.lpad);
 }
 
@@ -1235,5 +1254,23 @@ int launch_pack_t(const Params &P, void *f, void *h, void *qx, void *qy, int dty
 }
 
 inline int stage_slots(const Params &P) { return max_stage_blocks(P.nx, P.ny); }
+
+// One thread forms the padded index of cell (i, j) through pidx() and reads
+// the depth there (debug build: a failed check reads element 0 instead).
+template <typename T>
+__global__ void k_probe(Params P, Fields<T> F, int i, int j)
+{
+    const size_t o = pidx(P, i, j);
+    volatile T x = F.h[o];
+    (void)x;
+}
+
+template <typename T>
+int launch_probe_t(const Params &P, void *f, int i, int j, void *stream)
+{
+    const Fields<T> &F = *static_cast<const Fields<T> *>(f);
+    k_probe<T><<<1, 1, 0, (cudaStream_t)stream>>>(P, F, i, j);
+    return (int)cudaGetLastError();
+}
 
 }  // namespace swof

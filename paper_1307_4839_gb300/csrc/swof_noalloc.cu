@@ -1,10 +1,10 @@
 // swof_noalloc.cu -- swof_volume_noalloc: water volume and minimum depth of a
 // caller-owned depth field, with no device allocation at all.
 //
-// Who needs this: code that may not call cudaMalloc -- a caller that records
-// its work into a CUDA graph it captures itself, a host that hands every
-// byte of device memory to its own pool allocator, or a real-time loop where
-// an allocation (which can synchronise the device) is not allowed.  Such a
+// Who needs this: code that may not call cudaMalloc -- a host that hands
+// every byte of device memory to its own pool allocator (a cudaMalloc behind
+// its back could fail or fragment the pool), or a real-time loop where an
+// allocation is not allowed because it can synchronise the device.  Such a
 // caller passes its own input and output pointers; the only scratch is the
 // file-scope array below, fixed at load time.
 //
@@ -34,8 +34,14 @@ constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
 double *g_rows_ptr[MAX_DEVICES] = {};
 
-// Device address of g_rows on the current device (looked up once per device;
-// host code cannot use the symbol itself as a device pointer).
+template <typename S>
+__global__ void k_row_partials(const S *h, int nx, int ny, double *rows);
+__global__ void k_rows_final(const double *rows, int ny, double area, double *out);
+
+// Device address of g_rows on the current device, looked up once per device
+// (host code cannot use the symbol itself as a device pointer).  The same
+// one-time set-up also loads this file's three kernels on the device
+// (cudaFuncGetAttributes), so no later call has a module load left to do.
 int rows_ptr(double **out)
 {
     int dev = 0;
@@ -45,18 +51,27 @@ int rows_ptr(double **out)
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_rows);
         if (e != cudaSuccess || !p) return SWOF_ECUDA;
+        cudaFuncAttributes a;
+        if (cudaFuncGetAttributes(&a, k_row_partials<double>) != cudaSuccess ||
+            cudaFuncGetAttributes(&a, k_row_partials<float>) != cudaSuccess ||
+            cudaFuncGetAttributes(&a, k_rows_final) != cudaSuccess)
+            return SWOF_ECUDA;
         g_rows_ptr[dev] = static_cast<double *>(p);
     }
     *out = g_rows_ptr[dev];
     return SWOF_OK;
 }
 
+// min that keeps a NaN (fmin would drop it): a field holding NaN reports
+// NaN as its minimum depth, so a positivity check on out[1] sees it
+__device__ __forceinline__ double min_nan(double m, double v) { return (v != v || m != m) ? NAN : fmin(m, v); }
+
 __device__ __forceinline__ void block_sum_min(double &s, double &m, double *rs, double *rm)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         s += __shfl_xor_sync(0xffffffffu, s, o);
-        m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+        m = min_nan(m, __shfl_xor_sync(0xffffffffu, m, o));
     }
     if ((threadIdx.x & 31) == 0) {
         rs[threadIdx.x >> 5] = s;
@@ -68,7 +83,7 @@ __device__ __forceinline__ void block_sum_min(double &s, double &m, double *rs, 
         m = INFINITY;
         for (int w = 0; w < ROW_THREADS / 32; ++w) {
             s += rs[w];
-            m = fmin(m, rm[w]);
+            m = min_nan(m, rm[w]);
         }
     }
     __syncthreads();
@@ -84,7 +99,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_row_partials(const S *h, int nx
         for (int i = threadIdx.x; i < nx; i += ROW_THREADS) {
             double v = (double)row[i];
             s += v;
-            m = fmin(m, v);
+            m = min_nan(m, v);
         }
         block_sum_min(s, m, rs, rm);
         if (threadIdx.x == 0) {
@@ -100,7 +115,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_rows_final(const double *rows, 
     double s = 0.0, m = INFINITY;
     for (int j = threadIdx.x; j < ny; j += ROW_THREADS) {
         s += rows[2 * j];
-        m = fmin(m, rows[2 * j + 1]);
+        m = min_nan(m, rows[2 * j + 1]);
     }
     block_sum_min(s, m, rs, rm);
     if (threadIdx.x == 0) {
@@ -117,6 +132,9 @@ extern "C" int swof_volume_noalloc(const void *h, int nx, int ny, int dtype, dou
     if (!h || !out || nx < 1 || ny < 1 || !(dx > 0) || !(dy > 0)) return SWOF_EINVAL;
     if (dtype != SWOF_FP64 && dtype != SWOF_FP32) return SWOF_EINVAL;
     if (ny > SWOF_NOALLOC_MAX_ROWS) return SWOF_EINVAL;   // beyond the fixed scratch
+    // a CUDA error already pending on this thread belongs to the caller's own
+    // earlier work: leave it to the caller, launch nothing
+    if (cudaPeekAtLastError() != cudaSuccess) return SWOF_ECUDA;
     double *rows = nullptr;
     int st = rows_ptr(&rows);
     if (st) return st;

@@ -225,6 +225,8 @@ __device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, 
     const int x0 = bx * W - 2 + P.lpad;
     auto issue_block = [&](int b) {
         if (b >= nblk) return;
+        // a tensor copy starts on a 16-byte boundary
+        if (!bounds_ok(P, (x0 * (int)sizeof(T)) % 16 == 0 && b >= 0)) return;
         const int sl = b % RD;
         const uint32_t bar = tc05::smem_u32(&S.bar[sl]);
         T *base = ring + sl * (NF * RR * NTX);
@@ -244,6 +246,7 @@ __device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, 
     };
     // a row of the ring (field f at rowp[f * RR * NTX])
     auto ring_row = [&](int kk) -> const T * {
+        if (!bounds_ok(P, kk >= 0 && kk < H + 4)) kk = 0;
         return ring + ((kk / RR) % RD) * (NF * RR * NTX) + (kk & (RR - 1)) * NTX + t;
     };
     bool ring_ok = true;

@@ -60,3 +60,16 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     assert _call(lib, h, 1, sw.NOALLOC_MAX_ROWS + 1, sw.FP64, 1.0, 1.0, out, 0) == sw.EINVAL
     assert _call(lib, h, 2, 2, 7, 1.0, 1.0, out, 0) == sw.EINVAL
     assert lib.swof_volume_noalloc(None, 2, 2, sw.FP64, 1.0, 1.0, ctypes.c_void_p(out.data_ptr()), None) == sw.EINVAL
+
+
+def test_noalloc_min_depth_keeps_nan():
+    """A depth field holding a NaN reports NaN as its minimum (a positivity
+    check on out[1] must not pass such a field)."""
+    import torch
+    lib = sw.load()
+    h = torch.rand((37, 53), dtype=torch.float64, device="cuda")
+    h[20, 7] = float("nan")
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    assert _call(lib, h, 53, 37, sw.FP64, 1.0, 1.0, out, torch.cuda.current_stream().cuda_stream) == sw.OK
+    torch.cuda.synchronize()
+    assert torch.isnan(out[1]).item() and torch.isnan(out[0]).item()
