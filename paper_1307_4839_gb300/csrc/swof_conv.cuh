@@ -720,9 +720,12 @@ __global__ void __launch_bounds__(TmaCfg<NT>::THREADS)
 namespace swof {
 
 // ---------------------------------------------------------------------------
-// Weight gradient:  dW[n][k] += sum_p G[p, n] * X[p, k]  (FP32 atomics),
-// a GEMM with M' = n (output columns of the layer), N' = k, reduced over
-// pixels p.  G is the layer's output gradient (bf16, [P][gc]) -- for the
+// Weight gradient:  dW[n][k] += sum_p G[p, n] * X[p, k], a GEMM with M' = n
+// (output columns of the layer), N' = k, reduced over pixels p.  The pixel
+// range is split over the grid's z dimension; split z writes its partial
+// sum to part[z][n][k] and k_wgrad_sum adds the splits in index order, so
+// the result does not depend on which CTA finishes first (training is
+// reproducible bit for bit).  G is the layer's output gradient (bf16, [P][gc]) -- for the
 // transposed conv gathered from the 2x-resolution tensor (row n = sub *
 // cout + o); X is the layer's input, gathered like the forward A operand
 // (3x3 taps or 1x1).  Both are staged transposed (pixels along K) with an
@@ -736,7 +739,8 @@ struct WgradArgs {
     int B, H, W;               // pixel grid of the reduction
     int nrows;                 // M' (number of valid rows n)
     int Kp;                    // row length of dW (padded K)
-    float *dw;                 // [nrows][Kp] FP32, accumulated atomically
+    float *dw;                 // [nrows][Kp] FP32, accumulated (+=) by k_wgrad_sum
+    float *part;               // [splits][nrows][Kp] FP32 partial sums (scratch)
     int chunks_per_cta;        // pixel chunks (64 pixels) per CTA
     int *err;
 };
@@ -912,9 +916,10 @@ __global__ void __launch_bounds__(128) k_wgrad(WgradArgs A)
             float v[16];
             tc05::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
             if (n < A.nrows) {
+                float *row = A.part + ((long long)blockIdx.z * A.nrows + n) * A.Kp + kb0 + c0;
 #pragma unroll
                 for (int i = 0; i < 16; ++i)
-                    if (kb0 + c0 + i < A.Kp) atomicAdd(&A.dw[(long long)n * A.Kp + kb0 + c0 + i], v[i]);
+                    if (kb0 + c0 + i < A.Kp) row[i] = v[i];
             }
         }
     } else if (tid == 0 && A.err) {
@@ -923,6 +928,16 @@ __global__ void __launch_bounds__(128) k_wgrad(WgradArgs A)
     tc05::fence_before();
     __syncthreads();
     if (warp == 0) tc05::tmem_dealloc(tmem, 256);
+}
+
+// dW[e] += sum over the splits z = 0, 1, ... of part[z][e], in that order.
+__global__ void k_wgrad_sum(const float *part, int splits, long long n, float *dw)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        float s = 0.0f;
+        for (int z = 0; z < splits; ++z) s += part[(long long)z * n + e];
+        dw[e] += s;
+    }
 }
 
 }  // namespace swof

@@ -55,15 +55,35 @@ __global__ void k_act_bwd(const float *dy, int dyc, int dyc0, const bf16 *z, int
 }
 
 // column sums of a bf16 [P][N] matrix into db[n % nb] (atomics)
-__global__ void k_colsum(const bf16 *dz, long long P, int N, int nb, float *db)
+// Column sums of dz in two fixed-order passes (the result does not depend
+// on the order blocks run in): k_colsum writes each block's sums part[b][n]
+// (each thread owns one column n and a strided set of rows; the block's row
+// lanes are added in lane order), k_colsum_fin adds, per bias b, the columns
+// n = b (mod nb) and the blocks in index order to db[b].
+__global__ void k_colsum(const bf16 *dz, long long P, int N, float *part)
 {
-    // each thread owns one column n and a strided set of rows
+    extern __shared__ float lanes[];           // [rlanes][N]
     int n = threadIdx.x % N;
     int rlane = threadIdx.x / N, rlanes = blockDim.x / N;
     float s = 0.0f;
     for (long long p = blockIdx.x * (long long)rlanes + rlane; p < P; p += (long long)gridDim.x * rlanes)
         s += __bfloat162float(dz[p * N + n]);
-    atomicAdd(&db[n % nb], s);
+    if (rlane < rlanes) lanes[rlane * N + n] = s;
+    __syncthreads();
+    if (rlane == 0) {
+        float t = 0.0f;
+        for (int r = 0; r < rlanes; ++r) t += lanes[r * N + n];
+        part[(long long)blockIdx.x * N + n] = t;
+    }
+}
+__global__ void k_colsum_fin(const float *part, int blocks, int N, int nb, float *db)
+{
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+        float t = 0.0f;
+        for (int k = 0; k < blocks; ++k)
+            for (int n = b; n < N; n += nb) t += part[(long long)k * N + n];
+        db[b] += t;
+    }
 }
 
 // 2x2 average pooling: x (channels [xc0, xc0+C) of stride cx) at H x W ->
@@ -107,8 +127,8 @@ __global__ void k_pool_bwd_add(const float *dy, int B, int H, int W, int C, floa
 
 // Mean squared error over the first nch of 16 output channels; writes the
 // gradient d(pred) = 2 (pred - tgt) / (P * nch) (0 on unused channels) and
-// adds the loss sum (FP64).
-__global__ void k_mse(const float *pred, const float *tgt, long long P, int nch, float *dpred, double *loss)
+// writes each block's loss sum (FP64) to part[block] (k_sum_blocks adds them).
+__global__ void k_mse(const float *pred, const float *tgt, long long P, int nch, float *dpred, double *part)
 {
     __shared__ double red[32];
     double s = 0.0;
@@ -130,7 +150,16 @@ __global__ void k_mse(const float *pred, const float *tgt, long long P, int nch,
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        atomicAdd(loss, t);
+        part[blockIdx.x] = t;
+    }
+}
+// the loss: the blocks' sums in index order
+__global__ void k_sum_blocks(const double *part, int n, double *loss)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < n; ++k) t += part[k];
+        *loss += t;
     }
 }
 
@@ -478,33 +507,51 @@ int conv(ConvArgs A, cudaStream_t s)
     }
 }
 
+// Column tile of the weight-gradient kernel for a row length ncols, and the
+// grid of one launch: gx x gy output tiles, the P pixels split over gz CTAs
+// (about two CTAs per SM in all) of chunks_per_cta 64-pixel chunks each.
+int wgrad_nt(int ncols) { return ncols % 256 == 0 ? 256 : (ncols % 128 == 0 ? 128 : 64); }
+void wgrad_grid(int nrows, int ncols, long long P, unsigned *gx, unsigned *gy, unsigned *gz, int *chunks_per_cta)
+{
+    const int NT = wgrad_nt(ncols);
+    const long long chunks = (P + 63) / 64;
+    *gx = (unsigned)((nrows + 127) / 128);
+    *gy = (unsigned)((ncols + NT - 1) / NT);
+    long long splits = (2 * 152) / ((long long)*gx * *gy);
+    if (splits < 1) splits = 1;
+    if (splits > chunks) splits = chunks;
+    *chunks_per_cta = (int)((chunks + splits - 1) / splits);
+    *gz = (unsigned)((chunks + *chunks_per_cta - 1) / *chunks_per_cta);
+}
+
 template <int NT>
 int wgrad_launch(WgradArgs A, int ncols, cudaStream_t s)
 {
     size_t smem = sizeof(ConvSmem) + 1024;
     if (cudaFuncSetAttribute(k_wgrad<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return SWOF_ECUDA;
-    long long P = (long long)A.B * A.H * A.W;
-    long long chunks = (P + 63) / 64;
-    unsigned gx = (unsigned)((A.nrows + 127) / 128), gy = (unsigned)((ncols + NT - 1) / NT);
-    long long target = 2 * 152;      // CTAs to spread the pixel reduction over
-    long long splits = target / (gx * gy);
-    if (splits < 1) splits = 1;
-    if (splits > chunks) splits = chunks;
-    A.chunks_per_cta = (int)((chunks + splits - 1) / splits);
-    unsigned gz = (unsigned)((chunks + A.chunks_per_cta - 1) / A.chunks_per_cta);
+    unsigned gx, gy, gz;
+    wgrad_grid(A.nrows, ncols, (long long)A.B * A.H * A.W, &gx, &gy, &gz, &A.chunks_per_cta);
     k_wgrad<NT><<<dim3(gx, gy, gz), 128, smem, s>>>(A);
+    if (cudaGetLastError() != cudaSuccess) return SWOF_ECUDA;
+    const long long n = (long long)A.nrows * A.Kp;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 4 * 152) blocks = 4 * 152;
+    k_wgrad_sum<<<(unsigned)blocks, 256, 0, s>>>(A.part, (int)gz, n, A.dw);
     return cudaGetLastError() == cudaSuccess ? SWOF_OK : SWOF_ECUDA;
 }
 
 int wgrad(WgradArgs A, int ncols, cudaStream_t s)
 {
-    if (A.cin < 8 || (A.cin & (A.cin - 1)) || (long long)A.B * A.H * A.W >= (1LL << 31) / 4) return SWOF_EINVAL;
+    if (A.cin < 8 || (A.cin & (A.cin - 1)) || (long long)A.B * A.H * A.W >= (1LL << 31) / 4 || !A.part)
+        return SWOF_EINVAL;
     A.cin_shift = 0;
     while ((1 << A.cin_shift) < A.cin) ++A.cin_shift;
-    if (ncols % 256 == 0) return wgrad_launch<256>(A, ncols, s);
-    if (ncols % 128 == 0) return wgrad_launch<128>(A, ncols, s);
-    return wgrad_launch<64>(A, ncols, s);
+    switch (wgrad_nt(ncols)) {
+    case 256: return wgrad_launch<256>(A, ncols, s);
+    case 128: return wgrad_launch<128>(A, ncols, s);
+    default: return wgrad_launch<64>(A, ncols, s);
+    }
 }
 
 }  // namespace swof
@@ -555,6 +602,8 @@ struct swof_unet {
     double *loss = nullptr;
     int *err = nullptr;
     float *norm = nullptr;        // mean[16], inv[16], scale[16] (device)
+    float *wg_part = nullptr;     // partial sums: weight-gradient pixel splits, bias-gradient and loss blocks
+    size_t wg_part_n = 0;
     long long step = 0;
     std::vector<void *> allocs;
 };
@@ -703,7 +752,8 @@ int bwd_layer(swof_unet *u, int l, int B, int ih, int iw, Act in, const float *d
         if (threads > 1024) threads = L.cout;
         long long blocks = (Po + per - 1) / per;
         if (blocks > 1024) blocks = 1024;
-        swof::k_colsum<<<(unsigned)blocks, threads, 0, s>>>(u->dz, Po, L.cout, L.cout, GB(u, l));
+        swof::k_colsum<<<(unsigned)blocks, threads, threads * sizeof(float), s>>>(u->dz, Po, L.cout, u->wg_part);
+        swof::k_colsum_fin<<<1, 256, 0, s>>>(u->wg_part, (int)blocks, L.cout, L.cout, GB(u, l));
     }
     // weight gradient
     swof::WgradArgs G{};
@@ -722,7 +772,14 @@ int bwd_layer(swof_unet *u, int l, int B, int ih, int iw, Act in, const float *d
     G.nrows = L.ncols;
     G.Kp = L.Kp;
     G.dw = GW(u, l);
+    G.part = u->wg_part;
     G.err = u->err;
+    {
+        unsigned gx, gy, gz;
+        int cpc;
+        swof::wgrad_grid(G.nrows, L.Kp, (long long)B * ih * iw, &gx, &gy, &gz, &cpc);
+        if ((size_t)gz * (size_t)G.nrows * (size_t)G.Kp > u->wg_part_n) return SWOF_EINVAL;   // (sized at creation)
+    }
     int st = swof::wgrad(G, L.Kp, s);
     if (st || !dx) return st;
     // data gradient
@@ -836,7 +893,9 @@ int loss_and_grads(swof_unet *u, int B, cudaStream_t s)
     cudaMemsetAsync(u->loss, 0, sizeof(double), s);
     int st = forward(u, B, s);
     if (st) return st;
-    swof::k_mse<<<swof::grid_for(P * 16), 256, 0, s>>>(u->out, u->tgt, P, u->out_ch, u->gpred, u->loss);
+    const int mb = swof::grid_for(P * 16);
+    swof::k_mse<<<mb, 256, 0, s>>>(u->out, u->tgt, P, u->out_ch, u->gpred, reinterpret_cast<double *>(u->wg_part));
+    swof::k_sum_blocks<<<1, 32, 0, s>>>(reinterpret_cast<const double *>(u->wg_part), mb, u->loss);
     return backward(u, B, s);
 }
 
@@ -961,6 +1020,24 @@ int swof_unet_create(int base, int in_ch, int out_ch, int H, int W, int max_batc
     }
     maxdz = maxdz > (size_t)(P0 * 16) ? maxdz : (size_t)(P0 * 16);
     u->dz = dmalloc<bf16>(u, maxdz, &st);
+    {
+        // partial sums of the weight gradients: the largest splits x rows x
+        // columns over the layers (a layer's pixel count is at most P0, and
+        // fewer pixels give no more splits)
+        size_t need = 0;
+        for (const Layer &L : u->layers) {
+            unsigned gx, gy, gz;
+            int cpc;
+            swof::wgrad_grid(L.ncols, L.Kp, P0, &gx, &gy, &gz, &cpc);
+            size_t n = (size_t)gz * (size_t)L.ncols * (size_t)L.Kp;
+            need = need > n ? need : n;
+        }
+        // (also the bias-gradient and loss partial sums: <= 1024 blocks x 256
+        // columns of floats, 152 x 16 doubles)
+        need = need > (size_t)1024 * 256 ? need : (size_t)1024 * 256;
+        u->wg_part = dmalloc<float>(u, need, &st);
+        u->wg_part_n = need;
+    }
     if (!st) {
         // Kaiming-normal weights (std sqrt(2 / fan_in)), zero biases, in the
         // logical entries of each padded row

@@ -112,7 +112,23 @@ def test_solver_trajectories_pass_the_checks(ds):
 def test_training_reduces_loss(trained):
     net, losses = trained
     assert np.all(np.isfinite(losses))
-    assert losses[-50:].mean() < 0.3 * losses[:10].mean()
+    assert losses[-50:].mean() < 0.2 * losses[:10].mean()
+
+
+def test_training_is_reproducible(ds):
+    """Two trainings from the same seed give the same losses and weights bit
+    for bit: the weight and bias gradients and the loss are fixed-order
+    reductions (no atomics), the batches come from a seeded generator."""
+    from paper_1307_4839_gb300 import surrogate as S
+    pairs = ds.pairs(TRAIN)
+    runs = []
+    for _ in range(2):
+        net = S.make_net(ds, pairs, base=16, max_batch=16, seed=5)
+        losses = S.train(net, ds, pairs, steps=60, batch=16, lr=2e-3, seed=5)
+        runs.append((np.asarray(losses), net.params()))
+        net.close()
+    assert np.array_equal(runs[0][0], runs[1][0])
+    assert np.array_equal(runs[0][1], runs[1][1])
 
 
 def test_surrogate_gain_over_plain_solver(ds, trained):
@@ -150,7 +166,7 @@ def test_surrogate_gain_over_plain_solver(ds, trained):
           f"{per_span:.3g}, fine FP64 solver {t_fine:.3g}")
     assert e_sur[0] < 0.5 * e_per[0]
     assert e_sur[3] < 0.5 * e_per[3]
-    assert acc.mean() > 0.25     # training is not bit-reproducible (FP32 atomics): measured 0.59-0.79
+    assert acc.mean() > 0.5
     assert per_span < t_fine
 
 
