@@ -83,12 +83,18 @@ constexpr int ring_fields()
 {
     return (std::is_same<T, double>::value ? 4 : 5) + (STAGE == 2 ? 3 : 0);
 }
-// slots: as many blocks (2..4) as fit in 56 KB, so several CTAs share an SM
+// slots: as many blocks (2..4) as fit in RING_CAP bytes, so several CTAs
+// share an SM (FP64: a smaller ring and more resident warps to cover the
+// FP64 pipe's latency)
+#ifndef SWOF_RING_CAP64
+#define SWOF_RING_CAP64 (32 * 1024)
+#endif
 template <typename T, int STAGE, int NTX>
 constexpr int ring_depth()
 {
     constexpr size_t blk = (size_t)ring_fields<T, STAGE>() * RING_ROWS * NTX * sizeof(T);
-    constexpr size_t d = (56 * 1024) / blk;
+    constexpr size_t cap = std::is_same<T, double>::value ? SWOF_RING_CAP64 : 56 * 1024;
+    constexpr size_t d = cap / blk;
     return d < 2 ? 2 : (d > RING_MAX_SLOTS ? RING_MAX_SLOTS : (int)d);
 }
 template <typename T, int STAGE, int NTX>
