@@ -501,7 +501,7 @@ def measure_ensemble(sw, torch, args, ws):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     ens = sw.Ensemble(members, precision=sw.FP32, stream=stream.cuda_stream)
-    tune = ens.autotune(steps=2)
+    tune = ens.autotune(steps=2, cache=os.path.join(ROOT, "paper_1307_4839_gb300", "_build", "autotune.json"))
     ens.step(3)
     torch.cuda.synchronize()
     barrier(ws)
@@ -536,7 +536,7 @@ def measure_ensemble(sw, torch, args, ws):
     return {"value": value, "unit": UNIT, "members": len(members), "cells": cells,
             "steps": args.ens_steps, "ms_total": ms, "launches_per_call": 1,
             "scenario_steps_per_s": ws * len(members) * args.ens_steps / (ms * 1e-3),
-            "sides": sizes, "shape": [tune["ntx"], tune["rows"]], "dtype": "f32",
+            "sides": sizes, "tile_by_side": tune["by_size"], "dtype": "f32",
             "what": "one persistent kernel (queue of step/phase/member/tile items) per call, CUDA graph",
             "plain_fp32_members_one_by_one": plain["fp32"], "plain_fp64_members_one_by_one": plain["fp64"],
             "over_plain_fp32": value / plain["fp32"], "over_plain_fp64": value / plain["fp64"],

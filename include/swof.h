@@ -324,12 +324,14 @@ typedef struct swof_scenario {
     const double *h, *hu, *hv;     /* initial state [ny][nx] host, copied */
     double manning_n;              /* > 0: Manning friction with this n */
     double rain_rate, rain_t_on, rain_t_off;
-    int bc[4];                     /* W, E, S, N */
+    int bc[4];                     /* W, E, S, N: wall, outflow or an imposed edge (Sec. 2.2) */
+    double bc_h[4], bc_q[4];       /* imposed depth / discharge per edge (as in swof_params) */
 } swof_scenario;
 
 /* Create `count` members from specs; every other parameter (precision, g,
- * cfl, h_dry, dt_max, t_end, infiltration off...) comes from *common.
- * Errors: as swof_create / swof_set_state. */
+ * cfl, h_dry, dt_max, t_end, infiltration off...) comes from *common.  The
+ * launch runs the second-order step: common->order = SWOF_ORDER_1 is
+ * SWOF_EINVAL.  Errors: as swof_create / swof_set_state. */
 SWOF_API int swof_ensemble_create(int count, const swof_scenario *specs, const swof_params *common,
                                   swof_ens **out);
 SWOF_API void swof_ensemble_destroy(swof_ens *e);   /* NULL-safe; destroys the members */
@@ -341,12 +343,25 @@ SWOF_API int swof_ensemble_member(swof_ens *e, int k, swof_ctx **ctx);
  * status, or SWOF_ETIMEOUT when a bounded wait ran out (latched: later
  * calls return it). */
 SWOF_API int swof_ensemble_step(swof_ens *e, int n, int *status);
-/* Kernel shapes the ensemble launch can use, the choice, and a tuner that
- * times `steps` steps with each shape and restores every member afterwards
- * (ms: one entry per shape, nullable). */
+/* Member tile shapes (CTA width ntx, rows per tile): swof_ensemble_shapes
+ * writes up to max of them and returns how many exist.  One launch has one
+ * CTA width, each member its own tile height among that width's shapes.
+ * swof_ensemble_set_shape gives every member `shape` (and its width);
+ * swof_ensemble_set_member_shape gives member k a shape of the current
+ * width (SWOF_EINVAL otherwise); swof_ensemble_get_member_shape returns
+ * member k's.  swof_ensemble_autotune times launches of `steps` steps: for
+ * each width, every member on that width's first shape, then per member
+ * size class (grid nx x ny) each other height of the width, kept when the
+ * launch gets faster; the fastest width's choice is applied.  ms (nullable,
+ * 2 entries: widths 128 and 64) gets the ms per step of each width's best,
+ * best the shape of member 0, member_shapes (nullable, count entries) every
+ * member's.  Every member is put back as it was after each timed launch.
+ * Not in the paper: a GB300 launch-shape choice. */
 SWOF_API int swof_ensemble_shapes(int *ntx, int *rows, int max);
 SWOF_API int swof_ensemble_set_shape(swof_ens *e, int shape);
-SWOF_API int swof_ensemble_autotune(swof_ens *e, int steps, double *ms, int *best);
+SWOF_API int swof_ensemble_set_member_shape(swof_ens *e, int k, int shape);
+SWOF_API int swof_ensemble_get_member_shape(const swof_ens *e, int k);
+SWOF_API int swof_ensemble_autotune(swof_ens *e, int steps, double *ms, int *best, int *member_shapes);
 /* Bound on the polls of each wait (default 4M, about a second), and a test
  * hook: block_member >= 0 makes that member's waits impossible so the
  * bound is exercised (-1: off). */

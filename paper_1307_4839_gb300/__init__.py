@@ -67,7 +67,8 @@ class SwofScenario(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("dx", ctypes.c_double), ("dy", ctypes.c_double),
                 ("z", _D), ("h", _D), ("hu", _D), ("hv", _D), ("manning_n", ctypes.c_double),
                 ("rain_rate", ctypes.c_double), ("rain_t_on", ctypes.c_double),
-                ("rain_t_off", ctypes.c_double), ("bc", ctypes.c_int * 4)]
+                ("rain_t_off", ctypes.c_double), ("bc", ctypes.c_int * 4),
+                ("bc_h", ctypes.c_double * 4), ("bc_q", ctypes.c_double * 4)]
 
 
 class SwofError(RuntimeError):
@@ -115,7 +116,10 @@ _SIGS = {
     "swof_ensemble_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "swof_ensemble_shapes": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     "swof_ensemble_set_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
-    "swof_ensemble_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_int)]),
+    "swof_ensemble_set_member_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "swof_ensemble_get_member_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "swof_ensemble_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_int)]),
     "swof_ensemble_set_wait_limit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int]),
     "swof_gemm_bf16_nt": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -467,6 +471,16 @@ class Solver:
         return dict(rec, cached=False)
 
 
+def ensemble_shapes() -> list[tuple[int, int]]:
+    """Member tile shapes (CTA width, rows) of the ensemble launch."""
+    L = load()
+    n = L.swof_ensemble_shapes(None, None, 0)
+    a = (ctypes.c_int * n)()
+    b = (ctypes.c_int * n)()
+    L.swof_ensemble_shapes(a, b, n)
+    return [(a[k], b[k]) for k in range(n)]
+
+
 def flow_directions(z, out=None, nodata: float | None = None, stream=None):
     """D8 flow-direction codes (uint8 torch tensor [ny][nx], 0 = no lower
     neighbour, 1..8 = E, NE, N, NW, W, SW, S, SE) of a float32 CUDA DEM
@@ -536,8 +550,12 @@ class Ensemble:
             sc.z, sc.h, sc.hu, sc.hv = (_ptr(a) for a in arrs)
             sc.manning_n = w.manning_n if w.friction else 0.0
             sc.rain_rate, sc.rain_t_on, sc.rain_t_off = w.rain_rate, w.rain_t_on, w.rain_t_off
+            bh = getattr(w, "bc_h", None) or (0.0,) * 4     # imposed edge values (optional attributes)
+            bq = getattr(w, "bc_q", None) or (0.0,) * 4
             for b in range(4):
                 sc.bc[b] = int(w.bc[b])
+                sc.bc_h[b] = float(bh[b])
+                sc.bc_q[b] = float(bq[b])
         p = default_params(precision=int(precision), cfl=cfl, h_dry=h_dry, dt_max=dt_max, t_end=t_end)
         p.stream = stream
         e = ctypes.c_void_p()
@@ -580,16 +598,59 @@ class Ensemble:
     def set_shape(self, shape: int):
         _check(load().swof_ensemble_set_shape(self._e, int(shape)), "swof_ensemble_set_shape")
 
-    def autotune(self, steps: int = 2) -> dict:
+    def member_shapes(self) -> list[int]:
         L = load()
-        n = L.swof_ensemble_shapes(None, None, 0)
-        ms = (ctypes.c_double * n)()
+        return [int(L.swof_ensemble_get_member_shape(self._e, k)) for k in range(len(self.sizes))]
+
+    def set_member_shapes(self, shapes):
+        """Member shapes (indices into ensemble_shapes(), one launch width)."""
+        shapes = [int(x) for x in shapes]
+        self.set_shape(shapes[0])
+        for k, sh in enumerate(shapes):
+            if sh != shapes[0]:
+                _check(load().swof_ensemble_set_member_shape(self._e, k, sh), "swof_ensemble_set_member_shape")
+
+    def autotune(self, steps: int = 2, cache: str | None = None) -> dict:
+        """Launch width and per-size-class tile heights (swof_ensemble_autotune).
+        With `cache`, a JSON file maps "<gpu>|<precision>|<member sizes>" to
+        the member shapes, so later runs skip the timing."""
+        import json
+        import hashlib
+        key = None
+        if cache:
+            sizes = ",".join(f"{nx}x{ny}" for nx, ny in self.sizes)
+            key = (f"{_gpu_name()}|{'fp64' if self.precision == FP64 else 'fp32'}|"
+                   f"{hashlib.sha1(sizes.encode()).hexdigest()[:16]}|{len(ensemble_shapes())} shapes")
+            data = {}
+            if os.path.exists(cache):
+                try:
+                    data = json.load(open(cache))
+                except (OSError, ValueError):
+                    data = {}
+            if key in data:
+                self.set_member_shapes(data[key]["member_shapes"])
+                return dict(data[key], cached=True)
+        L = load()
+        ms = (ctypes.c_double * 2)()
         best = ctypes.c_int()
-        _check(L.swof_ensemble_autotune(self._e, int(steps), ms, ctypes.byref(best)), "swof_ensemble_autotune")
-        a = (ctypes.c_int * n)()
-        b = (ctypes.c_int * n)()
-        L.swof_ensemble_shapes(a, b, n)
-        return {"shape": best.value, "ntx": a[best.value], "rows": b[best.value], "ms": [ms[k] for k in range(n)]}
+        mem = (ctypes.c_int * len(self.sizes))()
+        _check(L.swof_ensemble_autotune(self._e, int(steps), ms, ctypes.byref(best), mem), "swof_ensemble_autotune")
+        shp = ensemble_shapes()
+        rec = {"shape": best.value, "ntx": shp[best.value][0], "rows": shp[best.value][1],
+               "member_shapes": [int(mem[k]) for k in range(len(self.sizes))],
+               "ms_per_step_width": {"128": ms[0], "64": ms[1]}}
+        by_size = {}
+        for (nx, ny), sh in zip(self.sizes, rec["member_shapes"]):
+            by_size[f"{nx}x{ny}"] = list(shp[sh])
+        rec["by_size"] = by_size
+        if cache:
+            data[key] = rec
+            tmp = cache + ".tmp"
+            os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
+            with open(tmp, "w") as f:
+                json.dump(data, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return dict(rec, cached=False)
 
     def set_wait_limit(self, polls: int, block_member: int = -1):
         _check(load().swof_ensemble_set_wait_limit(self._e, int(polls), int(block_member)),

@@ -12,10 +12,10 @@
 #include "swof_ensemble.cuh"
 
 namespace swof {
-int launch_ensemble_fp32(const void *desc, int shape, int grid, void *stream);
-int launch_ensemble_fp64(const void *desc, int shape, int grid, void *stream);
-int ensemble_max_grid_fp32(int shape, int *grid);
-int ensemble_max_grid_fp64(int shape, int *grid);
+int launch_ensemble_fp32(const void *desc, int ntx, int grid, void *stream);
+int launch_ensemble_fp64(const void *desc, int ntx, int grid, void *stream);
+int ensemble_max_grid_fp32(int ntx, int *grid);
+int ensemble_max_grid_fp64(int ntx, int *grid);
 }  // namespace swof
 
 struct swof_ens {
@@ -24,7 +24,8 @@ struct swof_ens {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     std::vector<swof_ctx *> members;
-    int shape = 0;                       // index into swof::ENS_SHAPES
+    std::vector<int> mshape;             // per member: index into swof::ENS_SHAPES
+    int ntx = 128;                       // the launch's CTA width (every member's shape has it)
     void *d_inst = nullptr;              // EnsInst<T>[n]
     long long *d_pre = nullptr;          // [3][n+1]
     unsigned int *d_done = nullptr;      // [n]
@@ -47,27 +48,26 @@ namespace {
 
 int cerr(cudaError_t e) { return e == cudaSuccess ? SWOF_OK : SWOF_ECUDA; }
 
-int member_shape_index(int ens_shape)
-{
-    // the ensemble shapes are (128, 32) and (256, 32): single-grid shapes 0 and 2
-    return ens_shape == 1 ? 2 : 0;
-}
-
 template <typename T>
 int build_desc(swof_ens *e, const Fields<T> &(*get)(swof_ctx *))
 {
-    const swof::TileShape sh = swof::ENS_SHAPES[e->shape];
-    const int W = sh.ntx - 4, H = sh.h;
-    const long long chunk = (long long)sh.ntx * swof::RING_CHUNK_PER_THREAD;
+    const long long chunk = (long long)e->ntx * swof::RING_CHUNK_PER_THREAD;
     std::vector<swof::EnsInst<T>> inst((size_t)e->n);
     e->pre.assign(3 * (size_t)(e->n + 1), 0);
     for (int k = 0; k < e->n; ++k) {
         swof_ctx *c = e->members[k];
-        int st = swof_set_tile_shapes(c, member_shape_index(e->shape), member_shape_index(e->shape));
+        const int ms = e->mshape[(size_t)k];
+        const swof::TileShape sh = swof::ENS_SHAPES[ms];
+        if (sh.ntx != e->ntx) return SWOF_EINVAL;
+        const int W = sh.ntx - 4, H = sh.h;
+        // the member's own tile shape: the same tiling, so its tile-edge
+        // ring lists are the ones the launch's ring phase walks
+        int st = swof_set_tile_shapes(c, swof::ENS_MEMBER_SHAPE[ms], swof::ENS_MEMBER_SHAPE[ms]);
         if (st) return st;
         swof::EnsInst<T> &I = inst[k];
         I.P = c->P;
         I.F = get(c);
+        I.H = H;
         I.gdx = (c->P.nx + W - 1) / W;
         I.gdy = (c->P.ny + H - 1) / H;
         I.ring_cells = (long long)I.F.n_ring_cols * c->P.ny + (long long)I.F.n_ring_rows * c->P.nx;
@@ -104,8 +104,8 @@ int rebuild(swof_ens *e)
 int max_grid(swof_ens *e)
 {
     int g = 0;
-    int r = e->prec == SWOF_FP64 ? swof::ensemble_max_grid_fp64(e->shape, &g)
-                                 : swof::ensemble_max_grid_fp32(e->shape, &g);
+    int r = e->prec == SWOF_FP64 ? swof::ensemble_max_grid_fp64(e->ntx, &g)
+                                 : swof::ensemble_max_grid_fp32(e->ntx, &g);
     if (r) return SWOF_ECUDA;
     e->grid = g;
     return SWOF_OK;
@@ -124,12 +124,12 @@ int enqueue(swof_ens *e, int n)
         swof::EnsDesc<double> D{static_cast<const swof::EnsInst<double> *>(e->d_inst), e->n, e->d_pre,
                                 {e->phase_items[0], e->phase_items[1], e->phase_items[2]}, e->per_step, n,
                                 e->d_done, e->d_q, e->spin_limit, e->block_member};
-        return swof::launch_ensemble_fp64(&D, e->shape, grid, e->stream) ? SWOF_ECUDA : SWOF_OK;
+        return swof::launch_ensemble_fp64(&D, e->ntx, grid, e->stream) ? SWOF_ECUDA : SWOF_OK;
     }
     swof::EnsDesc<float> D{static_cast<const swof::EnsInst<float> *>(e->d_inst), e->n, e->d_pre,
                            {e->phase_items[0], e->phase_items[1], e->phase_items[2]}, e->per_step, n,
                            e->d_done, e->d_q, e->spin_limit, e->block_member};
-    return swof::launch_ensemble_fp32(&D, e->shape, grid, e->stream) ? SWOF_ECUDA : SWOF_OK;
+    return swof::launch_ensemble_fp32(&D, e->ntx, grid, e->stream) ? SWOF_ECUDA : SWOF_OK;
 }
 
 // Seed each member whose wave-speed words are not valid with the full
@@ -198,15 +198,13 @@ int swof_ensemble_create(int count, const swof_scenario *specs, const swof_param
     *out = nullptr;
     if (count < 1 || !specs || !common) return SWOF_EINVAL;
     if (common->precision != SWOF_FP64 && common->precision != SWOF_FP32) return SWOF_EINVAL;
-    // the persistent kernel runs the second-order Heun step between walls /
-    // free outflow edges (its wave-speed phases know no imposed edge)
+    // the persistent kernel runs the second-order Heun step
     if (common->order == SWOF_ORDER_1) return SWOF_EINVAL;
-    for (int k = 0; k < count; ++k)
-        for (int b = 0; b < 4; ++b)
-            if (specs[k].bc[b] != SWOF_BC_WALL && specs[k].bc[b] != SWOF_BC_OUTFLOW) return SWOF_EINVAL;
     swof_ens *e = new (std::nothrow) swof_ens();
     if (!e) return SWOF_ENOMEM;
     e->n = count;
+    e->mshape.assign((size_t)count, 0);
+    e->ntx = swof::ENS_SHAPES[0].ntx;
     e->prec = common->precision;
     int st = SWOF_OK;
     if (common->stream) {
@@ -227,7 +225,11 @@ int swof_ensemble_create(int count, const swof_scenario *specs, const swof_param
         p.rain_rate = sc.rain_rate;
         p.rain_t_on = sc.rain_t_on;
         p.rain_t_off = sc.rain_t_off;
-        for (int b = 0; b < 4; ++b) p.bc[b] = sc.bc[b];
+        for (int b = 0; b < 4; ++b) {
+            p.bc[b] = sc.bc[b];
+            p.bc_h[b] = sc.bc_h[b];
+            p.bc_q[b] = sc.bc_q[b];
+        }
         p.friction_map = nullptr;
         p.ks_map = nullptr;
         p.stream = e->stream;
@@ -355,54 +357,119 @@ int swof_ensemble_shapes(int *ntx, int *rows, int max)
     return swof::N_ENS_SHAPES;
 }
 
-int swof_ensemble_set_shape(swof_ens *e, int shape)
+}  // extern "C"
+
+namespace {
+
+// Give the members the shapes ms (one launch width) and rebuild the launch.
+int apply_shapes(swof_ens *e, const std::vector<int> &ms)
 {
-    if (!e || shape < 0 || shape >= swof::N_ENS_SHAPES) return SWOF_EINVAL;
-    if (shape == e->shape) return SWOF_OK;
-    e->shape = shape;
+    const int ntx = swof::ENS_SHAPES[ms[0]].ntx;
+    for (int s : ms)
+        if (s < 0 || s >= swof::N_ENS_SHAPES || swof::ENS_SHAPES[s].ntx != ntx) return SWOF_EINVAL;
+    if (ms == e->mshape && ntx == e->ntx) return SWOF_OK;
+    e->mshape = ms;
+    e->ntx = ntx;
     int st = rebuild(e);       // member tile shapes change: their ring words restart
     return st ? st : max_grid(e);
 }
 
-int swof_ensemble_autotune(swof_ens *e, int steps, double *ms, int *best)
+}  // namespace
+
+extern "C" {
+
+int swof_ensemble_set_shape(swof_ens *e, int shape)
+{
+    if (!e || shape < 0 || shape >= swof::N_ENS_SHAPES) return SWOF_EINVAL;
+    return apply_shapes(e, std::vector<int>((size_t)e->n, shape));
+}
+
+int swof_ensemble_set_member_shape(swof_ens *e, int k, int shape)
+{
+    if (!e || k < 0 || k >= e->n || shape < 0 || shape >= swof::N_ENS_SHAPES) return SWOF_EINVAL;
+    if (swof::ENS_SHAPES[shape].ntx != e->ntx) return SWOF_EINVAL;
+    std::vector<int> ms = e->mshape;
+    ms[(size_t)k] = shape;
+    return apply_shapes(e, ms);
+}
+
+int swof_ensemble_get_member_shape(const swof_ens *e, int k)
+{
+    if (!e || k < 0 || k >= e->n) return SWOF_EINVAL;
+    return e->mshape[(size_t)k];
+}
+
+int swof_ensemble_autotune(swof_ens *e, int steps, double *ms, int *best, int *member_shapes)
 {
     if (!e || steps < 1 || !best) return SWOF_EINVAL;
     std::vector<Snap> snaps(e->members.size());
-    std::vector<bool> lam(e->members.size());
     int st = SWOF_OK;
-    for (size_t k = 0; k < e->members.size() && !st; ++k) {
-        st = snap(e->members[k], snaps[k], false);
-        lam[k] = e->members[k]->lam_valid;
-    }
+    for (size_t k = 0; k < e->members.size() && !st; ++k) st = snap(e->members[k], snaps[k], false);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (!st && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) st = SWOF_ECUDA;
-    double bms = INFINITY;
-    int bk = e->shape;
     long long hs = e->members.empty() ? 0 : e->members[0]->host_steps;
-    for (int s = 0; s < swof::N_ENS_SHAPES && !st; ++s) {
-        st = swof_ensemble_set_shape(e, s);
-        if (!st) st = seed_lambda(e);
-        if (!st) st = cerr(cudaEventRecord(e0, e->stream));
-        if (!st) st = enqueue(e, steps);
-        if (!st) st = cerr(cudaEventRecord(e1, e->stream));
+    // ms per step of `steps` steps with the member shapes ms_try; every
+    // member is put back as it was afterwards
+    auto timed = [&](const std::vector<int> &ms_try, double *out) -> int {
+        int r = apply_shapes(e, ms_try);
+        if (!r) r = seed_lambda(e);
+        if (!r) r = cerr(cudaEventRecord(e0, e->stream));
+        if (!r) r = enqueue(e, steps);
+        if (!r) r = cerr(cudaEventRecord(e1, e->stream));
         float t = 0.0f;
-        if (!st) st = cerr(cudaEventSynchronize(e1));
-        if (!st) st = cerr(cudaEventElapsedTime(&t, e0, e1));
+        if (!r) r = cerr(cudaEventSynchronize(e1));
+        if (!r) r = cerr(cudaEventElapsedTime(&t, e0, e1));
         swof::EnsQueue q;
-        if (!st) st = cerr(cudaMemcpy(&q, e->d_q, sizeof q, cudaMemcpyDeviceToHost));
-        if (!st && q.abort) st = SWOF_ETIMEOUT;
-        if (st) break;
-        if (ms) ms[s] = (double)t / steps;
-        if (t < bms) {
-            bms = t;
-            bk = s;
-        }
-        // put every member back as it was
-        for (size_t k = 0; k < e->members.size() && !st; ++k) {
-            st = snap(e->members[k], snaps[k], true);
+        if (!r) r = cerr(cudaMemcpy(&q, e->d_q, sizeof q, cudaMemcpyDeviceToHost));
+        if (!r && q.abort) r = SWOF_ETIMEOUT;
+        for (size_t k = 0; k < e->members.size() && !r; ++k) {
+            r = snap(e->members[k], snaps[k], true);
             e->members[k]->host_steps = hs;
         }
-        if (!st) st = cerr(cudaStreamSynchronize(e->stream));
+        if (!r) r = cerr(cudaStreamSynchronize(e->stream));
+        *out = (double)t / steps;
+        return r;
+    };
+    // member size classes (grid sides), in order of first appearance
+    std::vector<std::pair<int, int>> cls;
+    std::vector<int> of((size_t)e->n);
+    for (int k = 0; k < e->n; ++k) {
+        std::pair<int, int> sz(e->members[(size_t)k]->P.nx, e->members[(size_t)k]->P.ny);
+        size_t c = 0;
+        while (c < cls.size() && cls[c] != sz) ++c;
+        if (c == cls.size()) cls.push_back(sz);
+        of[(size_t)k] = (int)c;
+    }
+    // for each launch width: all members on its first shape, then per size
+    // class each other height of that width, kept when the launch is faster
+    const int widths[2] = {128, 64};
+    double overall = INFINITY;
+    std::vector<int> chosen = e->mshape;
+    for (int wi = 0; wi < 2 && !st; ++wi) {
+        std::vector<int> cand;
+        for (int s = 0; s < swof::N_ENS_SHAPES; ++s)
+            if (swof::ENS_SHAPES[s].ntx == widths[wi]) cand.push_back(s);
+        std::vector<int> cur((size_t)e->n, cand[0]);
+        double tcur = 0.0;
+        st = timed(cur, &tcur);
+        for (size_t c = 0; c < cls.size() && !st; ++c)
+            for (size_t a = 1; a < cand.size() && !st; ++a) {
+                std::vector<int> trial = cur;
+                for (int k = 0; k < e->n; ++k)
+                    if (of[(size_t)k] == (int)c) trial[(size_t)k] = cand[a];
+                double t = 0.0;
+                st = timed(trial, &t);
+                if (!st && t < tcur) {
+                    tcur = t;
+                    cur = trial;
+                }
+            }
+        if (st) break;
+        if (ms) ms[wi] = tcur;
+        if (tcur < overall) {
+            overall = tcur;
+            chosen = cur;
+        }
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -410,12 +477,14 @@ int swof_ensemble_autotune(swof_ens *e, int steps, double *ms, int *best)
     for (auto &s : snaps)
         for (void *p : s.bufs) cudaFree(p);
     if (st) return st;
-    st = swof_ensemble_set_shape(e, bk);
+    st = apply_shapes(e, chosen);
     // the restored control blocks hold the pre-tuning wave-speed words,
-    // which are valid for the pre-tuning shape only
+    // which are valid for the pre-tuning tiling only
     for (swof_ctx *c : e->members)
         if (!st) st = swof_ctx_invalidate_lambda(c);
-    *best = bk;
+    *best = e->mshape[0];
+    if (member_shapes)
+        for (int k = 0; k < e->n; ++k) member_shapes[k] = e->mshape[(size_t)k];
     return st;
 }
 

@@ -4,11 +4,11 @@
 
 namespace swof {
 
-int launch_ensemble_fp32(const void *desc, int shape, int grid, void *stream)
+int launch_ensemble_fp32(const void *desc, int ntx, int grid, void *stream)
 {
-    return launch_ensemble_t<float>(*static_cast<const EnsDesc<float> *>(desc), shape, grid, (cudaStream_t)stream);
+    return launch_ensemble_t<float>(*static_cast<const EnsDesc<float> *>(desc), ntx, grid, (cudaStream_t)stream);
 }
 
-int ensemble_max_grid_fp32(int shape, int *grid) { return ensemble_max_grid_t<float>(shape, grid); }
+int ensemble_max_grid_fp32(int ntx, int *grid) { return ensemble_max_grid_t<float>(ntx, grid); }
 
 }  // namespace swof

@@ -4,11 +4,11 @@
 
 namespace swof {
 
-int launch_ensemble_fp64(const void *desc, int shape, int grid, void *stream)
+int launch_ensemble_fp64(const void *desc, int ntx, int grid, void *stream)
 {
-    return launch_ensemble_t<double>(*static_cast<const EnsDesc<double> *>(desc), shape, grid, (cudaStream_t)stream);
+    return launch_ensemble_t<double>(*static_cast<const EnsDesc<double> *>(desc), ntx, grid, (cudaStream_t)stream);
 }
 
-int ensemble_max_grid_fp64(int shape, int *grid) { return ensemble_max_grid_t<double>(shape, grid); }
+int ensemble_max_grid_fp64(int ntx, int *grid) { return ensemble_max_grid_t<double>(ntx, grid); }
 
 }  // namespace swof

@@ -29,6 +29,7 @@ template <typename T>
 struct EnsInst {
     Params P;
     Fields<T> F;
+    int H;                     // rows per sweep tile of this instance (the launch fixes the width)
     int gdx, gdy;              // sweep tiling of this instance
     int ring_chunks;           // phase-0 items
     long long ring_cells;      // ring work (x-ring cells then y-ring cells)
@@ -76,12 +77,17 @@ __device__ __forceinline__ void ring_chunk(const EnsInst<T> &I, long long c0, lo
             V4<T> w = cell_rec(P, F, gi - 1, gj, C.hdry), m = cell_rec(P, F, gi, gj, C.hdry),
                   e = cell_rec(P, F, gi + 1, gj, C.hdry);
             kx = kmax(kx, speed_key(cell_speed(w.x, m.x, e.x, w.y, m.y, e.y, m.w, C.hdry, C.g)));
+            // an imposed edge's boundary state (the ghost beside the edge cell)
+            if (gi == 0 && P.bc[0] >= SWOF_BC_IMPOSED_H) kx = kmax(kx, speed_key(ab(w.y) + sq(C.g * w.x)));
+            if (gi == P.nx - 1 && P.bc[1] >= SWOF_BC_IMPOSED_H) kx = kmax(kx, speed_key(ab(e.y) + sq(C.g * e.x)));
         } else {
             long long q = k - nxr;
             int gj = F.ring_rows[q / P.nx], gi = (int)(q % P.nx);
             V4<T> s_ = cell_rec(P, F, gi, gj - 1, C.hdry), m = cell_rec(P, F, gi, gj, C.hdry),
                   n = cell_rec(P, F, gi, gj + 1, C.hdry);
             ky = kmax(ky, speed_key(cell_speed(s_.x, m.x, n.x, s_.z, m.z, n.z, m.w, C.hdry, C.g)));
+            if (gj == 0 && P.bc[2] >= SWOF_BC_IMPOSED_H) ky = kmax(ky, speed_key(ab(s_.z) + sq(C.g * s_.x)));
+            if (gj == P.ny - 1 && P.bc[3] >= SWOF_BC_IMPOSED_H) ky = kmax(ky, speed_key(ab(n.z) + sq(C.g * n.x)));
         }
     }
     kx = block_max(kx, red);
@@ -105,16 +111,35 @@ __device__ __forceinline__ int find_inst(const long long *pre, int n, long long 
     return lo;
 }
 
-// Three resident CTAs of 128 threads per SM for FP32 (registers capped at
-// 170): the stage code's live ranges otherwise take the kernel to ~215
-// registers and two CTAs, measured 1.35x slower on the 256-member batch.
+// Three resident CTAs of 128 threads (six of 64) per SM for FP32, registers
+// capped at 170: the stage code's live ranges otherwise take the kernel to
+// ~215 registers and two CTAs, measured 1.35x slower on the 256-member batch.
 template <typename T>
 constexpr int ens_min_blocks(int ntx)
 {
-    return std::is_same<T, float>::value && ntx == 128 ? 3 : 1;
+    return std::is_same<T, float>::value ? (ntx == 128 ? 3 : (ntx == 64 ? 6 : 1)) : 1;
 }
 
-template <typename T, int NTX, int H>
+// The launch's CTAs are NTX wide; each member's tiles are NTX - 4 columns
+// by its own H rows, from the heights the single-grid tile shapes have for
+// that width (members of one launch may differ in H).
+template <typename T, int STAGE, int NTX>
+__device__ __forceinline__ void ens_sweep(const EnsInst<T> &I, int bx, int by, SweepSmem<T, NTX> &S)
+{
+    if constexpr (NTX == 64) {
+        if (I.H == 16)
+            sweep_tile<T, STAGE, NTX, 16, false>(I.P, I.F, bx, by, I.gdx, I.gdy, S);
+        else
+            sweep_tile<T, STAGE, NTX, 64, false>(I.P, I.F, bx, by, I.gdx, I.gdy, S);
+    } else {
+        if (I.H == 64)
+            sweep_tile<T, STAGE, NTX, 64, false>(I.P, I.F, bx, by, I.gdx, I.gdy, S);
+        else
+            sweep_tile<T, STAGE, NTX, 32, false>(I.P, I.F, bx, by, I.gdx, I.gdy, S);
+    }
+}
+
+template <typename T, int NTX>
 __global__ void __launch_bounds__(NTX, ens_min_blocks<T>(NTX)) k_ensemble(EnsDesc<T> D)
 {
     __shared__ SweepSmem<T, NTX> S;
@@ -173,9 +198,9 @@ __global__ void __launch_bounds__(NTX, ens_min_blocks<T>(NTX)) k_ensemble(EnsDes
         } else {
             int bx = (int)(local % I.gdx), by = (int)(local / I.gdx);
             if (s_phase == 1)
-                sweep_tile<T, 1, NTX, H, false>(I.P, I.F, bx, by, I.gdx, I.gdy, S);
+                ens_sweep<T, 1, NTX>(I, bx, by, S);
             else
-                sweep_tile<T, 2, NTX, H, false>(I.P, I.F, bx, by, I.gdx, I.gdy, S);
+                ens_sweep<T, 2, NTX>(I, bx, by, S);
         }
         __threadfence();
         __syncthreads();
@@ -183,27 +208,30 @@ __global__ void __launch_bounds__(NTX, ens_min_blocks<T>(NTX)) k_ensemble(EnsDes
     }
 }
 
-// Shapes the ensemble kernel is built for: (threads, rows).
-constexpr int N_ENS_SHAPES = 2;
-constexpr TileShape ENS_SHAPES[N_ENS_SHAPES] = {{128, 32}, {256, 32}};
+// Member tile shapes the ensemble kernel is built for, (threads, rows): the
+// register-prefetch forms of single-grid shapes (ENS_MEMBER_SHAPE[k] is the
+// index in TILE_SHAPES, which keeps a member's own tile-edge ring lists
+// consistent with its ensemble tiling).  A launch takes one width.
+constexpr int N_ENS_SHAPES = 4;
+constexpr TileShape ENS_SHAPES[N_ENS_SHAPES] = {{128, 32}, {128, 64}, {64, 64}, {64, 16}};
+constexpr int ENS_MEMBER_SHAPE[N_ENS_SHAPES] = {5, 6, 8, 9};
 
 template <typename T>
-int launch_ensemble_t(const EnsDesc<T> &D, int shape, int grid, cudaStream_t s)
+int launch_ensemble_t(const EnsDesc<T> &D, int ntx, int grid, cudaStream_t s)
 {
-    if (shape == 1)
-        k_ensemble<T, 256, 32><<<grid, 256, 0, s>>>(D);
+    if (ntx == 64)
+        k_ensemble<T, 64><<<grid, 64, 0, s>>>(D);
     else
-        k_ensemble<T, 128, 32><<<grid, 128, 0, s>>>(D);
+        k_ensemble<T, 128><<<grid, 128, 0, s>>>(D);
     return (int)cudaGetLastError();
 }
 
 template <typename T>
-int ensemble_max_grid_t(int shape, int *grid)
+int ensemble_max_grid_t(int ntx, int *grid)
 {
     int per_sm = 0;
-    cudaError_t e = (shape == 1)
-                        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ensemble<T, 256, 32>, 256, 0)
-                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ensemble<T, 128, 32>, 128, 0);
+    cudaError_t e = (ntx == 64) ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ensemble<T, 64>, 64, 0)
+                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ensemble<T, 128>, 128, 0);
     if (e != cudaSuccess) return (int)e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
