@@ -113,25 +113,40 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def recorded_metric(kernel: str, precision: str, tile, name: str):
-    """A figure from the committed ncu summary of this kernel (current source
-    and tile shape only), else None."""
-    if tile is None:
+def _profile_summary(kernel: str, precision: str, tile):
+    """The committed ncu summary of this stage kernel (`kernel` = stage1 or
+    stage2) at this tile shape [ntx, rows, form], as a dict, if it was taken
+    on the current kernel source; else None."""
+    if not tile or len(tile) < 3:
         return None
+    ntx, h, form = tile[0], tile[1], tile[2]
     csrc = os.path.join(ROOT, "paper_1307_4839_gb300", "csrc")
     src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("swof_kernels.cuh", "swof_sweep.cuh"))
     sha = hashlib.sha256(src).hexdigest()[:16]
-    f = os.path.join(ROOT, "profiles", f"k_sweep_{kernel}_{precision}_valley4096_{tile[0]}x{tile[1]}.txt")
+    f = os.path.join(ROOT, "profiles", f"k_sweep_{kernel}_{precision}_valley4096_{ntx}x{h}_{form}.txt")
     if not os.path.exists(f):
         return None
-    vals = dict(line.split(":", 1) for line in open(f) if ":" in line)
-    vals = {k.strip(): v.strip() for k, v in vals.items()}
-    if vals.get("kernel_source_sha256_16") != sha or not re.search(rf", {tile[0]}, {tile[1]}[,>]",
-                                                                    vals.get("kernel", "")):
+    vals = {}
+    for line in open(f):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals.setdefault(k.strip(), v.strip())
+    name = vals.get("kernel", "")
+    stage = kernel[-1]
+    want = ("k_sweep_reg<" if form == "reg" else "k_sweep<") + \
+        ("float" if precision == "fp32" else "double") + f", {stage}, {ntx}, {h}, 0>"
+    if vals.get("kernel_source_sha256_16") != sha or want not in name:
         return None
+    return vals
+
+
+def recorded_metric(kernel: str, precision: str, tile, name: str):
+    """A figure from the committed ncu summary of this kernel (current source,
+    tile shape and form only), else None."""
+    vals = _profile_summary(kernel, precision, tile)
     try:
-        return float(vals[name])
-    except Exception:
+        return float(vals[name]) if vals else None
+    except (KeyError, ValueError):
         return None
 
 
@@ -175,29 +190,9 @@ def bf16_peak() -> float:
 
 def recorded_traffic(kernel: str, precision: str, tile):
     """DRAM bytes per launch from the committed ncu summary of this kernel,
-    if it was taken on the current kernel source and tile shape (else
+    if it was taken on the current kernel source, tile shape and form (else
     None)."""
-    csrc = os.path.join(ROOT, "paper_1307_4839_gb300", "csrc")
-    src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("swof_kernels.cuh", "swof_sweep.cuh"))
-    sha = hashlib.sha256(src).hexdigest()[:16]
-    if tile is None:
-        return None
-    f = os.path.join(ROOT, "profiles", f"k_sweep_{kernel}_{precision}_valley4096_{tile[0]}x{tile[1]}.txt")
-    if not os.path.exists(f):
-        return None
-    vals = {}
-    for line in open(f):
-        if ":" in line:
-            k, v = line.split(":", 1)
-            vals[k.strip()] = v.strip()
-    if vals.get("kernel_source_sha256_16") != sha:
-        return None
-    if not re.search(rf", {tile[0]}, {tile[1]}[,>]", vals.get("kernel", "")):
-        return None
-    try:
-        return float(vals["dram_bytes_per_launch"])
-    except Exception:
-        return None
+    return recorded_metric(kernel, precision, tile, "dram_bytes_per_launch")
 
 
 def recorded_d8_traffic(n: int):
@@ -390,12 +385,14 @@ def run_reference(args, ws, rank):
 
 def measure(sw, torch, w, precision: str, steps: int, warmup: int, ws: int, clocks: Clocks | None,
             autotune: bool = True, tile: int = -1, tile2: int = -1, over: dict | None = None,
-            skip: bool = False, tune_tag: str = ""):
+            skip: bool = False, tune_tag: str = "", contract: bool = False):
     prec = sw.FP32 if precision == "fp32" else sw.FP64
     # a dedicated (non-null) stream: the kernels and the timing events share it
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     s = sw.Solver.from_workload(w, prec, stream=stream.cuda_stream, **(over or {}))
+    if contract:
+        s.set_fp64_contraction(True)
     s.step(2)                      # a state past t = 0 for the shape choice
     if tile >= 0 or not autotune:
         shape = max(tile, 0)
@@ -451,6 +448,10 @@ def measure(sw, torch, w, precision: str, steps: int, warmup: int, ws: int, cloc
         reps.append(e0.elapsed_time(e1) / per)
     d = s.diagnostics()
     d["tile"] = {k: tune[k] for k in ("stage1", "stage2", "ms_stage1", "ms_stage2") if k in tune}
+    forms = sw.tile_shape_forms()
+    for k, st in ((0, "stage1"), (1, "stage2")):
+        if st in d["tile"]:
+            d["tile"][st] = list(d["tile"][st][:2]) + [forms[tune["shape"][k]]]
     d["reps"] = {"blocks": 10, "steps_each": per, "ms_per_step_best": min(reps),
                  "ms_per_step_median": statistics.median(reps)}
     if skip:
@@ -926,7 +927,8 @@ def summary(value, roofline, variants, accuracy, hbm):
     v = variants
     out = {"valley4096_fp32_G": g({"v": value}, "v"), "valley4096_fp32_stage2_hbm_frac": g(roofline, "frac", nd=3),
            "valley4096_fp32_step_hbm_frac": g(roofline, "step_frac_of_hbm", nd=3),
-           "valley4096_fp64_G": g(v, "fp64", "value"), "valley4096_fp64_step_hbm_frac": g(v, "fp64", "hbm_frac_algorithmic", nd=3),
+           "valley4096_fp64_G": g(v, "fp64", "value"), "valley4096_fp64_contracted_G": g(v, "fp64_contracted", "value"),
+           "valley4096_fp64_step_hbm_frac": g(v, "fp64", "hbm_frac_algorithmic", nd=3),
            "valley4096_fp32_fully_wet_G": g(v, "fp32_fully_wet", "value"),
            "valley4096_fp64_fully_wet_G": g(v, "fp64_fully_wet", "value"),
            "rainfall2048_fp32_G": g(v, "rainfall", "fp32", "value"), "rainfall2048_fp64_G": g(v, "rainfall", "fp64", "value"),
@@ -1021,6 +1023,20 @@ def main():
                                 st: recorded_metric(st, "fp64", d64["tile"].get(st), "FP64 pipe %")
                                 for st in ("stage1", "stage2")}}
         del s64
+        # the same with multiply-add contraction (within 1e-12 of the oracle
+        # under its dt sequence instead of bit for bit)
+        msc, tc, _, dc, sc = measure(sw, torch, w, "fp64", k64, args.warmup, ws, None,
+                                     not args.no_autotune, args.tile, tune_tag="contracted", contract=True)
+        msc = max_over_ranks(msc, ws)
+        vc = ws * cells / (msc / k64 * 1e-3) * 1e-9
+        variants["fp64_contracted"] = {
+            "value": vc, "unit": UNIT, "ms_per_step": msc / k64, "steps": k64,
+            "over_fp64_exact": vc / v64,
+            "kernel_ms": {kk: round(tc[kk + "_ms"], 4) for kk in ("lambda", "stage1", "stage2")},
+            "hbm_frac_algorithmic": STEP_BYTES["fp64"] * cells / (msc / k64 * 1e-3) * 1e-9 / hbm,
+            "tile": dc["tile"],
+            "parity": "relative L-inf <= 1e-12 against the oracle under its dt sequence (not bit for bit)"}
+        del sc
 
     if P == "fp32" and not args.no_wet:
         # the same grid fully wet (0.5 m of water added everywhere): no dry-face shortcuts

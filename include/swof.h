@@ -290,9 +290,25 @@ SWOF_API int swof_get_timing(swof_ctx *ctx, double *ms_lambda, double *ms_stage1
  * small grids gain the most. */
 SWOF_API int swof_use_graph(swof_ctx *ctx, int on);
 
+/* FP64 multiply-add contraction (SWOF_FP64 contexts; SWOF_EINVAL for
+ * SWOF_FP32).  Off (the default), every FP64 kernel follows the oracle's
+ * operation order with no a*b+c contracted, so states and the dt sequence
+ * equal the oracle's bit for bit.  On, the same kernels compiled with
+ * contraction run instead (~15 % faster on GB300's FP64 pipe): each fused
+ * multiply-add rounds once instead of twice, so results differ from the
+ * oracle by roundoff -- within relative L-inf 1e-12 under the oracle's dt
+ * sequence -- and the CFL dt may differ in its last bits.  Takes effect
+ * from the next swof_step; synchronises; a captured step graph is
+ * re-captured.  Not in the paper: a GB300 build choice.  The ensemble
+ * kernel always runs without contraction. */
+SWOF_API int swof_set_fp64_contraction(swof_ctx *ctx, int on);
+
 /* Stage-kernel tile shapes.  The stage kernels walk columns down the grid;
  * a shape is (threads per CTA along x, rows per CTA).  swof_tile_shapes
- * writes up to max shapes (ntx[k], rows[k]) and returns how many exist.
+ * writes up to max shapes (ntx[k], rows[k]) and returns how many exist:
+ * the first half stage their input rows through a TMA ring (with a fast
+ * path for rows dry across the CTA), the second half are the same
+ * (ntx, rows) with a one-row register prefetch instead.
  * swof_set_tile_shape(s) select the shape of both stages, or of stage 1 and
  * stage 2 separately (results do not depend on it).  swof_autotune times
  * each stage kernel with every shape `reps` times on the context's current

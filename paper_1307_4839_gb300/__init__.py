@@ -101,6 +101,7 @@ _SIGS = {
     "swof_enable_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "swof_get_timing": (ctypes.c_int, [ctypes.c_void_p, _D, _D, _D, ctypes.POINTER(ctypes.c_int)]),
     "swof_use_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "swof_set_fp64_contraction": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "swof_volume_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
                                            ctypes.c_void_p]),
@@ -235,6 +236,7 @@ class Solver:
         L = load()
         coef = manning_n if friction_coef is None else friction_coef
         self.nx, self.ny, self.precision = int(nx), int(ny), int(precision)
+        self.fp64_contraction = False
         self._ctx = None
         keep = []
         fm = km = None
@@ -428,6 +430,12 @@ class Solver:
     def use_graph(self, on=True):
         _check(load().swof_use_graph(self._ctx, int(bool(on))), "swof_use_graph")
 
+    def set_fp64_contraction(self, on=True):
+        """FP64 kernels with multiply-add contraction (within 1e-12 of the
+        oracle under its dt sequence) instead of the bit-exact ones."""
+        _check(load().swof_set_fp64_contraction(self._ctx, int(bool(on))), "swof_set_fp64_contraction")
+        self.fp64_contraction = bool(on)
+
     def set_tile_shape(self, shape: int, shape2: int | None = None):
         """Tile shape of both stage kernels, or of stage 1 and stage 2."""
         if shape2 is None:
@@ -443,7 +451,8 @@ class Solver:
         shape table is not used)."""
         import json
         if key is None:
-            key = f"{_gpu_name()}|{self.nx}x{self.ny}|{'fp64' if self.precision == FP64 else 'fp32'}"
+            prec = "fp32" if self.precision == FP32 else ("fp64c" if self.fp64_contraction else "fp64")
+            key = f"{_gpu_name()}|{self.nx}x{self.ny}|{prec}"
         key = f"{key}|{len(tile_shapes())} shapes"
         data = {}
         if cache and os.path.exists(cache):
@@ -508,6 +517,14 @@ def tile_shapes() -> list[tuple[int, int]]:
     b = (ctypes.c_int * n)()
     L.swof_tile_shapes(a, b, n)
     return [(a[k], b[k]) for k in range(n)]
+
+
+def tile_shape_forms() -> list[str]:
+    """How each stage-kernel shape brings in its input rows: "ring" (TMA
+    ring with the dry fast path) for the first half of the shapes, "reg"
+    (one-row register prefetch) for the second half."""
+    n = len(tile_shapes())
+    return ["ring"] * (n // 2) + ["reg"] * (n - n // 2)
 
 
 def _gpu_name() -> str:

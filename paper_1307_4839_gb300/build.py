@@ -1,7 +1,8 @@
 """Build libswof.so in-tree with nvcc for sm_103a.
 
 Each .cu file under csrc/ is compiled separately (in parallel); the FP64
-unit gets -fmad=false so no multiply-add is contracted.  The result lands in
+units get -fmad=false so no multiply-add is contracted, and the same FP64
+sources are compiled once more with contraction (swof_fp64c*.cu).  The result lands in
 paper_1307_4839_gb300/_build/libswof.so (git-ignored).  build(debug=True)
 builds the index-checking variant (-DSWOF_BOUNDS_CHECK=1) into
 _build/debug/libswof_debug.so.
@@ -27,6 +28,9 @@ PER_FILE = {
     "swof_fp64.cu": ["-fmad=false", "-prec-div=true", "-prec-sqrt=true"],
     "swof_fp32.cu": [],
     "swof_fp64_reg.cu": ["-fmad=false", "-prec-div=true", "-prec-sqrt=true"],
+    # the same two units with a*b+c contracted into FMAs (swof_set_fp64_contraction)
+    "swof_fp64c.cu": ["-fmad=true", "-prec-div=true", "-prec-sqrt=true"],
+    "swof_fp64c_reg.cu": ["-fmad=true", "-prec-div=true", "-prec-sqrt=true"],
     # the ensemble kernel reads, within one launch, data other CTAs wrote:
     # global loads bypass the (non-coherent) L1
     "swof_ens_fp64.cu": ["-fmad=false", "-prec-div=true", "-prec-sqrt=true", "-Xptxas", "-dlcm=cg"],
@@ -45,11 +49,16 @@ def sources() -> list[str]:
     return sorted(f for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
+# units that include another .cu file
+INCLUDES = {"swof_fp64c.cu": "swof_fp64.cu", "swof_fp64c_reg.cu": "swof_fp64_reg.cu"}
+
+
 def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
     t = os.path.getmtime(obj)
-    deps = [src] + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
+    inc = INCLUDES.get(os.path.basename(src))
+    deps = [src] + ([os.path.join(CSRC, inc)] if inc else []) + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     deps.append(os.path.join(HERE, "..", "include", "swof.h"))
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 

@@ -821,6 +821,19 @@ int swof_get_timing(swof_ctx *c, double *ms_l, double *ms_1, double *ms_2, int *
     return SWOF_OK;
 }
 
+int swof_set_fp64_contraction(swof_ctx *c, int on)
+{
+    if (!c || c->prec != SWOF_FP64) return SWOF_EINVAL;
+    const swof::Launch *L = on ? &swof::launch_fp64c() : &swof::launch_fp64();
+    if (L == c->L) return SWOF_OK;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SWOF_ECUDA;
+    int st = cuda_err((cudaError_t)L->configure());
+    if (st) return st;
+    c->L = L;
+    c->gen++;
+    return SWOF_OK;
+}
+
 int swof_use_graph(swof_ctx *c, int on)
 {
     if (!c) return SWOF_EINVAL;

@@ -3,10 +3,10 @@
 // ring forms, so both give the oracle's values bit for bit.
 #include "swof_reg.cuh"
 
-namespace swof {
+SWOF_KERNELS_BEGIN
 
 template int launch_stage_reg<double, 1, false>(int, const Params &, const Fields<double> &, cudaStream_t);
 template int launch_stage_reg<double, 2, false>(int, const Params &, const Fields<double> &, cudaStream_t);
 template int launch_stage_reg<double, 1, true>(int, const Params &, const Fields<double> &, cudaStream_t);
 
-}  // namespace swof
+SWOF_KERNELS_END

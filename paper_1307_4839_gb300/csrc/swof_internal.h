@@ -23,6 +23,22 @@
 #define SWOF_BOUNDS_CHECK 0
 #endif
 
+// The FP64 stencil is built twice: bit for bit with the oracle (-fmad=false)
+// and with multiply-add contraction (swof_fp64c*.cu, SWOF_FP64_CONTRACT=1).
+// The kernel headers open their namespace with SWOF_KERNELS_BEGIN, which in
+// the contracted build adds an inline namespace, so the two builds' kernels
+// and launchers have distinct symbols in one library.
+#ifndef SWOF_FP64_CONTRACT
+#define SWOF_FP64_CONTRACT 0
+#endif
+#if SWOF_FP64_CONTRACT
+#define SWOF_KERNELS_BEGIN namespace swof { inline namespace fp64c {
+#define SWOF_KERNELS_END } }
+#else
+#define SWOF_KERNELS_BEGIN namespace swof {
+#define SWOF_KERNELS_END }
+#endif
+
 namespace swof {
 
 // Per-context control block in device memory: the CFL reduction words, the
@@ -166,6 +182,7 @@ struct Launch {
 };
 
 const Launch &launch_fp64();
+const Launch &launch_fp64c();   // FP64 with multiply-add contraction
 const Launch &launch_fp32();
 
 }  // namespace swof

@@ -38,7 +38,7 @@
 #include "swof_internal.h"
 #include "tc05.cuh"
 
-namespace swof {
+SWOF_KERNELS_BEGIN
 
 constexpr int BX = 32, BY = 8, NT = BX * BY;              // wave-speed kernel tile
 constexpr int LX = BX + 2, LY = BY + 2, LA = LX * LY;    // wave-speed tile + 1-halo
@@ -849,9 +849,9 @@ __global__ void __launch_bounds__(NT) k_reduce(Params P, Fields<T> F, double *ou
     }
 }
 
-}  // namespace swof
+SWOF_KERNELS_END
 #include "swof_sweep.cuh"
-namespace swof {
+SWOF_KERNELS_BEGIN
 
 // ---------------------------------------------------------------------------
 // End of a first-order step (Sec. 3.3): U^{n+1} = U* of the single Euler
@@ -1273,4 +1273,4 @@ int launch_probe_t(const Params &P, void *f, int i, int j, void *stream)
     return (int)cudaGetLastError();
 }
 
-}  // namespace swof
+SWOF_KERNELS_END

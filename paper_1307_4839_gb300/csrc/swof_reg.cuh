@@ -5,7 +5,7 @@
 #pragma once
 #include "swof_kernels.cuh"
 
-namespace swof {
+SWOF_KERNELS_BEGIN
 
 template <typename T, int STAGE, bool ORD1>
 int launch_stage_reg(int cfg, const Params &P, const Fields<T> &F, cudaStream_t s)
@@ -19,4 +19,4 @@ int launch_stage_reg(int cfg, const Params &P, const Fields<T> &F, cudaStream_t 
     }
 }
 
-}  // namespace swof
+SWOF_KERNELS_END

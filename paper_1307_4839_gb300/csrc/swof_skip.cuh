@@ -12,7 +12,7 @@
 // the same whatever the order, so dt is the flat ring pass's bit for bit.
 #pragma once
 
-namespace swof {
+SWOF_KERNELS_BEGIN
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_lambda_ring_tiles(Params P, Fields<T> F)
@@ -80,4 +80,4 @@ int launch_ring_t(const Params &P, void *f, void *stream)
     return (int)cudaGetLastError();
 }
 
-}  // namespace swof
+SWOF_KERNELS_END

@@ -30,7 +30,7 @@
 // cell triples.  Dry tests run on bit patterns, off GB300's narrow FP64 pipe.
 #pragma once
 
-namespace swof {
+SWOF_KERNELS_BEGIN
 
 template <typename T>
 struct Cell {
@@ -794,4 +794,4 @@ __global__ void __launch_bounds__(NTX) k_sweep(Params P, Fields<T> F, const __gr
     sweep_tile<T, STAGE, NTX, H, true, ORD1, true>(P, F, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y, S, ring, &M);
 }
 
-}  // namespace swof
+SWOF_KERNELS_END
