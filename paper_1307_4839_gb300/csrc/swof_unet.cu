@@ -87,21 +87,35 @@ __global__ void k_colsum_fin(const float *part, int blocks, int N, int nb, float
 }
 
 // 2x2 average pooling: x (channels [xc0, xc0+C) of stride cx) at H x W ->
-// y compact [B][H/2][W/2][C]
+// y compact [B][H/2][W/2][C].  One thread per output pixel and 8-channel
+// group (C, cx and xc0 multiples of 8): four 16-byte loads, one store.
 __global__ void k_pool_fwd(const bf16 *x, int cx, int xc0, int B, int H, int W, int C, bf16 *y)
 {
-    long long total = (long long)B * (H / 2) * (W / 2) * C;
+    const int G = C >> 3;
+    long long total = (long long)B * (H / 2) * (W / 2) * G;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-        int c = (int)(i % C);
-        long long q = i / C;
+        int g = (int)(i % G);
+        long long q = i / G;
         int xo = (int)(q % (W / 2));
         long long r = q / (W / 2);
         int yo = (int)(r % (H / 2));
         int b = (int)(r / (H / 2));
         long long base = ((long long)b * H + 2 * yo) * W + 2 * xo;
-        float s = __bfloat162float(x[base * cx + xc0 + c]) + __bfloat162float(x[(base + 1) * cx + xc0 + c]) +
-                  __bfloat162float(x[(base + W) * cx + xc0 + c]) + __bfloat162float(x[(base + W + 1) * cx + xc0 + c]);
-        y[i] = __float2bfloat16_rn(0.25f * s);
+        const int c0 = xc0 + 8 * g;
+        uint4 a = *reinterpret_cast<const uint4 *>(x + base * cx + c0);
+        uint4 bq = *reinterpret_cast<const uint4 *>(x + (base + 1) * cx + c0);
+        uint4 cq = *reinterpret_cast<const uint4 *>(x + (base + W) * cx + c0);
+        uint4 dq = *reinterpret_cast<const uint4 *>(x + (base + W + 1) * cx + c0);
+        const bf16 *pa = reinterpret_cast<const bf16 *>(&a), *pb = reinterpret_cast<const bf16 *>(&bq);
+        const bf16 *pc = reinterpret_cast<const bf16 *>(&cq), *pd = reinterpret_cast<const bf16 *>(&dq);
+        __align__(16) bf16 t[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            float s = __bfloat162float(pa[k]) + __bfloat162float(pb[k]) + __bfloat162float(pc[k]) +
+                      __bfloat162float(pd[k]);
+            t[k] = __float2bfloat16_rn(0.25f * s);
+        }
+        *reinterpret_cast<uint4 *>(y + q * C + 8 * g) = *reinterpret_cast<const uint4 *>(t);
     }
 }
 
@@ -210,29 +224,55 @@ __global__ void k_replicate_bias(const float *b, int n, int reps, float *out)
 __global__ void k_pack_input(const float *state, int nin, int B, int H, int W, const float *mean, const float *inv,
                              bf16 *x)
 {
-    long long P = (long long)B * H * W;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P * 16; i += (long long)gridDim.x * blockDim.x) {
-        long long p = i >> 4;
-        int c = (int)(i & 15);
-        float v = 0.0f;
-        if (c < nin) {
-            long long b = p / ((long long)H * W), r = p - b * (long long)H * W;
-            v = (state[(b * nin + c) * (long long)H * W + r] - mean[c]) * inv[c];
-        }
-        x[i] = __float2bfloat16_rn(v);
+    // one thread per pixel: the nin channel planes read coalesced across
+    // threads, the pixel's 16 channels written as two 16-byte stores
+    const long long HW = (long long)H * W, P = (long long)B * HW;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+        const long long b = p / HW, r = p - b * HW;
+        __align__(16) bf16 t[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+            t[c] = __float2bfloat16_rn(c < nin ? (state[(b * nin + c) * HW + r] - mean[c]) * inv[c] : 0.0f);
+        uint4 *d = reinterpret_cast<uint4 *>(x + p * 16);
+        d[0] = reinterpret_cast<const uint4 *>(t)[0];
+        d[1] = reinterpret_cast<const uint4 *>(t)[1];
     }
 }
 
-// out[b][c] = in[b][c] + net[p][c] * scale[c]  (c < nout), NCHW fp32
-__global__ void k_residual(const float *in, int nin, const float *net, int nout, int B, int H, int W,
-                           const float *scale, float *out)
+// The prediction's 1x1 output convolution and residual update in one pass:
+// out[b][c] = in[b][c] + scale[c] * (bias[c] + sum_k x[p][k] w[c][k]) for
+// c < nout, NCHW fp32.  x: bf16 [P][C] (C a multiple of 8), w: bf16 rows of
+// Kp.  One thread per pixel; the products of bf16 values are exact in FP32
+// and accumulate in FP32, as on the tensor cores (nout <= 16 outputs are
+// too few columns for an MMA tile).
+__global__ void k_head_residual(const bf16 *x, int C, const bf16 *w, int Kp, const float *bias, const float *in,
+                                int nin, int nout, int B, int H, int W, const float *scale, float *out)
 {
-    long long HW = (long long)H * W, total = (long long)B * nout * HW;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-        long long b = i / (nout * HW), r = i - b * nout * HW;
-        int c = (int)(r / HW);
-        long long q = r - c * HW;
-        out[i] = in[(b * nin + c) * HW + q] + net[(b * HW + q) * 16 + c] * scale[c];
+    extern __shared__ float swt[];            // [nout][C]
+    for (int i = threadIdx.x; i < nout * C; i += blockDim.x) swt[i] = __bfloat162float(w[(i / C) * Kp + i % C]);
+    __syncthreads();
+    const long long HW = (long long)H * W, P = (long long)B * HW;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+        float acc[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) acc[c] = 0.0f;
+        for (int k0 = 0; k0 < C; k0 += 8) {
+            uint4 v = *reinterpret_cast<const uint4 *>(x + p * C + k0);
+            const bf16 *pv = reinterpret_cast<const bf16 *>(&v);
+            float xf[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) xf[j] = __bfloat162float(pv[j]);
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                if (c < nout) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[c] = fmaf(xf[j], swt[c * C + k0 + j], acc[c]);
+                }
+        }
+        const long long b = p / HW, r = p - b * HW;
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+            if (c < nout) out[(b * nout + c) * HW + r] = in[(b * nin + c) * HW + r] + (acc[c] + bias[c]) * scale[c];
     }
 }
 
@@ -809,7 +849,7 @@ int bwd_layer(swof_unet *u, int l, int B, int ih, int iw, Act in, const float *d
 
 // keep_pre = false (inference): the pre-activations are not stored (the
 // activations still use their bf16-rounded values, as in training).
-int forward(swof_unet *u, int B, cudaStream_t s, bool keep_pre = true)
+int forward(swof_unet *u, int B, cudaStream_t s, bool keep_pre = true, bool head = true)
 {
     int st = SWOF_OK;
     auto pre = [&](bf16 *p) { return keep_pre ? p : nullptr; };
@@ -820,7 +860,7 @@ int forward(swof_unet *u, int B, cudaStream_t s, bool keep_pre = true)
         if (l > 0) {
             int hp = u->H >> (l - 1), wp = u->W >> (l - 1), cp = C << (l - 1);
             long long n = (long long)B * h * w * cp;
-            swof::k_pool_fwd<<<swof::grid_for(n), 256, 0, s>>>(u->cat[l - 1], 2 * cp, 0, B, hp, wp, cp, u->pool[l]);
+            swof::k_pool_fwd<<<swof::grid_for(n / 8), 256, 0, s>>>(u->cat[l - 1], 2 * cp, 0, B, hp, wp, cp, u->pool[l]);
             in = Act{u->pool[l], cp, 0};
         }
         st = fwd_layer(u, 2 * l, B, h, w, in, Act{u->ea[l], c, 0}, pre(u->ea_pre[l]), nullptr, 0, s);
@@ -841,7 +881,7 @@ int forward(swof_unet *u, int B, cudaStream_t s, bool keep_pre = true)
                                 pre(u->db_pre[l]), nullptr, 0, s);
         below = Act{u->db[l], c, 0};
     }
-    if (!st) st = fwd_layer(u, 17, B, u->H, u->W, below, Act{nullptr, 16, 0}, nullptr, u->out, 16, s);
+    if (!st && head) st = fwd_layer(u, 17, B, u->H, u->W, below, Act{nullptr, 16, 0}, nullptr, u->out, 16, s);
     return st;
 }
 
@@ -1213,7 +1253,7 @@ int swof_surrogate_train_step(swof_unet *u, const float *in, const float *next, 
     cudaStream_t s = S(stream);
     long long P = (long long)B * u->H * u->W;
     cudaMemsetAsync(u->err, 0, sizeof(int), s);
-    swof::k_pack_input<<<swof::grid_for(P * 16), 256, 0, s>>>(in, u->in_ch, B, u->H, u->W, u->norm, u->norm + 16, u->x0);
+    swof::k_pack_input<<<swof::grid_for(P), 256, 0, s>>>(in, u->in_ch, B, u->H, u->W, u->norm, u->norm + 16, u->x0);
     swof::k_target<<<swof::grid_for(P * u->out_ch), 256, 0, s>>>(in, u->in_ch, next, u->out_ch, B, u->H, u->W,
                                                                    u->norm + 32, u->tgt);
     int st = loss_and_grads(u, B, s);
@@ -1227,11 +1267,12 @@ int swof_surrogate_predict(swof_unet *u, const float *in, int B, float *out, voi
     if (!u || !in || !out || B < 1 || B > u->maxB) return SWOF_EINVAL;
     cudaStream_t s = S(stream);
     long long P = (long long)B * u->H * u->W;
-    swof::k_pack_input<<<swof::grid_for(P * 16), 256, 0, s>>>(in, u->in_ch, B, u->H, u->W, u->norm, u->norm + 16, u->x0);
-    int st = forward(u, B, s, false);
+    swof::k_pack_input<<<swof::grid_for(P), 256, 0, s>>>(in, u->in_ch, B, u->H, u->W, u->norm, u->norm + 16, u->x0);
+    int st = forward(u, B, s, false, false);
     if (st) return st;
-    swof::k_residual<<<swof::grid_for((long long)B * u->out_ch * u->H * u->W), 256, 0, s>>>(
-        in, u->in_ch, u->out, u->out_ch, B, u->H, u->W, u->norm + 32, out);
+    const Layer &L = u->layers[17];
+    swof::k_head_residual<<<swof::grid_for(P), 256, (size_t)u->out_ch * u->C * sizeof(float), s>>>(
+        u->db[0], u->C, WB(u, 17), L.Kp, Bv(u, 17), in, u->in_ch, u->out_ch, B, u->H, u->W, u->norm + 32, out);
     return cudaGetLastError() == cudaSuccess ? SWOF_OK : SWOF_ECUDA;
 }
 

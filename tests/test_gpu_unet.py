@@ -205,3 +205,32 @@ def test_elementwise_forward_and_gradients(setup):
     # <= 3.9e-3, bias gradients <= 3.1e-3; both sides are deterministic
     assert max(fw) <= 4 * 2.0 ** -8, fw
     assert max(gw) <= 2 * 2.0 ** -8 and max(gb) <= 2 * 2.0 ** -8, (gw, gb)
+
+
+def test_predict_matches_reference(setup):
+    """The prediction path -- input normalisation and packing, the network,
+    then the 1x1 output convolution fused with the residual update -- against
+    the reference on the same bf16-rounded input, element by element within
+    4 bf16 units of each output channel's largest network value."""
+    import torch
+    net, p, x, tgt, C, H, B = setup
+    rng = np.random.default_rng(9)
+    state = rng.standard_normal((B, 4, H, H)).astype(np.float32)
+    mean = np.array([0.5, -0.1, 0.2, 0.0], np.float32)
+    scale_in = np.array([2.0, 0.5, 1.0, 3.0], np.float32)
+    scale_out = np.array([0.1, 0.2, 0.3], np.float32)
+    net.set_norm(mean, scale_in, scale_out)
+    out = torch.zeros((B, 3, H, H), device="cuda")
+    net.predict(torch.tensor(state, device="cuda"), out)
+    torch.cuda.synchronize()
+    xin = np.zeros((B, H, H, 16), np.float32)
+    inv = np.float32(1.0) / scale_in
+    xin[..., :4] = ((state - mean[None, :, None, None]) * inv[None, :, None, None]).transpose(0, 2, 3, 1)
+    xb = torch.tensor(xin).to(torch.bfloat16).float().numpy()
+    ref, _ = UNetRef(C, 4, 3, p.astype(np.float64), use_bf16=True).forward(xb.astype(np.float64))
+    want = state[:, :3] + scale_out[None, :, None, None] * ref[..., :3].transpose(0, 3, 1, 2)
+    got = out.cpu().numpy()
+    assert np.all(np.isfinite(got))
+    for c in range(3):
+        bound = 4 * 2.0 ** -8 * np.abs(ref[..., c]).max() * scale_out[c]
+        assert np.abs(got[:, c] - want[:, c]).max() <= bound, c
