@@ -570,6 +570,10 @@ __global__ void __launch_bounds__(HaloCfg<NT, CB>::THREADS)
 // per 8-column group of the weight rows.  No thread touches an operand.
 // Warp roles as in k_conv_halo.  K columns past the last tap (zero weights)
 // read whatever finite values the slot holds; the ring is zeroed at start.
+// SW (cin a multiple of 64, so a 64-wide K chunk lies in one tap): the
+// chunk's A operand is ONE box of 64 channels x 128 pixels and its weights
+// one box of 64 columns x NT rows, both written by the TMA unit in the
+// 128-byte-swizzled K-major layout -- two copies per chunk instead of 16.
 template <int NT>
 struct TmaCfg {
     static constexpr int STAGES = NT >= 256 ? 4 : 6;
@@ -582,7 +586,7 @@ struct TmaCfg {
     static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 256 * 4 + (2 * STAGES + 4) * 8 + 16 + 1024;
 };
 
-template <int NT>
+template <int NT, bool SW>
 __global__ void __launch_bounds__(TmaCfg<NT>::THREADS)
     k_conv_tma(ConvArgs A, const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap wmap)
 {
@@ -648,6 +652,15 @@ __global__ void __launch_bounds__(TmaCfg<NT>::THREADS)
                 const int b = rowi / A.H, y0 = rowi - b * A.H;
                 const uint32_t sa = sbase + slot * Cfg::STAGE_BYTES, sb = sa + Cfg::A_BYTES;
                 const uint32_t bar = tc05::smem_u32(&full[slot]);
+                if constexpr (SW) {
+                    const int k = kc * 64, tap = k >> A.cin_shift, c = k & (A.cin - 1);
+                    const int ty = A.ks == 3 ? (tap * 11) >> 5 : 0;    // tap / 3 for tap < 9
+                    const int dy = ty - half, dx = tap - ty * A.ks - half;
+                    tc05::mbar_arrive_expect_tx(bar, (uint32_t)(Cfg::A_BYTES + Cfg::B_BYTES));
+                    tc05::tma_load_4d(sa, &xmap, c, x0 + dx, y0 + dy, b, bar);
+                    tc05::tma_load_2d(sb, &wmap, k, n0, bar);
+                    continue;
+                }
                 int nA = 0;
                 for (int j = 0; j < 8; ++j) nA += ((kc * 64 + 8 * j) >> A.cin_shift) < taps;
                 tc05::mbar_arrive_expect_tx(bar, (uint32_t)(nA * 128 * 16 + 8 * NT * 16));
@@ -685,10 +698,15 @@ __global__ void __launch_bounds__(TmaCfg<NT>::THREADS)
                     tc05::fence_after();
                     const uint32_t a0 = sbase + slot * Cfg::STAGE_BYTES, b0 = a0 + Cfg::A_BYTES;
 #pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        tc05::mma_bf16(d, tc05::sdesc(a0 + q * 2 * 2048, 2048, 128),
-                                       tc05::sdesc(b0 + q * 2 * (NT * 16), NT * 16, 128), idesc,
-                                       (kc > 0 || q > 0) ? 1u : 0u);
+                    for (int q = 0; q < 4; ++q) {
+                        if constexpr (SW)
+                            tc05::mma_bf16(d, tc05::sdesc_sw128(a0 + q * 32), tc05::sdesc_sw128(b0 + q * 32), idesc,
+                                           (kc > 0 || q > 0) ? 1u : 0u);
+                        else
+                            tc05::mma_bf16(d, tc05::sdesc(a0 + q * 2 * 2048, 2048, 128),
+                                           tc05::sdesc(b0 + q * 2 * (NT * 16), NT * 16, 128), idesc,
+                                           (kc > 0 || q > 0) ? 1u : 0u);
+                    }
                     tc05::mma_commit(tc05::smem_u32(&empty[slot]));
                 }
                 if (ok) tc05::mma_commit(tc05::smem_u32(&accf[acc]));

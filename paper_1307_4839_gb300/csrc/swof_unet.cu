@@ -413,8 +413,9 @@ int conv_halo_launch(const ConvArgs &A, cudaStream_t s)
 
 // TMA maps of a same-resolution layer: the input slice (NHWC, channel
 // stride cx, offset xc0) with a 128-pixel tile box of 8 channels, and the
-// weight rows [ntot][Kp] with a box of 8 columns x NT rows.
-template <int NT>
+// weight rows [ntot][Kp] with a box of 8 columns x NT rows; SW: boxes of 64
+// channels / 64 columns, written with the 128-byte swizzle.
+template <int NT, bool SW>
 int conv_tma_launch(const ConvArgs &A, cudaStream_t s)
 {
     using Cfg = TmaCfg<NT>;
@@ -422,20 +423,21 @@ int conv_tma_launch(const ConvArgs &A, cudaStream_t s)
     if (!enc) return SWOF_ECUDA;
     CUtensorMap xmap, wmap;
     const int bw = A.W >= 128 ? 128 : A.W, bh = A.W >= 128 ? 1 : 128 / A.W;
+    const CUtensorMapSwizzle sz = SW ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE;
+    const cuuint32_t kbox = SW ? 64 : 8;
     cuuint64_t xd[4] = {(cuuint64_t)A.cin, (cuuint64_t)A.W, (cuuint64_t)A.H, (cuuint64_t)A.B};
     cuuint64_t xs[3] = {(cuuint64_t)A.cx * 2, (cuuint64_t)A.W * A.cx * 2, (cuuint64_t)A.H * A.W * A.cx * 2};
-    cuuint32_t xb[4] = {8, (cuuint32_t)bw, (cuuint32_t)bh, 1};
+    cuuint32_t xb[4] = {kbox, (cuuint32_t)bw, (cuuint32_t)bh, 1};
     cuuint32_t es[4] = {1, 1, 1, 1};
     if (enc(&xmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)(A.x + A.xc0), xd, xs, xb, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, sz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return SWOF_ECUDA;
     cuuint64_t wd[2] = {(cuuint64_t)A.Kp, (cuuint64_t)A.ntot};
     cuuint64_t ws[1] = {(cuuint64_t)A.Kp * 2};
-    cuuint32_t wb[2] = {8, (cuuint32_t)NT};
+    cuuint32_t wb[2] = {kbox, (cuuint32_t)NT};
     if (enc(&wmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)A.w, wd, ws, wb, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
-        CUDA_SUCCESS)
+            sz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return SWOF_ECUDA;
     static int per_dev[MAX_DEVICES] = {};
     const int dev = current_device();
@@ -443,10 +445,10 @@ int conv_tma_launch(const ConvArgs &A, cudaStream_t s)
     {
         std::lock_guard<std::mutex> g(g_launch_attr_lock);
         if (!per_dev[dev]) {
-            if (cudaFuncSetAttribute(k_conv_tma<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM) !=
-                cudaSuccess)
+            if (cudaFuncSetAttribute(k_conv_tma<NT, SW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)Cfg::SMEM) != cudaSuccess)
                 return SWOF_ECUDA;
-            per_dev[dev] = resident_ctas(k_conv_tma<NT>, Cfg::THREADS, Cfg::SMEM, dev);
+            per_dev[dev] = resident_ctas(k_conv_tma<NT, SW>, Cfg::THREADS, Cfg::SMEM, dev);
         }
         per_sm = per_dev[dev];
     }
@@ -455,7 +457,7 @@ int conv_tma_launch(const ConvArgs &A, cudaStream_t s)
     long long gx = (per_sm + gy - 1) / gy;
     if (gx > tiles) gx = tiles;
     if (gx < 1) gx = 1;
-    k_conv_tma<NT><<<dim3((unsigned)gx, (unsigned)gy), Cfg::THREADS, Cfg::SMEM, s>>>(A, xmap, wmap);
+    k_conv_tma<NT, SW><<<dim3((unsigned)gx, (unsigned)gy), Cfg::THREADS, Cfg::SMEM, s>>>(A, xmap, wmap);
     return cudaGetLastError() == cudaSuccess ? SWOF_OK : SWOF_ECUDA;
 }
 
@@ -529,11 +531,13 @@ int conv(ConvArgs A, cudaStream_t s)
     // (16-column layers -- the 1x1 output convolution -- stay on the gather
     // kernel: measured 35 us there against 54 us with TMA boxes at 256^2 x 8)
     if (tma_ok(A)) {
+        // one swizzled 64-channel box per K chunk when every chunk lies in one tap
+        const bool sw = A.cin % 64 == 0 && A.Kp == A.ks * A.ks * A.cin;
         switch (nt) {
-        case 32: return conv_tma_launch<32>(A, s);
-        case 64: return conv_tma_launch<64>(A, s);
-        case 128: return conv_tma_launch<128>(A, s);
-        case 256: return conv_tma_launch<256>(A, s);
+        case 32: return sw ? conv_tma_launch<32, true>(A, s) : conv_tma_launch<32, false>(A, s);
+        case 64: return sw ? conv_tma_launch<64, true>(A, s) : conv_tma_launch<64, false>(A, s);
+        case 128: return sw ? conv_tma_launch<128, true>(A, s) : conv_tma_launch<128, false>(A, s);
+        case 256: return sw ? conv_tma_launch<256, true>(A, s) : conv_tma_launch<256, false>(A, s);
         default: break;
         }
     }
