@@ -48,6 +48,8 @@ struct ConvArgs {
     int pre_round;             // 1: the activation acts on the bf16-rounded pre-activation
     int store;                 // STORE_NHWC or SCATTER_UP2
     int cout_up;               // SCATTER_UP2: output channels
+    int ystage;                // 32 or 64: bf16 output y staged in shared memory per piece of that many
+                               // columns and written by TMA stores (k_conv_halo, k_conv_tma); 0: plain stores
     int *err;
 };
 
@@ -187,6 +189,78 @@ __device__ __forceinline__ void conv_tile_epilogue(const ConvArgs &A, uint32_t t
             dp[0] = reinterpret_cast<uint4 *>(t)[0];
             dp[1] = reinterpret_cast<uint4 *>(t)[1];
         }
+    }
+}
+
+// Shared-memory staging of the TMA-store epilogue: per epilogue warp two
+// buffers of 32 rows (its pixels) x pw bf16 columns (pw = A.ystage), in the
+// swizzled layout of the output tensor map (128-byte swizzle for 64-column
+// rows, 64-byte for 32-column rows), so the 32 lanes' 16-byte writes of one
+// chunk hit distinct bank groups.
+constexpr int EPI_STAGE_BYTES_MAX = 4 * 2 * 32 * 64 * 2;   // 32 KB
+__host__ __device__ constexpr int epi_stage_bytes(int pw) { return 4 * 2 * 32 * pw * 2; }
+__device__ __forceinline__ uint32_t epi_swz(int r, int j, int pw)
+{
+    return pw == 64 ? (uint32_t)(r * 128 + ((j ^ (r & 7)) << 4)) : (uint32_t)(r * 64 + ((j ^ ((r >> 1) & 3)) << 4));
+}
+
+// The same epilogue for a bf16 output y only, through shared memory and TMA
+// stores: per piece of pw columns each lane writes its pixel's row into the
+// warp's staging buffer, lane 0 stores the 32 x pw block with one tensor
+// copy (NHWC: box {pw, 32} at (channel, pixel); SCATTER_UP2: the warp's 32
+// pixels are consecutive x of one input row, box {pw, 1, 32, 1} at
+// (channel, sub-x, x, output row)).  Two buffers alternate; a buffer is
+// rewritten only after the store that read it has finished reading.
+template <int NT>
+__device__ __forceinline__ void conv_tile_epilogue_tma(const ConvArgs &A, uint32_t tmem, int acc_col, int quarter,
+                                                       long long m0, int n0, const float *sbias,
+                                                       const CUtensorMap *ymap, uint8_t *stg, uint32_t &nbuf)
+{
+    const int lane = threadIdx.x & 31;
+    const int pw = A.ystage;
+    const long long p0 = m0 + quarter * 32;
+    const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)acc_col;
+    int b = 0, yy = 0, xx0 = 0;
+    if (A.store != STORE_NHWC) {
+        const int hw = A.H * A.W;
+        b = (int)(p0 / hw);
+        const int rem = (int)(p0 - (long long)b * hw);
+        yy = rem / A.W;
+        xx0 = rem - yy * A.W;
+    }
+#pragma unroll 1
+    for (int pc = 0; pc < NT; pc += pw) {
+        uint8_t *buf = stg + (nbuf & 1) * (32 * pw * 2);
+        if (lane == 0) tc05::bulk_wait_read<1>();
+        __syncwarp();
+#pragma unroll 1
+        for (int c0 = 0; c0 < pw; c0 += 16) {
+            float v[16];
+            tc05::tmem_ld16(tb + (uint32_t)(pc + c0), v);
+            __align__(16) __nv_bfloat16 t[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const float x = v[i] + sbias[pc + c0 + i];
+                // the activation acts on the bf16-rounded pre-activation
+                const float z = A.pre_round ? __bfloat162float(__float2bfloat16_rn(x)) : x;
+                t[i] = __float2bfloat16_rn(A.act == ACT_GELU ? gelu_f(z) : z);
+            }
+            *reinterpret_cast<uint4 *>(buf + epi_swz(lane, c0 >> 3, pw)) = reinterpret_cast<uint4 *>(t)[0];
+            *reinterpret_cast<uint4 *>(buf + epi_swz(lane, (c0 >> 3) + 1, pw)) = reinterpret_cast<uint4 *>(t)[1];
+        }
+        tc05::fence_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+            const int col = n0 + pc;
+            if (A.store == STORE_NHWC) {
+                tc05::tma_store_2d(ymap, tc05::smem_u32(buf), A.yc0 + col, (int)p0);
+            } else {
+                const int sub = col / A.cout_up, o = col - sub * A.cout_up;
+                tc05::tma_store_4d(ymap, tc05::smem_u32(buf), A.yc0 + o, sub & 1, xx0, b * 2 * A.H + 2 * yy + (sub >> 1));
+            }
+            tc05::bulk_commit();
+        }
+        ++nbuf;
     }
 }
 
@@ -411,26 +485,29 @@ struct HaloCfg {
     static constexpr int TC = NT < 32 ? 32 : NT;
     static constexpr int TMEM_COLS = 2 * TC;
     static constexpr int THREADS = 192;
-    static size_t smem(int Kp, int stages)
+    static size_t smem(int Kp, int stages, int stage_out = 0)
     {
-        return (size_t)stages * STAGE_BYTES + (size_t)NT * Kp * 2 + 256 * 4 + (2 * MAX_STAGES + 4) * 8 + 16 + 1024;
+        return (size_t)stages * STAGE_BYTES + (size_t)NT * Kp * 2 + 256 * 4 + (2 * MAX_STAGES + 4) * 8 + 16 + 1024 +
+               (size_t)stage_out;
     }
-    // the deepest ring (2 .. MAX_STAGES) that fits beside the weights; 0 if none
-    static int stages(int Kp)
+    // the deepest ring (2 .. MAX_STAGES) that fits beside the weights (and
+    // stage_out bytes of output staging); 0 if none
+    static int stages(int Kp, int stage_out = 0)
     {
         for (int sgs = MAX_STAGES; sgs >= 2; --sgs)
-            if (smem(Kp, sgs) <= (size_t)SMEM_MAX) return sgs;
+            if (smem(Kp, sgs, stage_out) <= (size_t)SMEM_MAX) return sgs;
         return 0;
     }
 };
 
 template <int NT, int CB>
 __global__ void __launch_bounds__(HaloCfg<NT, CB>::THREADS)
-    k_conv_halo(ConvArgs A, const __grid_constant__ CUtensorMap tmap, int S)
+    k_conv_halo(ConvArgs A, const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap ymap, int S)
 {
     using Cfg = HaloCfg<NT, CB>;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    uint8_t *base = smem_raw + ((1024 - (reinterpret_cast<uintptr_t>(smem_raw) & 1023)) & 1023);
+    uint8_t *stg = smem_raw + ((1024 - (reinterpret_cast<uintptr_t>(smem_raw) & 1023)) & 1023);
+    uint8_t *base = stg + (A.ystage ? epi_stage_bytes(A.ystage) : 0);   // TMA-store staging first (1024-aligned)
     uint8_t *wsm = base + S * Cfg::STAGE_BYTES;                        // weights, canonical per 64-chunk
     float *sbias = reinterpret_cast<float *>(wsm + (size_t)NT * A.Kp * 2);
     unsigned long long *full = reinterpret_cast<unsigned long long *>(sbias + 256);
@@ -542,16 +619,22 @@ __global__ void __launch_bounds__(HaloCfg<NT, CB>::THREADS)
     } else {
         // ---------------- epilogue ----------------
         const int quarter = warp & 3;
+        uint8_t *wstg = stg + quarter * (2 * 32 * A.ystage * 2);   // this warp's two staging buffers
+        uint32_t nbuf = 0;
 #pragma unroll 1
         for (int lt = 0; lt < my_tiles; ++lt) {
             const int acc = lt & 1;
             if (!conv_wait(tc05::smem_u32(&accf[acc]), (uint32_t)((lt >> 1) & 1), abort)) break;
             tc05::fence_after();
             const long long m0 = ((long long)blockIdx.x + (long long)lt * gridDim.x) * 128;
-            conv_tile_epilogue<NT>(A, tmem, acc * Cfg::TC, quarter, m0, n0, M, sbias);
+            if (A.ystage)
+                conv_tile_epilogue_tma<NT>(A, tmem, acc * Cfg::TC, quarter, m0, n0, sbias, &ymap, wstg, nbuf);
+            else
+                conv_tile_epilogue<NT>(A, tmem, acc * Cfg::TC, quarter, m0, n0, M, sbias);
             tc05::fence_before();
             mbar_arrive(tc05::smem_u32(&acce[acc]));
         }
+        if (A.ystage && lane == 0) tc05::bulk_wait<0>();   // the output stores have landed
     }
     tc05::fence_before();
     __syncthreads();
@@ -588,13 +671,15 @@ struct TmaCfg {
 
 template <int NT, bool SW>
 __global__ void __launch_bounds__(TmaCfg<NT>::THREADS)
-    k_conv_tma(ConvArgs A, const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap wmap)
+    k_conv_tma(ConvArgs A, const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap wmap,
+               const __grid_constant__ CUtensorMap ymap)
 {
     using Cfg = TmaCfg<NT>;
     constexpr int S = Cfg::STAGES;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *base = smem_raw + ((1024 - (reinterpret_cast<uintptr_t>(smem_raw) & 1023)) & 1023);
-    float *sbias = reinterpret_cast<float *>(base + S * Cfg::STAGE_BYTES);
+    uint8_t *stg = base + S * Cfg::STAGE_BYTES;                        // TMA-store staging (1024-aligned)
+    float *sbias = reinterpret_cast<float *>(stg + (A.ystage ? epi_stage_bytes(A.ystage) : 0));
     unsigned long long *full = reinterpret_cast<unsigned long long *>(sbias + 256);
     unsigned long long *empty = full + S;
     unsigned long long *accf = empty + S;
@@ -716,16 +801,22 @@ __global__ void __launch_bounds__(TmaCfg<NT>::THREADS)
     } else {
         // ---------------- epilogue ----------------
         const int quarter = warp & 3;
+        uint8_t *wstg = stg + quarter * (2 * 32 * A.ystage * 2);   // this warp's two staging buffers
+        uint32_t nbuf = 0;
 #pragma unroll 1
         for (int lt = 0; lt < my_tiles; ++lt) {
             const int acc = lt & 1;
             if (!conv_wait(tc05::smem_u32(&accf[acc]), (uint32_t)((lt >> 1) & 1), abort)) break;
             tc05::fence_after();
             const long long m0 = ((long long)blockIdx.x + (long long)lt * gridDim.x) * 128;
-            conv_tile_epilogue<NT>(A, tmem, acc * Cfg::TC, quarter, m0, n0, M, sbias);
+            if (A.ystage)
+                conv_tile_epilogue_tma<NT>(A, tmem, acc * Cfg::TC, quarter, m0, n0, sbias, &ymap, wstg, nbuf);
+            else
+                conv_tile_epilogue<NT>(A, tmem, acc * Cfg::TC, quarter, m0, n0, M, sbias);
             tc05::fence_before();
             mbar_arrive(tc05::smem_u32(&acce[acc]));
         }
+        if (A.ystage && lane == 0) tc05::bulk_wait<0>();   // the output stores have landed
     }
     tc05::fence_before();
     __syncthreads();

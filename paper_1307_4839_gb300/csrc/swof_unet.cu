@@ -366,10 +366,62 @@ EncodeTiledFn encode_tiled()
     return fn;
 }
 
+// Output tensor map of the TMA-store epilogue, for a bf16 output y alone
+// (no pre-activation or FP32 output): NHWC -- the [pixels][cy] array, box
+// {pw, 32}; SCATTER_UP2 -- the 2H x 2W output as [output rows][x][sub-x][cy]
+// (x the input column), box {pw, 1, 32, 1}, when each warp's 32 pixels lie
+// in one input row (W a multiple of 32).  pw = 64 columns (128-byte
+// swizzle) or 32 (64-byte swizzle).  Sets A.ystage = pw, or 0 (plain
+// stores) where the layout does not allow it.
+int epi_tma_map(ConvArgs &A, int nt, CUtensorMap *m)
+{
+    A.ystage = 0;
+    std::memset(m, 0, sizeof(*m));
+    if (!A.y || A.ypre || A.yf || nt < 32 || (A.cy * 2) % 16 || (A.yc0 * 2) % 16 ||
+        (reinterpret_cast<uintptr_t>(A.y) & 15))
+        return SWOF_OK;
+    int pw;
+    if (A.store == STORE_NHWC) {
+        pw = nt < 64 ? nt : 64;
+    } else {
+        if (A.W % 32 || A.cout_up % 32) return SWOF_OK;
+        pw = A.cout_up < 64 ? A.cout_up : 64;
+    }
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return SWOF_ECUDA;
+    const CUtensorMapSwizzle sz = pw == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r;
+    if (A.store == STORE_NHWC) {
+        cuuint64_t d[2] = {(cuuint64_t)A.cy, (cuuint64_t)A.B * A.H * A.W};
+        cuuint64_t st[1] = {(cuuint64_t)A.cy * 2};
+        cuuint32_t bx[2] = {(cuuint32_t)pw, 32};
+        r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)A.y, d, st, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sz,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+        cuuint64_t d[4] = {(cuuint64_t)A.cy, 2, (cuuint64_t)A.W, (cuuint64_t)A.B * 2 * A.H};
+        cuuint64_t st[3] = {(cuuint64_t)A.cy * 2, (cuuint64_t)A.cy * 4, (cuuint64_t)A.W * A.cy * 4};
+        cuuint32_t bx[4] = {(cuuint32_t)pw, 1, 32, 1};
+        r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)A.y, d, st, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sz,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
+    if (r != CUDA_SUCCESS) return SWOF_ECUDA;
+    A.ystage = pw;
+    return SWOF_OK;
+}
+
 template <int NT, int CB>
-int conv_halo_launch(const ConvArgs &A, cudaStream_t s)
+int conv_halo_launch(const ConvArgs &A0, cudaStream_t s)
 {
     using Cfg = HaloCfg<NT, CB>;
+    ConvArgs A = A0;
+    CUtensorMap ymap;
+    if (int e = epi_tma_map(A, NT, &ymap)) return e;
+    int stage_out = A.ystage ? epi_stage_bytes(A.ystage) : 0;
+    if (stage_out && Cfg::stages(A.Kp, stage_out) < 2) {    // no room: plain stores
+        A.ystage = 0;
+        stage_out = 0;
+    }
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return SWOF_ECUDA;
     CUtensorMap tmap;
@@ -381,9 +433,9 @@ int conv_halo_launch(const ConvArgs &A, cudaStream_t s)
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return SWOF_ECUDA;
-    const int stages = Cfg::stages(A.Kp);
+    const int stages = Cfg::stages(A.Kp, stage_out);
     if (stages < 2) return SWOF_EINVAL;
-    const size_t smem = Cfg::smem(A.Kp, stages);
+    const size_t smem = Cfg::smem(A.Kp, stages, stage_out);
     // the opt-in grows to the largest stage count asked for so far; the
     // resident CTAs are those of the size set last
     static int per_dev[MAX_DEVICES] = {};
@@ -407,7 +459,7 @@ int conv_halo_launch(const ConvArgs &A, cudaStream_t s)
     long long gx = (per_sm + gy - 1) / gy;
     if (gx > tiles) gx = tiles;
     if (gx < 1) gx = 1;
-    k_conv_halo<NT, CB><<<dim3((unsigned)gx, (unsigned)gy), Cfg::THREADS, smem, s>>>(A, tmap, stages);
+    k_conv_halo<NT, CB><<<dim3((unsigned)gx, (unsigned)gy), Cfg::THREADS, smem, s>>>(A, tmap, ymap, stages);
     return cudaGetLastError() == cudaSuccess ? SWOF_OK : SWOF_ECUDA;
 }
 
@@ -416,9 +468,15 @@ int conv_halo_launch(const ConvArgs &A, cudaStream_t s)
 // weight rows [ntot][Kp] with a box of 8 columns x NT rows; SW: boxes of 64
 // channels / 64 columns, written with the 128-byte swizzle.
 template <int NT, bool SW>
-int conv_tma_launch(const ConvArgs &A, cudaStream_t s)
+int conv_tma_launch(const ConvArgs &A0, cudaStream_t s)
 {
     using Cfg = TmaCfg<NT>;
+    ConvArgs A = A0;
+    CUtensorMap ymap;
+    if (int e = epi_tma_map(A, NT, &ymap)) return e;
+    const size_t smem = Cfg::SMEM + (A.ystage ? (size_t)epi_stage_bytes(A.ystage) : 0);
+    constexpr size_t smem_max = Cfg::SMEM + EPI_STAGE_BYTES_MAX;
+    static_assert(smem_max <= 227 * 1024, "TMA-operand conv: shared memory over the limit");
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return SWOF_ECUDA;
     CUtensorMap xmap, wmap;
@@ -446,9 +504,9 @@ int conv_tma_launch(const ConvArgs &A, cudaStream_t s)
         std::lock_guard<std::mutex> g(g_launch_attr_lock);
         if (!per_dev[dev]) {
             if (cudaFuncSetAttribute(k_conv_tma<NT, SW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)Cfg::SMEM) != cudaSuccess)
+                                     (int)smem_max) != cudaSuccess)
                 return SWOF_ECUDA;
-            per_dev[dev] = resident_ctas(k_conv_tma<NT, SW>, Cfg::THREADS, Cfg::SMEM, dev);
+            per_dev[dev] = resident_ctas(k_conv_tma<NT, SW>, Cfg::THREADS, smem_max, dev);
         }
         per_sm = per_dev[dev];
     }
@@ -457,7 +515,7 @@ int conv_tma_launch(const ConvArgs &A, cudaStream_t s)
     long long gx = (per_sm + gy - 1) / gy;
     if (gx > tiles) gx = tiles;
     if (gx < 1) gx = 1;
-    k_conv_tma<NT, SW><<<dim3((unsigned)gx, (unsigned)gy), Cfg::THREADS, Cfg::SMEM, s>>>(A, xmap, wmap);
+    k_conv_tma<NT, SW><<<dim3((unsigned)gx, (unsigned)gy), Cfg::THREADS, smem, s>>>(A, xmap, wmap, ymap);
     return cudaGetLastError() == cudaSuccess ? SWOF_OK : SWOF_ECUDA;
 }
 
