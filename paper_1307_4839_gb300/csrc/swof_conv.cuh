@@ -138,14 +138,15 @@ __device__ __forceinline__ bool conv_wait(uint32_t bar, uint32_t parity, volatil
 // from shared memory, optional pre-activation, activation, stores.
 template <int NT>
 __device__ __forceinline__ void conv_tile_epilogue(const ConvArgs &A, uint32_t tmem, int acc_col, int quarter,
-                                                   long long m0, int n0, long long M, const float *sbias)
+                                                   long long m0, int n0, long long M, const float *sbias, int cb = 0,
+                                                   int ce = NT)
 {
     const int lane = threadIdx.x & 31;
     const int hw = A.H * A.W;
     const long long p = m0 + quarter * 32 + lane;
     const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)acc_col;
 #pragma unroll 1
-    for (int c0 = 0; c0 < NT; c0 += 16) {
+    for (int c0 = cb; c0 < ce; c0 += 16) {
         float v[16];
         tc05::tmem_ld16(tb + (uint32_t)c0, v);
         if (p >= M) continue;
@@ -192,16 +193,20 @@ __device__ __forceinline__ void conv_tile_epilogue(const ConvArgs &A, uint32_t t
     }
 }
 
-// Shared-memory staging of the TMA-store epilogue: per epilogue warp two
-// buffers of 32 rows (its pixels) x pw bf16 columns (pw = A.ystage), in the
-// swizzled layout of the output tensor map (128-byte swizzle for 64-column
-// rows, 64-byte for 32-column rows), so the 32 lanes' 16-byte writes of one
-// chunk hit distinct bank groups.
-constexpr int EPI_STAGE_BYTES_MAX = 4 * 2 * 32 * 64 * 2;   // 32 KB
-__host__ __device__ constexpr int epi_stage_bytes(int pw) { return 4 * 2 * 32 * pw * 2; }
+// Shared-memory staging of the TMA-store epilogue: per epilogue warp one
+// (pw = 64) or two buffers of 32 rows (its pixels) x pw bf16 columns
+// (pw = A.ystage), in the swizzled layout of the output tensor map (128-,
+// 64- or 32-byte swizzle for rows of 64, 32 or 16 columns), so the 32
+// lanes' 16-byte writes of one chunk hit distinct bank groups.
+constexpr int EPI_WARPS = 8;                                 // two per TMEM lane quarter
+__host__ __device__ constexpr int epi_bufs(int pw) { return pw == 64 ? 1 : 2; }
+__host__ __device__ constexpr int epi_stage_bytes(int pw) { return EPI_WARPS * epi_bufs(pw) * 32 * pw * 2; }
+constexpr int EPI_STAGE_BYTES_MAX = 32 * 1024;               // epi_stage_bytes(16 / 32 / 64) <= 32 KB
 __device__ __forceinline__ uint32_t epi_swz(int r, int j, int pw)
 {
-    return pw == 64 ? (uint32_t)(r * 128 + ((j ^ (r & 7)) << 4)) : (uint32_t)(r * 64 + ((j ^ ((r >> 1) & 3)) << 4));
+    return pw == 64   ? (uint32_t)(r * 128 + ((j ^ (r & 7)) << 4))                 // 128-byte swizzle
+           : pw == 32 ? (uint32_t)(r * 64 + ((j ^ ((r >> 1) & 3)) << 4))           // 64-byte swizzle
+                      : (uint32_t)(r * 32 + ((j ^ ((r >> 2) & 1)) << 4));          // 32-byte swizzle
 }
 
 // The same epilogue for a bf16 output y only, through shared memory and TMA
@@ -214,7 +219,8 @@ __device__ __forceinline__ uint32_t epi_swz(int r, int j, int pw)
 template <int NT>
 __device__ __forceinline__ void conv_tile_epilogue_tma(const ConvArgs &A, uint32_t tmem, int acc_col, int quarter,
                                                        long long m0, int n0, const float *sbias,
-                                                       const CUtensorMap *ymap, uint8_t *stg, uint32_t &nbuf)
+                                                       const CUtensorMap *ymap, uint8_t *stg, uint32_t &nbuf,
+                                                       int cb, int ce)
 {
     const int lane = threadIdx.x & 31;
     const int pw = A.ystage;
@@ -229,9 +235,14 @@ __device__ __forceinline__ void conv_tile_epilogue_tma(const ConvArgs &A, uint32
         xx0 = rem - yy * A.W;
     }
 #pragma unroll 1
-    for (int pc = 0; pc < NT; pc += pw) {
-        uint8_t *buf = stg + (nbuf & 1) * (32 * pw * 2);
-        if (lane == 0) tc05::bulk_wait_read<1>();
+    for (int pc = cb; pc < ce; pc += pw) {
+        uint8_t *buf = stg + (epi_bufs(pw) == 2 ? (nbuf & 1) : 0) * (32 * pw * 2);
+        if (lane == 0) {
+            if (epi_bufs(pw) == 2)
+                tc05::bulk_wait_read<1>();
+            else
+                tc05::bulk_wait_read<0>();
+        }
         __syncwarp();
 #pragma unroll 1
         for (int c0 = 0; c0 < pw; c0 += 16) {
@@ -462,32 +473,40 @@ __global__ void __launch_bounds__(ConvCfg<NT>::THREADS) k_conv(ConvArgs A)
 // ---------------------------------------------------------------------------
 // 3x3 convolution over image rows of W >= 128 pixels (W a multiple of 128)
 // without a gather.  A tile is 128 consecutive pixels (h, w0 .. w0+127) of
-// one image row.  For each block of CB input channels the producer loads the
-// tile's halo -- rows h-1 .. h+1, pixels w0-1 .. w0+128 -- with one TMA box
-// per 8-channel plane, laid out plane by plane with the pixels at a 16-byte
-// stride; the box's out-of-image part is zero-filled by the TMA unit.  In
-// that layout the A operand of tap (dy, dx) is the same 128 x CB tile
-// shifted by ((1 + dy) * 130 + 1 + dx) pixels: a K-major no-swizzle
-// descriptor with 8-row groups 128 B apart (SBO) and k-groups one plane
-// apart (LBO).  The whole weight tile [NT][Kp] stays in shared memory.
-// Warp roles: 0 TMA producer, 1 MMA issue, 2-5 epilogue (two TMEM
-// accumulators, as in k_conv).  The halo ring has S stages, as many as
-// fit beside the weights (2 .. 6).
+// one image row.  For each block of CB input channels (16, 32 or 64) the
+// producer loads the tile's halo -- rows h-1 .. h+1, pixels w0-1 .. w0+128 --
+// with ONE TMA box of CB channels x 130 pixels x 3 rows, zero-filled outside
+// the image: 390 rows of CB * 2 bytes, one per halo pixel, written with the
+// swizzle of that row width.  In that layout the A operand of tap (dy, dx)
+// is the 128 rows starting at halo pixel (1 + dy) * 130 + 1 + dx: a K-major
+// swizzled descriptor started at that row (the swizzle follows the address).
+// (Boxes one 8-channel plane wide, 16-byte rows, kept the TMA unit busy for
+// ~1.2 cycles per row and set the pace of these layers.)  The whole weight
+// tile [NT][Kp] stays in shared memory.
+// Warp roles: 0 TMA producer, 1 MMA issue, 2-9 epilogue (two warps per
+// TMEM lane quarter, each draining half of the columns).  Four TMEM
+// accumulators (two at 256 columns): with 32 or 64 output channels a tile's
+// MMAs are short, and the MMAs of tile t + NACC wait for tile t's epilogue
+// to have drained its accumulator, so more accumulators hide more of the
+// epilogue's latency.  The halo ring has S stages, as many as fit beside the
+// weights (2 .. 6).
 constexpr int HALO_PX = 130, HALO_ROWS = 3;
-constexpr int HALO_PLANE = ((HALO_PX * HALO_ROWS * 16 + 127) / 128) * 128;   // 6272 B, 128-B aligned
 
 template <int NT, int CB>
 struct HaloCfg {
     static constexpr int MAX_STAGES = 6;
-    static constexpr int STAGE_BYTES = (CB / 8) * HALO_PLANE;
+    static constexpr int ROW_BYTES = CB * 2;                              // one halo pixel's CB channels
+    static constexpr int BOX_BYTES = HALO_PX * HALO_ROWS * ROW_BYTES;
+    static constexpr int STAGE_BYTES = (BOX_BYTES + 1023) / 1024 * 1024;  // stages on swizzle-group boundaries
     static constexpr int WMAX = 160 * 1024;                // resident weight tile limit
     static constexpr int SMEM_MAX = 227 * 1024;
     static constexpr int TC = NT < 32 ? 32 : NT;
-    static constexpr int TMEM_COLS = 2 * TC;
-    static constexpr int THREADS = 192;
+    static constexpr int NACC = TC <= 128 ? 4 : 2;        // TMEM accumulators (4 x TC <= 512 columns)
+    static constexpr int TMEM_COLS = NACC * TC;
+    static constexpr int THREADS = 32 * (2 + EPI_WARPS);   // producer, MMA issuer, epilogue warps
     static size_t smem(int Kp, int stages, int stage_out = 0)
     {
-        return (size_t)stages * STAGE_BYTES + (size_t)NT * Kp * 2 + 256 * 4 + (2 * MAX_STAGES + 4) * 8 + 16 + 1024 +
+        return (size_t)stages * STAGE_BYTES + (size_t)NT * Kp * 2 + 256 * 4 + (2 * MAX_STAGES + 2 * NACC) * 8 + 16 + 1024 +
                (size_t)stage_out;
     }
     // the deepest ring (2 .. MAX_STAGES) that fits beside the weights (and
@@ -513,8 +532,8 @@ __global__ void __launch_bounds__(HaloCfg<NT, CB>::THREADS)
     unsigned long long *full = reinterpret_cast<unsigned long long *>(sbias + 256);
     unsigned long long *empty = full + S;
     unsigned long long *accf = empty + S;
-    unsigned long long *acce = accf + 2;
-    uint32_t *tmem_word = reinterpret_cast<uint32_t *>(acce + 2);
+    unsigned long long *acce = accf + Cfg::NACC;
+    uint32_t *tmem_word = reinterpret_cast<uint32_t *>(acce + Cfg::NACC);
     volatile int *abort = reinterpret_cast<volatile int *>(tmem_word + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long M = (long long)A.B * A.H * A.W;
@@ -534,9 +553,9 @@ __global__ void __launch_bounds__(HaloCfg<NT, CB>::THREADS)
             tc05::mbar_init(tc05::smem_u32(&full[q]), 1);
             tc05::mbar_init(tc05::smem_u32(&empty[q]), 1);
         }
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < Cfg::NACC; ++q) {
             tc05::mbar_init(tc05::smem_u32(&accf[q]), 1);
-            tc05::mbar_init(tc05::smem_u32(&acce[q]), 128);
+            tc05::mbar_init(tc05::smem_u32(&acce[q]), 32 * EPI_WARPS);
         }
         *abort = 0;
     }
@@ -568,11 +587,8 @@ __global__ void __launch_bounds__(HaloCfg<NT, CB>::THREADS)
                 const int rowi = t / per_row, w0 = (t - rowi * per_row) * 128;
                 const int b = rowi / A.H, h = rowi - b * A.H;
                 const uint32_t bar = tc05::smem_u32(&full[slot]);
-                tc05::mbar_arrive_expect_tx(bar, (uint32_t)((CB / 8) * HALO_PX * HALO_ROWS * 16));
-#pragma unroll
-                for (int q = 0; q < CB / 8; ++q)
-                    tc05::tma_load_4d(sbase + slot * Cfg::STAGE_BYTES + q * HALO_PLANE, &tmap, cb * CB + 8 * q, w0 - 1,
-                                      h - 1, b, bar);
+                tc05::mbar_arrive_expect_tx(bar, (uint32_t)Cfg::BOX_BYTES);
+                tc05::tma_load_4d(sbase + slot * Cfg::STAGE_BYTES, &tmap, cb * CB, w0 - 1, h - 1, b, bar);
             }
         }
         __syncwarp();
@@ -583,8 +599,8 @@ __global__ void __launch_bounds__(HaloCfg<NT, CB>::THREADS)
             bool ok = true;
 #pragma unroll 1
             for (int lt = 0; lt < my_tiles && ok; ++lt) {
-                const int acc = lt & 1;
-                if (!conv_wait(tc05::smem_u32(&acce[acc]), (uint32_t)(((lt >> 1) & 1) ^ 1), abort)) break;
+                const int acc = lt % Cfg::NACC;
+                if (!conv_wait(tc05::smem_u32(&acce[acc]), (uint32_t)(((lt / Cfg::NACC) & 1) ^ 1), abort)) break;
                 tc05::fence_after();
                 const uint32_t d = tmem + (uint32_t)(acc * Cfg::TC);
 #pragma unroll 1
@@ -599,13 +615,13 @@ __global__ void __launch_bounds__(HaloCfg<NT, CB>::THREADS)
 #pragma unroll 1
                     for (int tap = 0; tap < 9; ++tap) {
                         const int ty = (tap * 11) >> 5, tx = tap - 3 * ty;        // tap / 3, tap % 3
-                        const uint32_t a_tap = hb + (uint32_t)((ty * HALO_PX + tx) * 16);
+                        const uint32_t a_tap = hb + (uint32_t)((ty * HALO_PX + tx) * Cfg::ROW_BYTES);
                         const int kb = tap * A.cin + cb * CB;                     // weight column of this slice
 #pragma unroll
                         for (int q = 0; q < CB / 16; ++q) {
                             const int k = kb + 16 * q;
                             const uint32_t b_k = wbase + (uint32_t)((k >> 6) * (NT * 128) + ((k & 63) >> 3) * 128);
-                            tc05::mma_bf16(d, tc05::sdesc(a_tap + (uint32_t)(2 * q * HALO_PLANE), HALO_PLANE, 128),
+                            tc05::mma_bf16(d, tc05::sdesc_swz(a_tap + (uint32_t)(32 * q), Cfg::ROW_BYTES),
                                            tc05::sdesc(b_k, tc05::CANON_LBO, tc05::CANON_SBO), idesc,
                                            (cb > 0 || tap > 0 || q > 0) ? 1u : 0u);
                         }
@@ -618,19 +634,23 @@ __global__ void __launch_bounds__(HaloCfg<NT, CB>::THREADS)
         __syncwarp();
     } else {
         // ---------------- epilogue ----------------
-        const int quarter = warp & 3;
-        uint8_t *wstg = stg + quarter * (2 * 32 * A.ystage * 2);   // this warp's two staging buffers
+        // two warps per TMEM lane quarter (warp % 4), each half of the columns
+        // (16-column tiles: the first warp of the pair takes all 16)
+        constexpr int PER = NT >= 32 ? NT / 2 : NT;
+        const int quarter = warp & 3, e = warp - 2;
+        const int cb = (e >> 2) * PER < NT ? (e >> 2) * PER : NT, ce = cb + PER < NT ? cb + PER : NT;
+        uint8_t *wstg = stg + e * (epi_bufs(A.ystage) * 32 * A.ystage * 2);   // this warp's staging
         uint32_t nbuf = 0;
 #pragma unroll 1
         for (int lt = 0; lt < my_tiles; ++lt) {
-            const int acc = lt & 1;
-            if (!conv_wait(tc05::smem_u32(&accf[acc]), (uint32_t)((lt >> 1) & 1), abort)) break;
+            const int acc = lt % Cfg::NACC;
+            if (!conv_wait(tc05::smem_u32(&accf[acc]), (uint32_t)((lt / Cfg::NACC) & 1), abort)) break;
             tc05::fence_after();
             const long long m0 = ((long long)blockIdx.x + (long long)lt * gridDim.x) * 128;
             if (A.ystage)
-                conv_tile_epilogue_tma<NT>(A, tmem, acc * Cfg::TC, quarter, m0, n0, sbias, &ymap, wstg, nbuf);
+                conv_tile_epilogue_tma<NT>(A, tmem, acc * Cfg::TC, quarter, m0, n0, sbias, &ymap, wstg, nbuf, cb, ce);
             else
-                conv_tile_epilogue<NT>(A, tmem, acc * Cfg::TC, quarter, m0, n0, M, sbias);
+                conv_tile_epilogue<NT>(A, tmem, acc * Cfg::TC, quarter, m0, n0, M, sbias, cb, ce);
             tc05::fence_before();
             mbar_arrive(tc05::smem_u32(&acce[acc]));
         }
@@ -664,9 +684,10 @@ struct TmaCfg {
     static constexpr int B_BYTES = 8 * NT * 16;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr int TC = NT < 32 ? 32 : NT;
-    static constexpr int TMEM_COLS = 2 * TC;
-    static constexpr int THREADS = 192;
-    static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 256 * 4 + (2 * STAGES + 4) * 8 + 16 + 1024;
+    static constexpr int NACC = TC <= 128 ? 4 : 2;        // TMEM accumulators (4 x TC <= 512 columns)
+    static constexpr int TMEM_COLS = NACC * TC;
+    static constexpr int THREADS = 32 * (2 + EPI_WARPS);   // producer, MMA issuer, epilogue warps
+    static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 256 * 4 + (2 * STAGES + 2 * NACC) * 8 + 16 + 1024;
 };
 
 template <int NT, bool SW>
@@ -683,8 +704,8 @@ __global__ void __launch_bounds__(TmaCfg<NT>::THREADS)
     unsigned long long *full = reinterpret_cast<unsigned long long *>(sbias + 256);
     unsigned long long *empty = full + S;
     unsigned long long *accf = empty + S;
-    unsigned long long *acce = accf + 2;
-    uint32_t *tmem_word = reinterpret_cast<uint32_t *>(acce + 2);
+    unsigned long long *acce = accf + Cfg::NACC;
+    uint32_t *tmem_word = reinterpret_cast<uint32_t *>(acce + Cfg::NACC);
     volatile int *abort = reinterpret_cast<volatile int *>(tmem_word + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long M = (long long)A.B * A.H * A.W;
@@ -703,9 +724,9 @@ __global__ void __launch_bounds__(TmaCfg<NT>::THREADS)
             tc05::mbar_init(tc05::smem_u32(&full[q]), 1);
             tc05::mbar_init(tc05::smem_u32(&empty[q]), 1);
         }
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < Cfg::NACC; ++q) {
             tc05::mbar_init(tc05::smem_u32(&accf[q]), 1);
-            tc05::mbar_init(tc05::smem_u32(&acce[q]), 128);
+            tc05::mbar_init(tc05::smem_u32(&acce[q]), 32 * EPI_WARPS);
         }
         *abort = 0;
     }
@@ -769,8 +790,8 @@ __global__ void __launch_bounds__(TmaCfg<NT>::THREADS)
             bool ok = true;
 #pragma unroll 1
             for (int lt = 0; lt < my_tiles && ok; ++lt) {
-                const int acc = lt & 1;
-                if (!conv_wait(tc05::smem_u32(&acce[acc]), (uint32_t)(((lt >> 1) & 1) ^ 1), abort)) break;
+                const int acc = lt % Cfg::NACC;
+                if (!conv_wait(tc05::smem_u32(&acce[acc]), (uint32_t)(((lt / Cfg::NACC) & 1) ^ 1), abort)) break;
                 tc05::fence_after();
                 const uint32_t d = tmem + (uint32_t)(acc * Cfg::TC);
 #pragma unroll 1
@@ -800,19 +821,23 @@ __global__ void __launch_bounds__(TmaCfg<NT>::THREADS)
         __syncwarp();
     } else {
         // ---------------- epilogue ----------------
-        const int quarter = warp & 3;
-        uint8_t *wstg = stg + quarter * (2 * 32 * A.ystage * 2);   // this warp's two staging buffers
+        // two warps per TMEM lane quarter (warp % 4), each half of the columns
+        // (16-column tiles: the first warp of the pair takes all 16)
+        constexpr int PER = NT >= 32 ? NT / 2 : NT;
+        const int quarter = warp & 3, e = warp - 2;
+        const int cb = (e >> 2) * PER < NT ? (e >> 2) * PER : NT, ce = cb + PER < NT ? cb + PER : NT;
+        uint8_t *wstg = stg + e * (epi_bufs(A.ystage) * 32 * A.ystage * 2);   // this warp's staging
         uint32_t nbuf = 0;
 #pragma unroll 1
         for (int lt = 0; lt < my_tiles; ++lt) {
-            const int acc = lt & 1;
-            if (!conv_wait(tc05::smem_u32(&accf[acc]), (uint32_t)((lt >> 1) & 1), abort)) break;
+            const int acc = lt % Cfg::NACC;
+            if (!conv_wait(tc05::smem_u32(&accf[acc]), (uint32_t)((lt / Cfg::NACC) & 1), abort)) break;
             tc05::fence_after();
             const long long m0 = ((long long)blockIdx.x + (long long)lt * gridDim.x) * 128;
             if (A.ystage)
-                conv_tile_epilogue_tma<NT>(A, tmem, acc * Cfg::TC, quarter, m0, n0, sbias, &ymap, wstg, nbuf);
+                conv_tile_epilogue_tma<NT>(A, tmem, acc * Cfg::TC, quarter, m0, n0, sbias, &ymap, wstg, nbuf, cb, ce);
             else
-                conv_tile_epilogue<NT>(A, tmem, acc * Cfg::TC, quarter, m0, n0, M, sbias);
+                conv_tile_epilogue<NT>(A, tmem, acc * Cfg::TC, quarter, m0, n0, M, sbias, cb, ce);
             tc05::fence_before();
             mbar_arrive(tc05::smem_u32(&acce[acc]));
         }

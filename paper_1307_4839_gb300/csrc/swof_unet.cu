@@ -370,9 +370,9 @@ EncodeTiledFn encode_tiled()
 // (no pre-activation or FP32 output): NHWC -- the [pixels][cy] array, box
 // {pw, 32}; SCATTER_UP2 -- the 2H x 2W output as [output rows][x][sub-x][cy]
 // (x the input column), box {pw, 1, 32, 1}, when each warp's 32 pixels lie
-// in one input row (W a multiple of 32).  pw = 64 columns (128-byte
-// swizzle) or 32 (64-byte swizzle).  Sets A.ystage = pw, or 0 (plain
-// stores) where the layout does not allow it.
+// in one input row (W a multiple of 32).  pw = 64, 32 or 16 columns
+// (128-, 64- or 32-byte swizzle).  Sets A.ystage = pw, or 0 (plain stores)
+// where the layout does not allow it.
 int epi_tma_map(ConvArgs &A, int nt, CUtensorMap *m)
 {
     A.ystage = 0;
@@ -380,16 +380,18 @@ int epi_tma_map(ConvArgs &A, int nt, CUtensorMap *m)
     if (!A.y || A.ypre || A.yf || nt < 32 || (A.cy * 2) % 16 || (A.yc0 * 2) % 16 ||
         (reinterpret_cast<uintptr_t>(A.y) & 15))
         return SWOF_OK;
-    int pw;
+    int pw;                       // each epilogue warp takes nt / 2 columns
     if (A.store == STORE_NHWC) {
-        pw = nt < 64 ? nt : 64;
+        pw = nt / 2 < 64 ? nt / 2 : 64;
     } else {
         if (A.W % 32 || A.cout_up % 32) return SWOF_OK;
         pw = A.cout_up < 64 ? A.cout_up : 64;
     }
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return SWOF_ECUDA;
-    const CUtensorMapSwizzle sz = pw == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+    const CUtensorMapSwizzle sz = pw == 64   ? CU_TENSOR_MAP_SWIZZLE_128B
+                                  : pw == 32 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                             : CU_TENSOR_MAP_SWIZZLE_32B;
     cuuint32_t es[4] = {1, 1, 1, 1};
     CUresult r;
     if (A.store == STORE_NHWC) {
@@ -427,10 +429,13 @@ int conv_halo_launch(const ConvArgs &A0, cudaStream_t s)
     CUtensorMap tmap;
     cuuint64_t dims[4] = {(cuuint64_t)A.cin, (cuuint64_t)A.W, (cuuint64_t)A.H, (cuuint64_t)A.B};
     cuuint64_t strides[3] = {(cuuint64_t)A.cx * 2, (cuuint64_t)A.W * A.cx * 2, (cuuint64_t)A.H * A.W * A.cx * 2};
-    cuuint32_t box[4] = {8, (cuuint32_t)HALO_PX, (cuuint32_t)HALO_ROWS, 1};
+    cuuint32_t box[4] = {(cuuint32_t)CB, (cuuint32_t)HALO_PX, (cuuint32_t)HALO_ROWS, 1};
     cuuint32_t es[4] = {1, 1, 1, 1};
+    const CUtensorMapSwizzle sz = CB == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                  : CB == 32 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                             : CU_TENSOR_MAP_SWIZZLE_32B;
     if (enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)(A.x + A.xc0), dims, strides, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, sz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return SWOF_ECUDA;
     const int stages = Cfg::stages(A.Kp, stage_out);

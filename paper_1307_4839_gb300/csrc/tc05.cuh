@@ -137,22 +137,27 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
     return d;          // base offset 0, layout type 0 (no swizzle)
 }
 
-// Shared-memory matrix descriptor, K-major with the 128-byte swizzle (the
-// layout a TMA copy with CU_TENSOR_MAP_SWIZZLE_128B writes): one 128-byte
-// row (64 bf16 of K) per M (or N) row, the 16-byte chunks of row r stored at
-// chunk position (j ^ r % 8) within each 1024-byte group of 8 rows; 8-row
-// groups 1024 B apart (sbo).  The group must start on a 1024-byte boundary;
-// a K16 slice at k0 within the row starts at addr + 2 * k0.
-__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr)
+// Shared-memory matrix descriptor, K-major with a 32-, 64- or 128-byte
+// swizzle (the layout a TMA copy with CU_TENSOR_MAP_SWIZZLE_32B / 64B / 128B
+// writes when its rows are that wide): one row of row_bytes (16, 32 or 64
+// bf16 of K) per M (or N) row, the 16-byte chunks permuted by the address
+// bits above them within each 8-row group; 8-row groups 8 * row_bytes apart
+// (sbo).  The swizzle follows the shared-memory address, so the copy's
+// destination must start on a multiple of 8 rows (1024 B at 128-byte rows)
+// and a start at any row of it (or at a K16 slice k0 within the row: addr +
+// 2 * k0) addresses the same data.
+__device__ __forceinline__ uint64_t sdesc_swz(uint32_t addr, uint32_t row_bytes)
 {
+    const uint64_t mode = row_bytes == 128 ? 2 : (row_bytes == 64 ? 4 : 6);   // 128 B, 64 B, 32 B
     uint64_t d = 0;
     d |= (uint64_t)((addr >> 4) & 0x3FFFu);
-    d |= 1ull << 16;                          // leading byte offset: unused by swizzled K-major layouts
-    d |= (uint64_t)(1024u >> 4) << 32;        // stride byte offset
-    d |= 1ull << 46;                          // descriptor version of the sm_100 family
-    d |= 2ull << 61;                          // layout type: 128-byte swizzle
+    d |= 1ull << 16;                              // leading byte offset: unused by swizzled K-major layouts
+    d |= (uint64_t)(((8 * row_bytes) >> 4) & 0x3FFFu) << 32;   // stride byte offset
+    d |= 1ull << 46;                              // descriptor version of the sm_100 family
+    d |= mode << 61;                              // layout type
     return d;
 }
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) { return sdesc_swz(addr, 128); }
 
 // Instruction descriptor of kind::f16: BF16 A and B, FP32 accumulator,
 // both operands K-major, shape M x N (M in {64, 128}, N multiple of 16).
