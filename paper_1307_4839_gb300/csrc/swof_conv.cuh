@@ -559,11 +559,12 @@ __global__ void __launch_bounds__(HaloCfg<NT, CB>::THREADS)
         }
         *abort = 0;
     }
-    // resident weights and biases
+    // resident weights and biases: K-major core matrices [k / 8][NT rows][8],
+    // so the descriptor of weight column k is a linear step from column 0
     const uint32_t wbase = tc05::smem_u32(wsm);
     for (int v = tid; v < NT * (A.Kp / 8); v += Cfg::THREADS) {
-        const int r = v % NT, kg = v / NT, k = kg * 8;
-        cp_async16(wbase + (k >> 6) * (NT * 128) + tc05::canon_off(r, k & 63), A.w + (long long)(n0 + r) * A.Kp + k, 16u);
+        const int r = v % NT, kg = v / NT;
+        cp_async16(wbase + (uint32_t)(kg * (NT * 16) + r * 16), A.w + (long long)(n0 + r) * A.Kp + kg * 8, 16u);
     }
     cp_async_commit();
     for (int i = tid; i < NT; i += Cfg::THREADS) sbias[i] = A.bias ? A.bias[n0 + i] : 0.0f;
@@ -596,6 +597,7 @@ __global__ void __launch_bounds__(HaloCfg<NT, CB>::THREADS)
         // ---------------- MMA issue ----------------
         if (lane == 0) {
             const uint32_t idesc = tc05::idesc_bf16(128, NT);
+            const uint64_t b_tap_step = (uint64_t)((A.cin * NT * 2) >> 4);   // weight columns tap*cin apart
             bool ok = true;
 #pragma unroll 1
             for (int lt = 0; lt < my_tiles && ok; ++lt) {
@@ -611,20 +613,20 @@ __global__ void __launch_bounds__(HaloCfg<NT, CB>::THREADS)
                         break;
                     }
                     tc05::fence_after();
-                    const uint32_t hb = sbase + slot * Cfg::STAGE_BYTES;
-#pragma unroll 1
-                    for (int tap = 0; tap < 9; ++tap) {
-                        const int ty = (tap * 11) >> 5, tx = tap - 3 * ty;        // tap / 3, tap % 3
-                        const uint32_t a_tap = hb + (uint32_t)((ty * HALO_PX + tx) * Cfg::ROW_BYTES);
-                        const int kb = tap * A.cin + cb * CB;                     // weight column of this slice
+                    // descriptors built once per stage and stepped by constants
+                    // (descriptor address fields count 16-byte units): the
+                    // single issuing thread spends ~2 instructions per MMA
+                    const uint64_t a0 = tc05::sdesc_swz(sbase + slot * Cfg::STAGE_BYTES, Cfg::ROW_BYTES);
+                    const uint64_t b0 = tc05::sdesc(wbase + (uint32_t)(cb * CB * NT * 2), NT * 16, 128);
 #pragma unroll
-                        for (int q = 0; q < CB / 16; ++q) {
-                            const int k = kb + 16 * q;
-                            const uint32_t b_k = wbase + (uint32_t)((k >> 6) * (NT * 128) + ((k & 63) >> 3) * 128);
-                            tc05::mma_bf16(d, tc05::sdesc_swz(a_tap + (uint32_t)(32 * q), Cfg::ROW_BYTES),
-                                           tc05::sdesc(b_k, tc05::CANON_LBO, tc05::CANON_SBO), idesc,
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const int ty = tap / 3, tx = tap % 3;
+                        const uint64_t at = a0 + (uint64_t)(((ty * HALO_PX + tx) * Cfg::ROW_BYTES) >> 4);
+                        const uint64_t bt = b0 + (uint64_t)tap * b_tap_step;
+#pragma unroll
+                        for (int q = 0; q < CB / 16; ++q)
+                            tc05::mma_bf16(d, at + (uint64_t)(2 * q), bt + (uint64_t)(2 * q * NT), idesc,
                                            (cb > 0 || tap > 0 || q > 0) ? 1u : 0u);
-                        }
                     }
                     tc05::mma_commit(tc05::smem_u32(&empty[slot]));
                 }
@@ -806,8 +808,8 @@ __global__ void __launch_bounds__(TmaCfg<NT>::THREADS)
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         if constexpr (SW)
-                            tc05::mma_bf16(d, tc05::sdesc_sw128(a0 + q * 32), tc05::sdesc_sw128(b0 + q * 32), idesc,
-                                           (kc > 0 || q > 0) ? 1u : 0u);
+                            tc05::mma_bf16(d, tc05::sdesc_sw128(a0) + (uint64_t)(2 * q), tc05::sdesc_sw128(b0) + (uint64_t)(2 * q),
+                                           idesc, (kc > 0 || q > 0) ? 1u : 0u);
                         else
                             tc05::mma_bf16(d, tc05::sdesc(a0 + q * 2 * 2048, 2048, 128),
                                            tc05::sdesc(b0 + q * 2 * (NT * 16), NT * 16, 128), idesc,
