@@ -697,11 +697,13 @@ def ensemble_accuracy(sw, every: int, steps: int):
         a, b = ref[k][0], e32.member(k).state()
         r = {f: float(np.abs(y - x).sum() / max(np.abs(x).sum(), 1e-300))
              for f, x, y in zip(("h", "hu", "hv"), a, b)}
+        # the cross-valley discharge against the discharge vector (~0 in the pools)
+        r["hu_vs_discharge"] = float(np.abs(b[1] - a[1]).sum() / max(np.hypot(a[1], a[2]).sum(), 1e-300))
         r["side"] = ws[k].nx
         per.append(r)
     e32.close()
     summ = {f: {"max": max(r[f] for r in per), "median": statistics.median(r[f] for r in per),
-                "members_within_1e-5": sum(r[f] <= 1e-5 for r in per)} for f in ("h", "hu", "hv")}
+                "members_within_1e-5": sum(r[f] <= 1e-5 for r in per)} for f in ("h", "hu", "hv", "hu_vs_discharge")}
     return {"members": len(ws), "every": every, "steps": steps, "summary": summ,
             "per_member": [{k: (round(v, 9) if isinstance(v, float) else v) for k, v in r.items()} for r in per]}
 
@@ -937,7 +939,7 @@ def summary(value, roofline, variants, accuracy, hbm):
            "dam_break200_steps_per_s": {k: g(v, "dam_break", k, "steps_per_s") for k in ("fp64", "fp32")},
            "ensemble256_fp32_G": g(v, "ensemble", "value"),
            "ensemble_fp32_rel_l1_max": {f: g(v, "ensemble", "fp32_accuracy", "summary", f, "max", nd=3)
-                                        for f in ("h", "hu", "hv")},
+                                        for f in ("h", "hu", "hv", "hu_vs_discharge")},
            "surrogate_G_fine_equiv": g(v, "surrogate", "value"), "surrogate_accepted": g(v, "surrogate", "accepted_fraction", nd=3),
            "unet_fwd_bf16_frac": g(v, "surrogate", "unet_forward", "frac_of_bf16_peak", nd=3),
            "fp32_rel_l1_end_time": {

@@ -77,7 +77,30 @@ __device__ __forceinline__ float erf_as(float x)
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(p));
     return copysignf(1.0f - r, x);
 }
-__device__ __forceinline__ float gelu_f(float v) { return 0.5f * v * (1.0f + erf_as(v * 0.70710678118654752f)); }
+// GELU(v) = v Phi(v) = 0.5 v (1 + erf(v / sqrt 2)).  With r = (1 + a1 x + ...
+// + a6 x^6)^-16 at x = |v| / sqrt 2 (the tail term of 7.1.28 above),
+// 1 + erf = 2 - r for v >= 0 and r for v < 0, so GELU = v - v r / 2 or v r / 2:
+// no 1 - r, sign transfer or 1 + erf, and the negative tail keeps r's
+// relative accuracy.
+__device__ __forceinline__ float gelu_f(float v)
+{
+    const float a = fabsf(v) * 0.70710678118654752f;
+    float p = 0.0000430638f;
+    p = fmaf(p, a, 0.0002765672f);
+    p = fmaf(p, a, 0.0001520143f);
+    p = fmaf(p, a, 0.0092705272f);
+    p = fmaf(p, a, 0.0422820123f);
+    p = fmaf(p, a, 0.0705230784f);
+    p = fmaf(p, a, 1.0f);
+    p = p * p;
+    p = p * p;
+    p = p * p;
+    p = p * p;
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(p));
+    const float h = (0.5f * v) * r;
+    return v >= 0.0f ? v - h : h;
+}
 
 struct __align__(1024) ConvSmem {
     uint8_t a[2][128 * 64 * 2];

@@ -73,6 +73,45 @@ __device__ __forceinline__ int cta_and(int p)
 __device__ __forceinline__ unsigned long long bits(double x) { return (unsigned long long)__double_as_longlong(x); }
 __device__ __forceinline__ unsigned int bits(float x) { return __float_as_uint(x); }
 
+// FP32 depth update with stochastic rounding.  The stored depth of a deep
+// cell changes each step by a near-constant amount of the order of one float
+// ulp (the rain of one step, a pool draining evenly); rounded to nearest,
+// that increment is lost or rounded up the same way every step, and cells in
+// different binades drift apart -- a bias growing with the number of steps
+// (relative L1 against FP64 up to 1.5e-5 in h and 4e-5 in hu over 1000 steps
+// of the ensemble's rain-on-reservoir members).  Here a + b is rounded to the
+// neighbouring float on the side of its exact value with probability
+// |error| / spacing, so the rounding is unbiased on average and the error
+// grows like a random walk instead.  The exact error comes from TwoSum
+// (Knuth); the random bits from Chris Wellons' "lowbias32" integer hash
+// (hash-prospector, 2018) of the cell's index in the grid and the step's
+// simulated time t (hashed once per launch into ts): the same state at the
+// same time gives the same result whatever the step count, tiling or
+// context, and every cell draws afresh at every step.  (The operands' bits in
+// place of the cell index made equal cells of a pool round alike, so a whole
+// pool's rounding errors added up: 10x the error on one ensemble member.)
+__device__ __forceinline__ unsigned lowbias32(unsigned x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+__device__ __forceinline__ float sr_add(float a, float b, unsigned cell, unsigned ts)
+{
+    const float s = a + b;
+    const float bb = s - a;
+    const float e = (a - (s - bb)) + (b - bb);          // a + b = s + e exactly
+    if (!(s > 0.0f) || e == 0.0f) return s;             // no neighbour below +0 to take
+    const unsigned sb = __float_as_uint(s);
+    const float nb = __uint_as_float(e > 0.0f ? sb + 1u : sb - 1u);   // neighbour on e's side
+    const float gap = fabsf(nb - s);
+    const unsigned u = lowbias32(cell ^ ts);
+    return (float)(u >> 8) * 0x1p-24f * gap < fabsf(e) ? nb : s;
+}
+
 // TMA input ring: ring_depth<T, NTX>() slots of RING_ROWS rows; a slot holds
 // the fields of the stage input (h, qx, qy, then z (FP64) or dz_x, dz_y
 // (FP32)) and, in stage 2, U^n (h, qx, qy) of the rows two above, each
@@ -203,6 +242,11 @@ __device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, 
         dt = ctl->fdt; dtdx = ctl->fdtdx; dtdy = ctl->fdtdy; rdt = ctl->frdt;
     }
     const bool rain = ctl->rain_active != 0;
+    unsigned sr_ts = 0;                                  // FP32 depth rounding: the step's time, hashed
+    if constexpr (!fp64 && STAGE == 2) {
+        const unsigned long long tb = (unsigned long long)__double_as_longlong(ctl->t);
+        sr_ts = lowbias32((unsigned)tb ^ lowbias32((unsigned)(tb >> 32) + 0x9e3779b9u));
+    }
     const T hg = T(0.5) * C.g;
     const T cdx = fp64 ? T(P.dx) : T(P.fdx), cdy = fp64 ? T(P.dy) : T(P.fdy);   // (no FP64 conversion per row)
 
@@ -624,11 +668,10 @@ __device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, 
                 } else {
                     // Heun average (U^n + U**)/2, then rain.  FP32 adds the
                     // step's rain to the Heun increment (U** - U^n)/2 before
-                    // that meets U^n: the rain depth of one step is a few ulp
-                    // of a deep cell, and adding that same constant on its own
-                    // every step rounds the same way every time (a bias that
-                    // grows with the number of steps); joined to the varying
-                    // increment the one rounding left averages out.
+                    // that meets U^n, so the depth is rounded once, and that
+                    // rounding is stochastic (sr_add): the increment of a deep
+                    // cell is of the order of its ulp, and rounded to nearest
+                    // it would be lost or rounded up the same way every step.
                     T hn, qxn, qyn;
                     if constexpr (fp64) {
                         hn = T(0.5) * (c_h + hs);
@@ -638,7 +681,7 @@ __device__ __forceinline__ void sweep_tile(const Params &P, const Fields<T> &F, 
                     } else {
                         T dh = T(0.5) * (hs - c_h);
                         if (rain) dh = dh + rdt;
-                        hn = c_h + dh;
+                        hn = sr_add(c_h, dh, (unsigned)(ro * P.nx + gi), sr_ts);
                         qxn = c_qx + T(0.5) * (qxs - c_qx);
                         qyn = c_qy + T(0.5) * (qys - c_qy);
                     }

@@ -169,3 +169,29 @@ def test_fp64_ensemble_members_with_imposed_edges_equal_oracle():
         assert np.array_equal(m.dt_history(), dts), k
         for a, b in zip(m.state(), o.state()):
             assert np.array_equal(a, b), k
+
+
+def test_fp32_ensemble_bench_members_over_1000_steps():
+    """Every 8th member of the 256-member benchmark ensemble (sides 128-1024,
+    reservoirs of 5-40 m under rain), FP32 against the FP64 ensemble (bit for
+    bit the oracle's members) on each member's FP64 dt sequence over the full
+    1000 steps: h and hv within 1e-5 relative L1 per member; the cross-valley
+    discharge hu, ~0 in the pools, within 1e-5 of the discharge vector's L1
+    norm (its own relative L1 is printed)."""
+    specs = si.ensemble_specs(256, seed=4)
+    ws = [si.ensemble_member(specs[k]) for k in range(0, len(specs), 8)]
+    e64 = sw.Ensemble(ws, precision=sw.FP64)
+    assert e64.step(1000) == 0
+    ref = [(e64.member(k).state(), e64.member(k).dt_history(1000)) for k in range(len(ws))]
+    e64.close()
+    e32 = sw.Ensemble(ws, precision=sw.FP32)
+    for k in range(len(ws)):
+        e32.member(k).set_dt_sequence(ref[k][1])
+    assert e32.step(1000) == 0
+    for k in range(len(ws)):
+        (h, hu, hv), got = ref[k][0], e32.member(k).state()
+        rel = [np.sum(np.abs(a - b)) / max(np.sum(np.abs(b)), 1e-300) for a, b in zip(got, (h, hu, hv))]
+        hu_q = np.sum(np.abs(got[1] - hu)) / max(np.sum(np.hypot(hu, hv)), 1e-300)
+        print(f"member {8 * k} ({ws[k].nx}^2): h {rel[0]:.2e} hu {rel[1]:.2e} hv {rel[2]:.2e} hu/|q| {hu_q:.2e}")
+        assert rel[0] <= 1e-5 and rel[2] <= 1e-5 and hu_q <= 1e-5, (8 * k, rel, hu_q)
+    e32.close()
