@@ -932,6 +932,7 @@ def summary(value, roofline, variants, accuracy, hbm):
            "valley4096_fp64_G": g(v, "fp64", "value"), "valley4096_fp64_contracted_G": g(v, "fp64_contracted", "value"),
            "valley4096_fp64_step_hbm_frac": g(v, "fp64", "hbm_frac_algorithmic", nd=3),
            "valley4096_fp32_fully_wet_G": g(v, "fp32_fully_wet", "value"),
+           "valley4096_fp32_fully_wet_stage2_hbm_frac": g(v, "fp32_fully_wet", "stage2_hbm_frac", nd=3),
            "valley4096_fp64_fully_wet_G": g(v, "fp64_fully_wet", "value"),
            "rainfall2048_fp32_G": g(v, "rainfall", "fp32", "value"), "rainfall2048_fp64_G": g(v, "rainfall", "fp64", "value"),
            "rainfall2048_fp32_step_hbm_frac": g(v, "rainfall", "fp32", "step_frac_of_hbm", nd=3),
