@@ -111,13 +111,16 @@ __device__ __forceinline__ int find_inst(const long long *pre, int n, long long 
     return lo;
 }
 
-// Three resident CTAs of 128 threads (six of 64) per SM for FP32, registers
-// capped at 170: the stage code's live ranges otherwise take the kernel to
-// ~215 registers and two CTAs, measured 1.35x slower on the 256-member batch.
+// Four resident CTAs of 128 threads (eight of 64) per SM for FP32, registers
+// capped at 128 without spills: on the 256-member batch (200 steps, default
+// member shapes) 13.9 G cell-updates/s against 11.8 G at three CTAs (162
+// registers; ncu: 0.72 eligible warps per cycle, issue 50 % busy) and 13.4 G
+// at five (96 registers, spills); uncapped the stage code's live ranges take
+// ~215 registers and two CTAs.
 template <typename T>
 constexpr int ens_min_blocks(int ntx)
 {
-    return std::is_same<T, float>::value ? (ntx == 128 ? 3 : (ntx == 64 ? 6 : 1)) : 1;
+    return std::is_same<T, float>::value ? (ntx == 128 ? 4 : (ntx == 64 ? 8 : 1)) : 1;
 }
 
 // The launch's CTAs are NTX wide; each member's tiles are NTX - 4 columns
