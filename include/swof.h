@@ -451,6 +451,20 @@ SWOF_API int swof_surrogate_predict(swof_unet *u, const float *in, int B, float 
  * coarsened).  Errors: SWOF_EINVAL. */
 SWOF_API int swof_coarsen(swof_ctx *ctx, int f, float *out);
 
+/* The surrogate's static input channels from a fine bed z and K_s map
+ * (device float64 [ny][nx], caller-owned; ks NULL: the scalar ks_const
+ * everywhere), coarsened by block means over f x f cells (FP64 sums in a
+ * fixed order): channel 0 = dz_c/dx, 1 = dz_c/dy -- central differences of
+ * the block-mean bed z_c with spacings f dx, f dy, one-sided at the edges --
+ * and 2 = the block-mean K_s, written as device fp32 to
+ * out[k * snap_stride + c * (ny/f)(nx/f) + J (nx/f) + I] for every snapshot
+ * k < nsnap (out points at channel 0 of snapshot 0), enqueued on stream.
+ * nx, ny multiples of f, nx/f and ny/f >= 2, snap_stride >= 3 (ny/f)(nx/f).
+ * Not in the paper: the network's inputs (the dynamics depend on the bed's
+ * slopes, not its height).  Errors: SWOF_EINVAL. */
+SWOF_API int swof_coarsen_static(const double *z, const double *ks, double ks_const, int nx, int ny, double dx,
+                                 double dy, int f, float *out, long long snap_stride, int nsnap, void *stream);
+
 /* Per-member FP64 statistics of a batch of states [B][C][H][W] (device
  * fp32; channels h, hu, hv, then V_inf when C >= 4) into the device array
  * out[5B]: out[5b..5b+4] = {sum h, sum min(h, 0), discharge leaving through

@@ -148,6 +148,9 @@ _SIGS = {
     "swof_set_infiltrated_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "swof_get_infiltrated_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "swof_coarsen": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "swof_coarsen_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                           ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int, ctypes.c_void_p]),
     "swof_batch_stats": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 5 + [ctypes.c_double] * 2
                          + [ctypes.c_void_p, ctypes.c_void_p]),
     "swof_surrogate_rollout": (ctypes.c_int, [ctypes.c_void_p] * 2 + [ctypes.c_int] + [ctypes.c_void_p] * 8),
@@ -774,6 +777,19 @@ class UNet:
         _check(load().swof_surrogate_predict(self._u, ctypes.c_void_p(state_in.data_ptr()), int(state_in.shape[0]),
                                              ctypes.c_void_p(out.data_ptr()), self._s(stream)),
                "swof_surrogate_predict")
+
+
+def coarsen_static(z, ks, dx, dy, f, out, snap_stride, nsnap, ks_const=0.0, stream=None):
+    """The surrogate's static channels (bed slopes dz/dx, dz/dy of the f x f
+    block-mean bed, block-mean K_s) from device float64 tensors z and ks
+    [ny][nx] (ks None: ks_const) into the float32 CUDA tensor `out` (channel
+    0 of snapshot 0; snapshots snap_stride floats apart), swof_coarsen_static."""
+    ny, nx = z.shape
+    _check(load().swof_coarsen_static(ctypes.c_void_p(z.data_ptr()),
+                                      None if ks is None else ctypes.c_void_p(ks.data_ptr()), float(ks_const),
+                                      int(nx), int(ny), float(dx), float(dy), int(f),
+                                      ctypes.c_void_p(out.data_ptr()), int(snap_stride), int(nsnap),
+                                      None if stream is None else ctypes.c_void_p(stream)), "swof_coarsen_static")
 
 
 def batch_stats(states, out, outmask=0, dx=1.0, dy=1.0, stream=None):

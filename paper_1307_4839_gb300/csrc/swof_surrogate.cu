@@ -51,6 +51,42 @@ __global__ void k_coarsen(Params P, Fields<T> F, int f, float *out)
     }
 }
 
+// Block mean over the f x f fine cells of coarse cell (I, J) of a dense
+// [ny][nx] field (FP64 sum in a fixed order).
+__device__ __forceinline__ double block_mean(const double *a, int nx, int f, int I, int J)
+{
+    double s = 0.0;
+    for (int dj = 0; dj < f; ++dj)
+        for (int di = 0; di < f; ++di) s += a[(size_t)(J * f + dj) * nx + (size_t)(I * f + di)];
+    return s / ((double)f * f);
+}
+
+// The surrogate's static channels per coarse cell: the slopes of the
+// block-mean bed (central differences, one-sided at the edges, spacing
+// f dx and f dy -- each thread recomputes its neighbours' block means) and
+// the block-mean K_s, written to every snapshot.
+__global__ void k_coarsen_static(const double *z, const double *ks, double ks_const, int nx, int ny, double dx,
+                                 double dy, int f, float *out, long long snap_stride, int nsnap)
+{
+    const int cx = nx / f, cy = ny / f;
+    const long long plane = (long long)cx * cy;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < plane;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int J = (int)(i / cx), I = (int)(i - (long long)J * cx);
+        const int Iw = I > 0 ? I - 1 : I, Ie = I < cx - 1 ? I + 1 : I;
+        const int Js = J > 0 ? J - 1 : J, Jn = J < cy - 1 ? J + 1 : J;
+        const double zx = (block_mean(z, nx, f, Ie, J) - block_mean(z, nx, f, Iw, J)) / ((double)(Ie - Iw) * f * dx);
+        const double zy = (block_mean(z, nx, f, I, Jn) - block_mean(z, nx, f, I, Js)) / ((double)(Jn - Js) * f * dy);
+        const double kc = ks ? block_mean(ks, nx, f, I, J) : ks_const;
+        for (int k = 0; k < nsnap; ++k) {
+            float *o = out + (long long)k * snap_stride;
+            o[i] = (float)zx;
+            o[plane + i] = (float)zy;
+            o[2 * plane + i] = (float)kc;
+        }
+    }
+}
+
 // One block per member b of states [B][C][H][W] (channels h, hu, hv, then
 // V_inf when C >= 4).  out[5b .. 5b+4] = {sum h, sum min(h, 0), discharge
 // out of the domain through the edges flagged in outmask [m^3/s], sum V_inf,
@@ -285,6 +321,18 @@ int swof_coarsen(swof_ctx *c, int f, float *out)
         k_coarsen<double><<<grid_for(n), 256, 0, c->stream>>>(c->P, c->f64, f, out);
     else
         k_coarsen<float><<<grid_for(n), 256, 0, c->stream>>>(c->P, c->f32, f, out);
+    return cuerr(cudaGetLastError());
+}
+
+int swof_coarsen_static(const double *z, const double *ks, double ks_const, int nx, int ny, double dx, double dy,
+                        int f, float *out, long long snap_stride, int nsnap, void *stream)
+{
+    if (!z || !out || f < 1 || nx % f || ny % f || nx / f < 2 || ny / f < 2 || !(dx > 0) || !(dy > 0) || nsnap < 1 ||
+        snap_stride < 3LL * (nx / f) * (ny / f))
+        return SWOF_EINVAL;
+    const long long n = (long long)(nx / f) * (ny / f);
+    k_coarsen_static<<<grid_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(z, ks, ks_const, nx, ny, dx, dy, f,
+                                                                               out, snap_stride, nsnap);
     return cuerr(cudaGetLastError());
 }
 

@@ -27,7 +27,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from . import FP32, FRIC_MANNING, Solver, UNet, rollout as _rollout
+from . import FP32, FRIC_MANNING, Solver, UNet, coarsen_static, rollout as _rollout
 
 IN_CH, OUT_CH = 8, 4
 CH_RAIN, CH_ZX, CH_ZY, CH_KS = 4, 5, 6, 7
@@ -108,12 +108,16 @@ def generate(works, f: int, dt: float, span_steps: int, n_spans: int, precision=
     span = dt * span_steps
     times = np.arange(n_spans + 1) * span
     for i, w in enumerate(works):
+        # the static channels (bed slopes, K_s) on the device, every snapshot
+        zd = torch.from_numpy(np.ascontiguousarray(w.z, dtype=np.float64)).to("cuda")
+        ksd = (torch.from_numpy(np.ascontiguousarray(w.ks, dtype=np.float64)).to("cuda")
+               if isinstance(w.ks, np.ndarray) else None)
+        ks_const = 0.0 if isinstance(w.ks, np.ndarray) else float(w.ks)
+        coarsen_static(zd, ksd, w.dx, w.dy, f, data[i, 0, CH_ZX], IN_CH * Hc * Wc, n_spans + 1, ks_const=ks_const)
+        # the coarse bed and K_s the fallback solver runs on (host; its topography and map)
         z_c = block_mean(w.z, f)
         ks = w.ks if isinstance(w.ks, np.ndarray) else np.full((ny, nx), float(w.ks))
         ks_c = block_mean(ks, f)
-        zy, zx = np.gradient(z_c, f * w.dy, f * w.dx)
-        static = np.stack([zx, zy, ks_c]).astype(np.float32)
-        data[i, :, CH_ZX:CH_KS + 1] = torch.from_numpy(static).to("cuda")
         for k in range(n_spans + 1):
             data[i, k, CH_RAIN] = span_rain(w.rain_rate, w.rain_t_on, w.rain_t_off, times[k], span, span_steps)
         trajs.append(Trajectory(w, f, dt, span_steps, times, z_c, ks_c))

@@ -60,6 +60,44 @@ def test_coarsen_is_block_mean():
     np.testing.assert_allclose(got, ref, rtol=2e-7, atol=1e-30)
 
 
+def test_static_channels_on_the_device_match_numpy():
+    """The surrogate's static inputs from swof_coarsen_static -- slopes of the
+    block-mean bed (numpy.gradient's central and one-sided differences) and
+    the block-mean K_s -- against numpy, written to every snapshot; a scalar
+    K_s fills its channel."""
+    import torch
+    sw.build()
+    from paper_1307_4839_gb300.surrogate import block_mean
+    rng = np.random.default_rng(3)
+    ny, nx, f, dx, dy = 48, 80, 4, 1.5, 2.0
+    z = rng.standard_normal((ny, nx)).cumsum(axis=1) * 0.1
+    ks = np.exp(rng.standard_normal((ny, nx))) * 1e-6
+    out = torch.full((3, 5, 3, ny // f, nx // f), -1.0, device="cuda")     # [snapshot][slot][channel]
+    stride = 5 * 3 * (ny // f) * (nx // f)
+    sw.coarsen_static(torch.tensor(z, device="cuda"), torch.tensor(ks, device="cuda"), dx, dy, f,
+                      out[0, 1, 0], stride, 1)
+    torch.cuda.synchronize()
+    zc = block_mean(z, f)
+    zy, zx = np.gradient(zc, f * dy, f * dx)
+    ref = np.stack([zx, zy, block_mean(ks, f)])
+    got = out[0, 1].cpu().numpy().astype(np.float64)
+    # FP64 sums in another order, then one rounding to float32
+    assert np.all(np.abs(got - ref) <= 1e-7 * np.abs(ref) + 1e-20)
+    others = out.cpu().numpy()
+    others[0, 1] = -1.0
+    assert np.all(others == -1.0)                   # nothing written outside its block
+    # every snapshot (stride of one [slot][channel] block), scalar K_s
+    out2 = torch.full((4, 8, ny // f, nx // f), -1.0, device="cuda")      # [snapshot][channel]
+    sw.coarsen_static(torch.tensor(z, device="cuda"), None, dx, dy, f, out2[0, 5], 8 * (ny // f) * (nx // f), 4,
+                      ks_const=2.5e-6)
+    torch.cuda.synchronize()
+    o2 = out2.cpu().numpy()
+    for k in range(4):
+        assert np.array_equal(o2[k, 5:8], o2[0, 5:8]) and np.all(o2[k, :5] == -1.0)
+        assert np.all(o2[k, 7] == np.float32(2.5e-6))
+    assert np.all(np.abs(o2[0, 5:7] - ref[:2]) <= 1e-7 * np.abs(ref[:2]) + 1e-20)
+
+
 def test_batch_stats_against_numpy():
     import torch
     sw.build()
