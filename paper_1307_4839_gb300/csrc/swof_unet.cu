@@ -89,19 +89,17 @@ __global__ void k_colsum_fin(const float *part, int blocks, int N, int nb, float
 // 2x2 average pooling: x (channels [xc0, xc0+C) of stride cx) at H x W ->
 // y compact [B][H/2][W/2][C].  One thread per output pixel and 8-channel
 // group (C, cx and xc0 multiples of 8): four 16-byte loads, one store.
+template <typename I>
 __global__ void k_pool_fwd(const bf16 *x, int cx, int xc0, int B, int H, int W, int C, bf16 *y)
 {
-    const int G = C >> 3;
-    long long total = (long long)B * (H / 2) * (W / 2) * G;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-        int g = (int)(i % G);
-        long long q = i / G;
-        int xo = (int)(q % (W / 2));
-        long long r = q / (W / 2);
-        int yo = (int)(r % (H / 2));
-        int b = (int)(r / (H / 2));
-        long long base = ((long long)b * H + 2 * yo) * W + 2 * xo;
-        const int c0 = xc0 + 8 * g;
+    const I G = (I)(C >> 3), Wo = (I)(W / 2), Ho = (I)(H / 2);
+    const I total = (I)B * Ho * Wo * G;
+    for (I i = (I)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (I)gridDim.x * blockDim.x) {
+        const I q = i / G, g = i - q * G;
+        const I r = q / Wo, xo = q - r * Wo;
+        const I b = r / Ho, yo = r - b * Ho;
+        const long long base = ((long long)b * H + 2 * (long long)yo) * W + 2 * (long long)xo;
+        const int c0 = xc0 + 8 * (int)g;
         uint4 a = *reinterpret_cast<const uint4 *>(x + base * cx + c0);
         uint4 bq = *reinterpret_cast<const uint4 *>(x + (base + 1) * cx + c0);
         uint4 cq = *reinterpret_cast<const uint4 *>(x + (base + W) * cx + c0);
@@ -115,7 +113,7 @@ __global__ void k_pool_fwd(const bf16 *x, int cx, int xc0, int B, int H, int W, 
                       __bfloat162float(pd[k]);
             t[k] = __float2bfloat16_rn(0.25f * s);
         }
-        *reinterpret_cast<uint4 *>(y + q * C + 8 * g) = *reinterpret_cast<const uint4 *>(t);
+        *reinterpret_cast<uint4 *>(y + (long long)q * C + 8 * (long long)g) = *reinterpret_cast<const uint4 *>(t);
     }
 }
 
@@ -221,19 +219,21 @@ __global__ void k_replicate_bias(const float *b, int n, int reps, float *out)
 }
 
 // state [B][4][H][W] fp32 (h, hu, hv, z) -> x [B*H*W][16] bf16 normalised
+template <typename I>
 __global__ void k_pack_input(const float *state, int nin, int B, int H, int W, const float *mean, const float *inv,
                              bf16 *x)
 {
     // one thread per pixel: the nin channel planes read coalesced across
-    // threads, the pixel's 16 channels written as two 16-byte stores
-    const long long HW = (long long)H * W, P = (long long)B * HW;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
-        const long long b = p / HW, r = p - b * HW;
+    // threads, the pixel's 16 channels written as two 16-byte stores; index
+    // arithmetic in I (32-bit when the batch fits)
+    const I HW = (I)H * W, P = (I)B * HW;
+    for (I p = (I)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (I)gridDim.x * blockDim.x) {
+        const I b = p / HW, r = p - b * HW;
         __align__(16) bf16 t[16];
 #pragma unroll
         for (int c = 0; c < 16; ++c)
-            t[c] = __float2bfloat16_rn(c < nin ? (state[(b * nin + c) * HW + r] - mean[c]) * inv[c] : 0.0f);
-        uint4 *d = reinterpret_cast<uint4 *>(x + p * 16);
+            t[c] = __float2bfloat16_rn(c < nin ? (state[((long long)b * nin + c) * HW + r] - mean[c]) * inv[c] : 0.0f);
+        uint4 *d = reinterpret_cast<uint4 *>(x + (long long)p * 16);
         d[0] = reinterpret_cast<const uint4 *>(t)[0];
         d[1] = reinterpret_cast<const uint4 *>(t)[1];
     }
@@ -245,19 +245,20 @@ __global__ void k_pack_input(const float *state, int nin, int B, int H, int W, c
 // Kp.  One thread per pixel; the products of bf16 values are exact in FP32
 // and accumulate in FP32, as on the tensor cores (nout <= 16 outputs are
 // too few columns for an MMA tile).
+template <typename I>
 __global__ void k_head_residual(const bf16 *x, int C, const bf16 *w, int Kp, const float *bias, const float *in,
                                 int nin, int nout, int B, int H, int W, const float *scale, float *out)
 {
     extern __shared__ float swt[];            // [nout][C]
     for (int i = threadIdx.x; i < nout * C; i += blockDim.x) swt[i] = __bfloat162float(w[(i / C) * Kp + i % C]);
     __syncthreads();
-    const long long HW = (long long)H * W, P = (long long)B * HW;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+    const I HW = (I)H * W, P = (I)B * HW;
+    for (I p = (I)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (I)gridDim.x * blockDim.x) {
         float acc[16];
 #pragma unroll
         for (int c = 0; c < 16; ++c) acc[c] = 0.0f;
         for (int k0 = 0; k0 < C; k0 += 8) {
-            uint4 v = *reinterpret_cast<const uint4 *>(x + p * C + k0);
+            uint4 v = *reinterpret_cast<const uint4 *>(x + (long long)p * C + k0);
             const bf16 *pv = reinterpret_cast<const bf16 *>(&v);
             float xf[8];
 #pragma unroll
@@ -265,14 +266,24 @@ __global__ void k_head_residual(const bf16 *x, int C, const bf16 *w, int Kp, con
 #pragma unroll
             for (int c = 0; c < 16; ++c)
                 if (c < nout) {
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) acc[c] = fmaf(xf[j], swt[c * C + k0 + j], acc[c]);
+                    const float4 w0 = *reinterpret_cast<const float4 *>(swt + c * C + k0);
+                    const float4 w1 = *reinterpret_cast<const float4 *>(swt + c * C + k0 + 4);
+                    acc[c] = fmaf(xf[0], w0.x, acc[c]);
+                    acc[c] = fmaf(xf[1], w0.y, acc[c]);
+                    acc[c] = fmaf(xf[2], w0.z, acc[c]);
+                    acc[c] = fmaf(xf[3], w0.w, acc[c]);
+                    acc[c] = fmaf(xf[4], w1.x, acc[c]);
+                    acc[c] = fmaf(xf[5], w1.y, acc[c]);
+                    acc[c] = fmaf(xf[6], w1.z, acc[c]);
+                    acc[c] = fmaf(xf[7], w1.w, acc[c]);
                 }
         }
-        const long long b = p / HW, r = p - b * HW;
+        const I b = p / HW, r = p - b * HW;
 #pragma unroll
         for (int c = 0; c < 16; ++c)
-            if (c < nout) out[(b * nout + c) * HW + r] = in[(b * nin + c) * HW + r] + (acc[c] + bias[c]) * scale[c];
+            if (c < nout)
+                out[((long long)b * nout + c) * HW + r] =
+                    in[((long long)b * nin + c) * HW + r] + (acc[c] + bias[c]) * scale[c];
     }
 }
 
@@ -927,7 +938,12 @@ int forward(swof_unet *u, int B, cudaStream_t s, bool keep_pre = true, bool head
         if (l > 0) {
             int hp = u->H >> (l - 1), wp = u->W >> (l - 1), cp = C << (l - 1);
             long long n = (long long)B * h * w * cp;
-            swof::k_pool_fwd<<<swof::grid_for(n / 8), 256, 0, s>>>(u->cat[l - 1], 2 * cp, 0, B, hp, wp, cp, u->pool[l]);
+            if (n < (1LL << 31))
+                swof::k_pool_fwd<unsigned><<<swof::grid_for(n / 8), 256, 0, s>>>(u->cat[l - 1], 2 * cp, 0, B, hp, wp, cp,
+                                                                            u->pool[l]);
+            else
+                swof::k_pool_fwd<long long><<<swof::grid_for(n / 8), 256, 0, s>>>(u->cat[l - 1], 2 * cp, 0, B, hp, wp,
+                                                                             cp, u->pool[l]);
             in = Act{u->pool[l], cp, 0};
         }
         st = fwd_layer(u, 2 * l, B, h, w, in, Act{u->ea[l], c, 0}, pre(u->ea_pre[l]), nullptr, 0, s);
@@ -1303,6 +1319,17 @@ int swof_unet_activation(swof_unet *u, int which, int l, float *host, long long 
     return SWOF_OK;
 }
 
+// the input packing, with 32-bit index arithmetic when the batch fits
+void pack_input(const float *in, swof_unet *u, int B, long long P, cudaStream_t s)
+{
+    if (P * 16 < (1LL << 31))
+        swof::k_pack_input<unsigned><<<swof::grid_for(P), 256, 0, s>>>(in, u->in_ch, B, u->H, u->W, u->norm,
+                                                                     u->norm + 16, u->x0);
+    else
+        swof::k_pack_input<long long><<<swof::grid_for(P), 256, 0, s>>>(in, u->in_ch, B, u->H, u->W, u->norm,
+                                                                       u->norm + 16, u->x0);
+}
+
 // One AdamW update of the FP32 master weights from the current gradients.
 int swof_unet_adamw(swof_unet *u, float lr, float beta1, float beta2, float eps, float weight_decay, void *stream)
 {
@@ -1320,7 +1347,7 @@ int swof_surrogate_train_step(swof_unet *u, const float *in, const float *next, 
     cudaStream_t s = S(stream);
     long long P = (long long)B * u->H * u->W;
     cudaMemsetAsync(u->err, 0, sizeof(int), s);
-    swof::k_pack_input<<<swof::grid_for(P), 256, 0, s>>>(in, u->in_ch, B, u->H, u->W, u->norm, u->norm + 16, u->x0);
+    pack_input(in, u, B, P, s);
     swof::k_target<<<swof::grid_for(P * u->out_ch), 256, 0, s>>>(in, u->in_ch, next, u->out_ch, B, u->H, u->W,
                                                                    u->norm + 32, u->tgt);
     int st = loss_and_grads(u, B, s);
@@ -1334,12 +1361,17 @@ int swof_surrogate_predict(swof_unet *u, const float *in, int B, float *out, voi
     if (!u || !in || !out || B < 1 || B > u->maxB) return SWOF_EINVAL;
     cudaStream_t s = S(stream);
     long long P = (long long)B * u->H * u->W;
-    swof::k_pack_input<<<swof::grid_for(P), 256, 0, s>>>(in, u->in_ch, B, u->H, u->W, u->norm, u->norm + 16, u->x0);
+    pack_input(in, u, B, P, s);
     int st = forward(u, B, s, false, false);
     if (st) return st;
     const Layer &L = u->layers[17];
-    swof::k_head_residual<<<swof::grid_for(P), 256, (size_t)u->out_ch * u->C * sizeof(float), s>>>(
-        u->db[0], u->C, WB(u, 17), L.Kp, Bv(u, 17), in, u->in_ch, u->out_ch, B, u->H, u->W, u->norm + 32, out);
+    const size_t hs = (size_t)u->out_ch * u->C * sizeof(float);
+    if (P * 16 < (1LL << 31))
+        swof::k_head_residual<unsigned><<<swof::grid_for(P), 256, hs, s>>>(
+            u->db[0], u->C, WB(u, 17), L.Kp, Bv(u, 17), in, u->in_ch, u->out_ch, B, u->H, u->W, u->norm + 32, out);
+    else
+        swof::k_head_residual<long long><<<swof::grid_for(P), 256, hs, s>>>(
+            u->db[0], u->C, WB(u, 17), L.Kp, Bv(u, 17), in, u->in_ch, u->out_ch, B, u->H, u->W, u->norm + 32, out);
     return cudaGetLastError() == cudaSuccess ? SWOF_OK : SWOF_ECUDA;
 }
 
